@@ -1,0 +1,397 @@
+#!/usr/bin/env python
+"""Throughput of the dense state-vector hot path on one or more GB300s.
+
+Workload: the 30-qubit depth-20 random circuit (per layer a Haar-random
+single-qubit unitary on every qubit, then CZ on a random matching of the
+qubits, seed 1234): 600 single-qubit gates + 300 CZ = 900 gates on a
+complex64 state of 8 GiB.  One step = the whole path over that input:
+|0...0> initialisation, the 900 gates under the chosen plan, the FP64 norm,
+<sum Z> and 10^6 shots sampled from the FP64 prefix of |a|^2.
+
+Metric: gates/s (unfused gate count / step time) and the HBM GB/s of the
+step (algorithmic bytes / step time).  The state (8 GiB) is far larger than
+L2 (129 MB), so no L2 flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--plan P] [--impl reference]
+
+Multi-GPU: the path does not shard on these one-GPU machines; under torchrun
+each rank runs an independent replica of the workload (weak scaling), with a
+barrier and the max over ranks of the timed region.
+
+Prints one JSON line (rank 0).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "gates/s + HBM GB/s at 30 qubits; learned-fused FP32 vs plain per-gate at 1-F≤1e-6"
+N_QUBITS, DEPTH, SEED, SHOTS = 30, 20, 1234, 1_000_000
+
+
+def workload_name(n, depth):
+    return "haar_cz: %d qubits, depth %d (Haar U(2) on every qubit + CZ on a random matching per layer)" % (n, depth)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def mem_available_gb():
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    return int(line.split()[1]) / 2 ** 20
+    except Exception:
+        pass
+    return 0.0
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.file.read())) if len(r) >= 9]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def oracle_sample(gates, n_target, budget_s, warm_gates=0):
+    """Time the FP64 oracle gate by gate on this host's cores over a prefix of
+    the circuit until budget_s is spent.  Runs at n_target qubits when host
+    RAM allows (16 GiB state at 30 qubits), else at 28 qubits with the rate
+    scaled by 2^(n - 30) (the oracle's work per gate is proportional to 2^n)."""
+    import oracle
+    n = n_target
+    need = (2 ** n) * 16 / 2 ** 30 + 2.0
+    while n > 20 and mem_available_gb() < need * 1.3:
+        n -= 1
+        need = (2 ** n) * 16 / 2 ** 30 + 2.0
+    from paper_1805_00988_gb300 import circuits as C
+    g = gates if n == n_target else C.haar_cz(n, DEPTH, seed=SEED)
+    psi = oracle.basis_state(n, 0)
+    for k in range(warm_gates):
+        oracle.apply_circuit(psi, g[k:k + 1], inplace=True)
+    done, t0 = 0, time.perf_counter()
+    k = warm_gates
+    while True:
+        oracle.apply_circuit(psi, g[k % len(g):k % len(g) + 1], inplace=True)
+        done += 1
+        k += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or done >= len(g):
+            break
+    rate = done / el * (2.0 ** (n - n_target))
+    sample = "first %d gates of the %d-qubit circuit, FP64 oracle, %d host threads" % (
+        done, n, oracle.num_threads())
+    if n != n_target:
+        sample += ", rate scaled by 2^(%d-%d) to %d qubits (host RAM %.0f GB free)" % (
+            n, n_target, n_target, mem_available_gb())
+    return rate, sample, oracle.num_threads(), done, el
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    from paper_1805_00988_gb300 import circuits as C
+    gates = C.haar_cz(N_QUBITS, DEPTH, seed=SEED)
+    per_step = float(os.environ.get("QSIM_REF_STEP_SECONDS", "6"))
+    rates = []
+    info = None
+    for i in range(args.warmup + args.steps):
+        rate, sample, cores, done, el = oracle_sample(gates, N_QUBITS, per_step, warm_gates=0)
+        if i >= args.warmup:
+            rates.append(rate)
+            info = (sample, cores)
+    v = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "gates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 900.0 / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_name(N_QUBITS, DEPTH), "n_qubits": N_QUBITS,
+                                            "depth": DEPTH, "gates": 900, "state": "complex128 (host)"},
+            "cpu_baseline": {"value": v, "unit": "gates/s", "cores": info[1], "kind": "oracle", "sample": info[0]},
+            "e2e": {"value": v, "unit": "gates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU leg
+def infidelity_torch(a, b, chunk=1 << 26):
+    """1 - |<a|b>|^2 / (<a|a><b|b>) in FP64 over two CUDA tensors (chunked)."""
+    import torch
+    ip = torch.zeros((), dtype=torch.complex128, device=a.device)
+    na = torch.zeros((), dtype=torch.float64, device=a.device)
+    nb = torch.zeros((), dtype=torch.float64, device=a.device)
+    for o in range(0, a.numel(), chunk):
+        x = a[o:o + chunk].to(torch.complex128)
+        y = b[o:o + chunk].to(torch.complex128)
+        ip += torch.vdot(x, y)
+        na += torch.vdot(x, x).real
+        nb += torch.vdot(y, y).real
+    return float(1.0 - (ip.abs() ** 2) / (na * nb))
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_1805_00988_gb300 import build
+    build.build()
+    from paper_1805_00988_gb300 import circuits as C
+    from paper_1805_00988_gb300 import sim
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n, depth, shots = args.qubits, args.depth, args.shots
+    gates = C.haar_cz(n, depth, seed=SEED)
+    sg = sim.to_sim_gates(gates)
+    plan = args.plan
+    opts = sim.plan_opts(plan, fuse_k=args.fuse_k)
+    st = sim.State(n, "c64", device=dev)
+    stream = st.stream
+    shot_buf = torch.empty(shots, dtype=torch.int64, device=dev)
+
+    def step():
+        sim.sim_set_basis_state(st.h, 0)
+        sim.sim_apply_circuit(st.h, sg, opts)
+        nrm = sim.sim_norm(st.h)
+        ez = sim.sim_expect_z_sum(st.h)
+        sim.sim_sample(st.h, shots, 99, shot_buf.data_ptr(), out_on_device=True)
+        return nrm, ez
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    clk = ClockSampler(vis.split(",")[local_rank] if vis else str(local_rank))
+    sim.sim_profile_read(st.h, reset=True)
+    sim.sim_profile_enable(st.h, True)
+    l0 = sim.sim_launch_count(st.h)
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        nrm, ez = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    launches = sim.sim_launch_count(st.h) - l0
+    prof = sim.sim_profile_read(st.h, reset=True)
+    sim.sim_profile_enable(st.h, False)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    gates_per_s = world * len(gates) / (ms_per_step / 1e3)
+    step_bytes = sum(v[2] for v in prof.values()) / args.steps
+    peaks, peak_kind = load_peaks()
+
+    # roofline: the kernel class with the largest device time
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    dname, (dl, dms, dbytes) = dom
+    achieved = (dbytes / dl) / (dms / dl / 1e3) / 1e9
+    roofline = {"kernel": dname, "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peak_kind + " (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
+                else "fallback 6.8 TB/s", "alg_bytes_per_launch": dbytes / dl,
+                "avg_launch_ms": dms / dl, "launches": dl}
+    kernels = {k: {"launches": v[0], "ms": v[1], "alg_GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None}
+               for k, v in prof.items()}
+
+    # end to end through the public API with host buffers
+    host_gates = torch.empty(sg.nbytes, dtype=torch.uint8, pin_memory=True)
+    hg = host_gates.numpy().view(sim.SIM_GATE_DTYPE)
+    hg[:] = sg
+    host_shots = torch.empty(shots, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sim.sim_set_basis_state(st.h, 0)
+        sim.sim_apply_circuit(st.h, hg, opts)
+        sim.sim_norm(st.h)
+        sim.sim_expect_z_sum(st.h)
+        sim.sim_sample(st.h, shots, 99, out=host_shots)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": world * len(gates) / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": int(sg.nbytes),
+           "d2h_bytes_per_step": int(shots * 8 + 16)}
+
+    line = {"metric": METRIC, "value": gates_per_s, "unit": "gates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Haar/CZ circuit)",
+            "config": {"workload": workload_name(n, depth), "n_qubits": n, "depth": depth,
+                       "gates": int(len(gates)), "state": "complex64", "plan": plan, "shots": shots,
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (8 GiB state vs 129 MB L2); no flush"},
+            "hbm_gbs": world * step_bytes / (ms_per_step / 1e3) / 1e9,
+            "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
+            "kernels": kernels, "norm": nrm, "expect_z_sum": ez}
+
+    # plan variants on the same workload, each with its infidelity
+    if args.variants and rank == 0:
+        line["variants"] = run_variants(args, sim, C, gates, sg, dev, st, peaks)
+
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        rate, sample, cores, done, el = oracle_sample(gates, n, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": "gates/s", "cores": cores, "kind": "oracle",
+                                "sample": sample, "seconds": el}
+    st.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_variants(args, sim, C, gates, sg, dev, st_c64, peaks):
+    """Each plan once warm, timed once or twice; infidelity of every complex64
+    result against the complex128 per-gate state (itself checked against the
+    FP64 oracle at up to 20 qubits by the parity tests)."""
+    import torch
+    out = {}
+    stream = st_c64.stream
+
+    def timed(st, opts, reps):
+        sim.sim_set_basis_state(st.h, 0)
+        sim.sim_apply_circuit(st.h, sg, opts)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            sim.sim_set_basis_state(st.h, 0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(st.stream)
+            sim.sim_apply_circuit(st.h, sg, opts)
+            e1.record(st.stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        return best
+
+    ref = sim.State(args.qubits, "c128", device=dev)
+    t128 = timed(ref, sim.plan_opts("per_gate"), 1)
+    out["per_gate_c128"] = {"ms": t128, "gates_per_s": len(gates) / (t128 / 1e3), "infidelity": 0.0,
+                            "note": "reference state for the complex64 infidelities"}
+    for plan in args.variant_plans:
+        try:
+            opts = sim.plan_opts(plan, fuse_k=args.fuse_k)
+            t = timed(st_c64, opts, 2)
+            inf = infidelity_torch(st_c64.tensor, ref.tensor)
+            out[plan + "_c64"] = {"ms": t, "gates_per_s": len(gates) / (t / 1e3), "infidelity": inf}
+        except sim.SimError as e:
+            out[plan + "_c64"] = {"error": str(e)}
+    ref.close()
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--plan", default="per_gate")
+    ap.add_argument("--fuse-k", type=int, default=5)
+    ap.add_argument("--qubits", type=int, default=N_QUBITS)
+    ap.add_argument("--depth", type=int, default=DEPTH)
+    ap.add_argument("--shots", type=int, default=SHOTS)
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--variant-plans", default="per_gate")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    args.variant_plans = [p for p in args.variant_plans.split(",") if p]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

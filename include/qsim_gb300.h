@@ -1,0 +1,172 @@
+/*
+ * qsim_gb300.h -- C ABI of the GB300 (sm_103a) dense state-vector simulator.
+ *
+ * The operations are those of Kelly, "Simulating Quantum Computers Using
+ * OpenCL" (arXiv:1805.00988): a register of n qubits held as 2^n complex
+ * amplitudes (§2.1), single-qubit gates given as 2x2 matrices applied by
+ * Algorithm 1 (§2.3), the same gates with control qubits (§2.3, App. B.2),
+ * probabilities |a_j|^2 (App. B.3) and measurement / repeated sampling from
+ * one state (§1.3.3, §2.4).
+ *
+ * Conventions used by every entry point:
+ *   - amplitude j is the coefficient of basis state |j>; qubit t is bit t of
+ *     j (qubit 0 = least-significant bit), as the App. B kernels index it.
+ *   - SIM_C64 = interleaved (re, im) FP32 pairs, 8 bytes per amplitude (§2.1);
+ *     SIM_C128 = interleaved FP64 pairs, 16 bytes.
+ *   - a gate matrix is [[A, B], [C, D]] given as 8 doubles
+ *     (A.re, A.im, B.re, B.im, C.re, C.im, D.re, D.im), row-major (App. B.1).
+ *     A controlled gate updates only index pairs whose control bits are all 1.
+ *   - all sizes are in elements unless named *_bytes.
+ *
+ * Ownership and ordering: host arrays passed in are copied before the call
+ * returns.  Work is enqueued on the handle's CUDA stream and is asynchronous
+ * unless the entry point returns a host value (it then synchronises that
+ * stream).  Device pointers passed in stay owned by the caller.
+ *
+ * Errors: every entry point returns a sim_status; nothing throws or aborts
+ * across the ABI.  Arguments are validated on the host before any launch.
+ * sim_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef QSIM_GB300_H
+#define QSIM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qsim_state *sim_t;
+
+typedef enum { SIM_C64 = 0, SIM_C128 = 1 } sim_dtype;
+typedef enum { SIM_F32 = 0, SIM_F64 = 1 } sim_real;
+
+typedef enum {
+    SIM_OK = 0,
+    SIM_EINVAL = 1,        /* bad argument (qubit out of range, duplicate control, ...) */
+    SIM_ENOMEM = 2,        /* device allocation failed or state does not fit */
+    SIM_ECUDA = 3,         /* a CUDA runtime call failed */
+    SIM_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    SIM_EUNSUPPORTED = 5   /* valid request this build does not implement */
+} sim_status;
+
+/* Gate kinds of sim_gate.kind.  SIM_GATE_U takes its matrix from
+ * sim_gate.matrix; the named kinds build it from sim_gate.params:
+ *   RX/RY/RZ(theta) = exp(-i theta sigma / 2), P(lambda) = diag(1, e^{i lambda}),
+ *   U3(theta, phi, lambda) = [[cos t/2, -e^{i l} sin t/2], [e^{i p} sin t/2, e^{i(p+l)} cos t/2]].
+ * SIM_GATE_SWAP exchanges qubits target and target2. */
+typedef enum {
+    SIM_GATE_U = 0, SIM_GATE_X = 1, SIM_GATE_Y = 2, SIM_GATE_Z = 3, SIM_GATE_H = 4,
+    SIM_GATE_S = 5, SIM_GATE_SDG = 6, SIM_GATE_T = 7, SIM_GATE_TDG = 8,
+    SIM_GATE_RX = 9, SIM_GATE_RY = 10, SIM_GATE_RZ = 11, SIM_GATE_P = 12, SIM_GATE_U3 = 13,
+    SIM_GATE_SWAP = 14
+} sim_gate_kind;
+
+/* One gate of a circuit (112 bytes, no padding). */
+typedef struct sim_gate {
+    int32_t kind;          /* sim_gate_kind */
+    int32_t target;        /* target qubit */
+    int32_t target2;       /* second qubit of SIM_GATE_SWAP, else ignored */
+    int32_t n_controls;    /* 0, 1 or 2 */
+    int32_t controls[2];   /* control qubits; all must be 1 for the update */
+    double params[3];      /* theta, phi, lambda */
+    double matrix[8];      /* SIM_GATE_U: A, B, C, D as (re, im) */
+} sim_gate;
+
+/* How sim_apply_circuit schedules a gate list.  Every plan computes the same
+ * product of gates (Algorithm 1 applied gate after gate); they differ in how
+ * many passes over the state they make. */
+typedef enum {
+    SIM_PLAN_PER_GATE = 0,   /* one kernel launch per gate (one state pass each) */
+    SIM_PLAN_STAGED = 1,     /* runs of gates applied per tile in one pass (registers + shared memory) */
+    SIM_PLAN_FUSED = 2,      /* gates fused into k-qubit unitaries built in FP64, applied on tensor cores */
+    SIM_PLAN_LEARNED = 3     /* per-block choice made by the trained cost model */
+} sim_plan_kind;
+
+typedef struct sim_plan_opts {
+    int32_t plan;            /* sim_plan_kind */
+    int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block, 2..6 */
+    int32_t tile_qubits;     /* SIM_PLAN_STAGED: tile size log2 (0 = default) */
+    int32_t flags;           /* reserved, 0 */
+} sim_plan_opts;
+
+/* ---- handles --------------------------------------------------------------
+ * sim_create: allocate a 2^n state on the current CUDA device and set it to
+ *   |0...0> (§2.1).  n in [1, 34]; the state must fit in free device memory
+ *   (SIM_ENOMEM otherwise).  stream: a cudaStream_t (NULL = the handle
+ *   creates its own non-blocking stream).
+ * sim_create_from_buffer: wrap caller-owned device memory of at least
+ *   2^n * sizeof(amplitude) bytes, 16-byte aligned; its contents are kept.
+ * sim_destroy: free what the handle owns (not a wrapped buffer). */
+int sim_create(int n, int dtype, void *stream, sim_t *out);
+int sim_create_from_buffer(int n, int dtype, void *dev_ptr, size_t bytes, void *stream, sim_t *out);
+int sim_destroy(sim_t s);
+int sim_state_info(sim_t s, int *n, int *dtype, void **dev_ptr, size_t *bytes);
+int sim_synchronize(sim_t s);
+
+/* sim_set_basis_state: the state becomes |j>, j < 2^n (§2.1 starts at j = 0). */
+int sim_set_basis_state(sim_t s, uint64_t j);
+
+/* sim_load_state / sim_copy_state: copy 2^n amplitudes of the handle's dtype
+ * from / to src / dst (host memory when *_is_host, else device memory). */
+int sim_load_state(sim_t s, const void *src, int src_is_host);
+int sim_copy_state(sim_t s, void *dst, int dst_is_host);
+
+/* ---- gates ----------------------------------------------------------------
+ * sim_apply_gate: Algorithm 1 (§2.3) with matrix U on qubit target; with
+ *   n_controls in {1, 2} only the pairs whose control bits are all 1 are
+ *   updated (§2.3, App. B.2).  SIM_EINVAL if a qubit is out of range, a
+ *   control equals the target or two controls are equal.
+ * sim_apply_circuit: apply n_gates gates in order, scheduled by opts (NULL =
+ *   SIM_PLAN_PER_GATE).  The whole list is validated before anything runs. */
+int sim_apply_gate(sim_t s, const double U[8], int target, const int *controls, int n_controls);
+int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts);
+
+/* ---- measurement ------------------------------------------------------------
+ * sim_probabilities: p_j = |a_j|^2 for all j (App. B.3) into dev_out, a device
+ *   array of 2^n floats (out_real = SIM_F32) or doubles (SIM_F64).
+ * sim_norm: sum_j |a_j|^2 accumulated in FP64 (squares taken in FP64).
+ * sim_measure: measure one qubit in the computational basis (§1.3.3):
+ *   p0, p1 summed in FP64; outcome 0 iff p0 > u (p0 + p1) with
+ *   u = (splitmix64(seed + draw) >> 11) * 2^-53 (SplitMix64, Steele et al.
+ *   2014); the other half is zeroed and the kept half scaled by
+ *   1 / sqrt(p_outcome).  *prob (may be NULL) gets p_outcome / (p0 + p1).
+ * sim_sample: non-destructive shot sampling (§2.4): shot s is the smallest j
+ *   with C_j > u_s C_total, C the inclusive FP64 prefix of |a_j|^2,
+ *   u_s = (splitmix64(seed + s) >> 11) * 2^-53.  out: shots uint64 indices,
+ *   on the device when out_on_device, else host memory.
+ * sim_expect_z_sum: <sum_i Z_i> = sum_x |a_x|^2 (n - 2 popcount x), FP64. */
+int sim_probabilities(sim_t s, void *dev_out, int out_real);
+int sim_norm(sim_t s, double *out);
+int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob);
+int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
+int sim_expect_z_sum(sim_t s, double *out);
+
+/* ---- instrumentation --------------------------------------------------------
+ * sim_profile_enable: when on, every kernel launch of the handle is bracketed
+ *   by CUDA events on the handle's stream.
+ * sim_profile_read: synchronise, then report per kernel class (see
+ *   sim_kernel_class_name) the launches, summed device milliseconds and
+ *   summed algorithmic bytes (the state bytes each launch must read and
+ *   write: 2S / 2^c for a dense gate with c controls, S for a pass over the
+ *   whole state, ...) since the last reset; any output array may be NULL;
+ *   reset != 0 clears the counters.  Fills at most max_classes entries.
+ * sim_launch_count: kernels this handle has launched since creation. */
+int sim_profile_enable(sim_t s, int on);
+int sim_profile_read(sim_t s, int max_classes, uint64_t *launches, double *total_ms, double *alg_bytes,
+                     int reset);
+int sim_launch_count(sim_t s, uint64_t *out);
+const char *sim_kernel_class_name(int k);
+int sim_num_kernel_classes(void);
+
+/* Thread-local description of the last failure (empty string if none). */
+const char *sim_last_error(void);
+/* Library version string. */
+const char *sim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSIM_GB300_H */

@@ -113,10 +113,17 @@ def basis_state(n: int, j: int = 0) -> np.ndarray:
     return psi
 
 
-def apply_circuit(psi: np.ndarray, gates: np.ndarray) -> np.ndarray:
-    """Apply the gate list in order to a copy of psi (complex128); returns it."""
+def apply_circuit(psi: np.ndarray, gates: np.ndarray, inplace: bool = False) -> np.ndarray:
+    """Apply the gate list in order to a copy of psi (complex128); returns it.
+    With inplace=True psi (a C-contiguous complex128 array) is updated and
+    returned."""
     lib = _load()
-    out = np.array(psi, dtype=np.complex128, copy=True, order="C")
+    if inplace:
+        if psi.dtype != np.complex128 or not psi.flags["C_CONTIGUOUS"]:
+            raise ValueError("inplace needs a C-contiguous complex128 array")
+        out = psi
+    else:
+        out = np.array(psi, dtype=np.complex128, copy=True, order="C")
     n = _nqubits(out)
     m = len(gates)
     kind = np.array([KINDS[str(x)] for x in gates["name"]], dtype=np.int32)

@@ -1,0 +1,390 @@
+// api.cu -- the C ABI: handles, validation, dispatch, measurement host logic,
+// instrumentation.  Every entry point returns a sim_status and records a
+// thread-local message on failure; nothing throws across the boundary.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "internal.cuh"
+
+namespace qsim {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int status, const std::string &msg)
+{
+    set_error(msg);
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    char buf[512];
+    snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+    set_error(buf);
+    return e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA;
+}
+
+const char *kernel_class_name(int k)
+{
+    static const char *names[KC_COUNT] = {"init", "dense", "diag", "perm", "swap", "staged", "fused",
+                                          "fuse_build", "prob", "reduce", "collapse", "sample", "batch", "mlp"};
+    return (k >= 0 && k < KC_COUNT) ? names[k] : "?";
+}
+
+static cudaEvent_t pool_event(qsim_state *s)
+{
+    if (s->event_next < s->event_pool.size()) return s->event_pool[s->event_next++];
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    s->event_pool.push_back(e);
+    s->event_next = s->event_pool.size();
+    return e;
+}
+
+void launch_begin(qsim_state *s, int cls, double alg_bytes)
+{
+    if (!s->profiling) return;
+    qsim_state::Mark m{cls, alg_bytes, pool_event(s), pool_event(s)};
+    if (m.a) cudaEventRecord(m.a, s->stream);
+    s->marks.push_back(m);
+}
+
+int launch_end(qsim_state *s, const char *what)
+{
+    s->launches++;
+    if (s->profiling && !s->marks.empty() && s->marks.back().b) cudaEventRecord(s->marks.back().b, s->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return SIM_OK;
+}
+
+int ensure_device(qsim_state *s, void **buf, size_t *cap, size_t need)
+{
+    if (*cap >= need) return SIM_OK;
+    if (*buf) QSIM_CUDA(cudaFreeAsync(*buf, s->stream));
+    *buf = nullptr;
+    *cap = 0;
+    size_t sz = need < 4096 ? 4096 : need;
+    QSIM_CUDA(cudaMallocAsync(buf, sz, s->stream));
+    *cap = sz;
+    return SIM_OK;
+}
+
+int ensure_host_pinned(void **buf, size_t *cap, size_t need)
+{
+    if (*cap >= need) return SIM_OK;
+    if (*buf) cudaFreeHost(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    size_t sz = need < 4096 ? 4096 : need;
+    QSIM_CUDA(cudaMallocHost(buf, sz));
+    *cap = sz;
+    return SIM_OK;
+}
+
+static int amp_bytes(int dtype) { return dtype == SIM_C128 ? 16 : 8; }
+
+static int init_handle(qsim_state *s, void *stream)
+{
+    QSIM_CUDA(cudaGetDevice(&s->device));
+    QSIM_CUDA(cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device));
+    if (stream) {
+        s->stream = (cudaStream_t)stream;
+        s->owns_stream = false;
+    } else {
+        QSIM_CUDA(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+        s->owns_stream = true;
+    }
+    QSIM_CUDA(cudaMalloc((void **)&s->red_partial, sizeof(double) * 2 * kRedBlocks));
+    QSIM_CUDA(cudaMalloc((void **)&s->red_out, sizeof(double) * 4));
+    QSIM_CUDA(cudaMallocHost((void **)&s->host_red, sizeof(double) * 4));
+    return SIM_OK;
+}
+
+static void free_handle(qsim_state *s)
+{
+    if (!s) return;
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    if (s->owns_amps && s->amps) cudaFree(s->amps);
+    if (s->red_partial) cudaFree(s->red_partial);
+    if (s->red_out) cudaFree(s->red_out);
+    if (s->host_red) cudaFreeHost(s->host_red);
+    if (s->dev_ops) cudaFree(s->dev_ops);
+    if (s->host_ops) cudaFreeHost(s->host_ops);
+    for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
+    if (s->owns_stream && s->stream) cudaStreamDestroy(s->stream);
+    delete s;
+}
+
+static int check_handle(sim_t s)
+{
+    if (!s) return fail(SIM_EINVAL, "null handle");
+    return SIM_OK;
+}
+
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" {
+
+const char *sim_last_error(void) { return g_last_error.c_str(); }
+const char *sim_version(void) { return "qsim-gb300 0.1 (sm_103a)"; }
+const char *sim_kernel_class_name(int k) { return kernel_class_name(k); }
+int sim_num_kernel_classes(void) { return KC_COUNT; }
+
+int sim_create(int n, int dtype, void *stream, sim_t *out)
+{
+    set_error("");
+    if (!out) return fail(SIM_EINVAL, "sim_create: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 34) return fail(SIM_EINVAL, "sim_create: n must be in [1, 34]");
+    if (dtype != SIM_C64 && dtype != SIM_C128) return fail(SIM_EINVAL, "sim_create: unknown dtype");
+    qsim_state *s = new (std::nothrow) qsim_state();
+    if (!s) return fail(SIM_ENOMEM, "sim_create: host allocation");
+    s->n = n;
+    s->dtype = dtype;
+    s->bytes = (size_t)amp_bytes(dtype) << n;
+    int rc = init_handle(s, stream);
+    if (rc) { free_handle(s); return rc; }
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && s->bytes > free_b) {
+        free_handle(s);
+        return fail(SIM_ENOMEM, "sim_create: state does not fit in free device memory");
+    }
+    cudaError_t e = cudaMalloc(&s->amps, s->bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        free_handle(s);
+        return fail(SIM_ENOMEM, "sim_create: device allocation of the state failed");
+    }
+    s->owns_amps = true;
+    rc = launch_init_basis(s, 0);
+    if (rc) { free_handle(s); return rc; }
+    *out = s;
+    return SIM_OK;
+}
+
+int sim_create_from_buffer(int n, int dtype, void *dev_ptr, size_t bytes, void *stream, sim_t *out)
+{
+    set_error("");
+    if (!out) return fail(SIM_EINVAL, "sim_create_from_buffer: out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > 34) return fail(SIM_EINVAL, "sim_create_from_buffer: n must be in [1, 34]");
+    if (dtype != SIM_C64 && dtype != SIM_C128) return fail(SIM_EINVAL, "sim_create_from_buffer: unknown dtype");
+    if (!dev_ptr || ((uintptr_t)dev_ptr & 15)) return fail(SIM_EINVAL, "sim_create_from_buffer: buffer must be 16-byte aligned");
+    const size_t need = (size_t)amp_bytes(dtype) << n;
+    if (bytes < need) return fail(SIM_EINVAL, "sim_create_from_buffer: buffer too small for 2^n amplitudes");
+    qsim_state *s = new (std::nothrow) qsim_state();
+    if (!s) return fail(SIM_ENOMEM, "host allocation");
+    s->n = n;
+    s->dtype = dtype;
+    s->bytes = need;
+    s->amps = dev_ptr;
+    s->owns_amps = false;
+    int rc = init_handle(s, stream);
+    if (rc) { free_handle(s); return rc; }
+    *out = s;
+    return SIM_OK;
+}
+
+int sim_destroy(sim_t s)
+{
+    if (!s) return SIM_OK;
+    free_handle(s);
+    return SIM_OK;
+}
+
+int sim_state_info(sim_t s, int *n, int *dtype, void **dev_ptr, size_t *bytes)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (n) *n = s->n;
+    if (dtype) *dtype = s->dtype;
+    if (dev_ptr) *dev_ptr = s->amps;
+    if (bytes) *bytes = s->bytes;
+    return SIM_OK;
+}
+
+int sim_synchronize(sim_t s)
+{
+    if (int rc = check_handle(s)) return rc;
+    QSIM_CUDA(cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+int sim_set_basis_state(sim_t s, uint64_t j)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (j >> s->n) return fail(SIM_EINVAL, "sim_set_basis_state: j >= 2^n");
+    return launch_init_basis(s, j);
+}
+
+int sim_load_state(sim_t s, const void *src, int src_is_host)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (!src) return fail(SIM_EINVAL, "sim_load_state: src is NULL");
+    QSIM_CUDA(cudaMemcpyAsync(s->amps, src, s->bytes, src_is_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                              s->stream));
+    if (src_is_host) QSIM_CUDA(cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+int sim_copy_state(sim_t s, void *dst, int dst_is_host)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (!dst) return fail(SIM_EINVAL, "sim_copy_state: dst is NULL");
+    QSIM_CUDA(cudaMemcpyAsync(dst, s->amps, s->bytes, dst_is_host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                              s->stream));
+    if (dst_is_host) QSIM_CUDA(cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+int sim_apply_gate(sim_t s, const double U[8], int target, const int *controls, int n_controls)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (!U) return fail(SIM_EINVAL, "sim_apply_gate: U is NULL");
+    if (n_controls < 0 || n_controls > 2 || (n_controls > 0 && !controls))
+        return fail(SIM_EINVAL, "sim_apply_gate: n_controls must be 0..2 with a controls array");
+    sim_gate g;
+    memset(&g, 0, sizeof g);
+    g.kind = SIM_GATE_U;
+    g.target = target;
+    g.target2 = -1;
+    g.n_controls = n_controls;
+    g.controls[0] = n_controls > 0 ? controls[0] : -1;
+    g.controls[1] = n_controls > 1 ? controls[1] : -1;
+    memcpy(g.matrix, U, sizeof g.matrix);
+    std::string why;
+    if (validate_gate(s->n, g, &why)) return fail(SIM_EINVAL, "sim_apply_gate: " + why);
+    return launch_pair_gate(s, make_pair_gate(g));
+}
+
+int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (n_gates == 0) return SIM_OK;
+    if (!gates) return fail(SIM_EINVAL, "sim_apply_circuit: gates is NULL");
+    for (size_t k = 0; k < n_gates; ++k) {
+        std::string why;
+        if (validate_gate(s->n, gates[k], &why)) {
+            char buf[64];
+            snprintf(buf, sizeof buf, "sim_apply_circuit: gate %zu: ", k);
+            return fail(SIM_EINVAL, buf + why);
+        }
+    }
+    sim_plan_opts o{};
+    o.plan = SIM_PLAN_PER_GATE;
+    if (opts) o = *opts;
+    switch (o.plan) {
+    case SIM_PLAN_PER_GATE:
+        for (size_t k = 0; k < n_gates; ++k)
+            if (int rc = launch_pair_gate(s, make_pair_gate(gates[k]))) return rc;
+        return SIM_OK;
+    case SIM_PLAN_STAGED:
+        return apply_circuit_staged(s, gates, n_gates, o);
+    case SIM_PLAN_FUSED:
+    case SIM_PLAN_LEARNED:
+        return apply_circuit_fused(s, gates, n_gates, o);
+    default:
+        return fail(SIM_EINVAL, "sim_apply_circuit: unknown plan");
+    }
+}
+
+int sim_probabilities(sim_t s, void *dev_out, int out_real)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (!dev_out) return fail(SIM_EINVAL, "sim_probabilities: dev_out is NULL");
+    if (out_real != SIM_F32 && out_real != SIM_F64) return fail(SIM_EINVAL, "sim_probabilities: out_real");
+    return launch_probabilities(s, dev_out, out_real);
+}
+
+int sim_norm(sim_t s, double *out)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (!out) return fail(SIM_EINVAL, "sim_norm: out is NULL");
+    double r[2];
+    if (int rc = reduce_sums(s, RED_NORM, 0, r)) return rc;
+    *out = r[0];
+    return SIM_OK;
+}
+
+int sim_expect_z_sum(sim_t s, double *out)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (!out) return fail(SIM_EINVAL, "sim_expect_z_sum: out is NULL");
+    double r[2];
+    if (int rc = reduce_sums(s, RED_EXPZ, 0, r)) return rc;
+    *out = r[0];
+    return SIM_OK;
+}
+
+int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (qubit < 0 || qubit >= s->n) return fail(SIM_EINVAL, "sim_measure: qubit out of range");
+    double r[2];
+    if (int rc = reduce_sums(s, RED_BIT, qubit, r)) return rc;
+    const double p0 = r[0], p1 = r[1];
+    if (!(p0 + p1 > 0.0)) return fail(SIM_EINVAL, "sim_measure: the state has zero norm");
+    const double u = uniform_host(seed, draw);
+    const int m = (p0 > u * (p0 + p1)) ? 0 : 1;
+    const double pm = m ? p1 : p0;
+    if (int rc = launch_collapse(s, qubit, m, 1.0 / std::sqrt(pm))) return rc;
+    if (outcome) *outcome = m;
+    if (prob) *prob = pm / (p0 + p1);
+    return SIM_OK;
+}
+
+int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (shots > 0 && !out) return fail(SIM_EINVAL, "sim_sample: out is NULL");
+    return run_sample(s, shots, seed, out, out_on_device);
+}
+
+int sim_profile_enable(sim_t s, int on)
+{
+    if (int rc = check_handle(s)) return rc;
+    s->profiling = on != 0;
+    return SIM_OK;
+}
+
+int sim_profile_read(sim_t s, int max_classes, uint64_t *launches, double *total_ms, double *alg_bytes, int reset)
+{
+    if (int rc = check_handle(s)) return rc;
+    QSIM_CUDA(cudaStreamSynchronize(s->stream));
+    for (const auto &m : s->marks) {
+        float ms = 0.f;
+        if (m.a && m.b && cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            s->prof_launches[m.cls]++;
+            s->prof_ms[m.cls] += ms;
+            s->prof_bytes[m.cls] += m.bytes;
+        }
+    }
+    s->marks.clear();
+    s->event_next = 0;
+    for (int k = 0; k < max_classes && k < KC_COUNT; ++k) {
+        if (launches) launches[k] = s->prof_launches[k];
+        if (total_ms) total_ms[k] = s->prof_ms[k];
+        if (alg_bytes) alg_bytes[k] = s->prof_bytes[k];
+    }
+    if (reset) {
+        for (int k = 0; k < KC_COUNT; ++k) { s->prof_launches[k] = 0; s->prof_ms[k] = 0; s->prof_bytes[k] = 0; }
+    }
+    return SIM_OK;
+}
+
+int sim_launch_count(sim_t s, uint64_t *out)
+{
+    if (int rc = check_handle(s)) return rc;
+    if (out) *out = s->launches;
+    return SIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// internal.cuh -- shared declarations of the CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qsim_gb300.h"
+
+namespace qsim {
+
+// ---------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int fail(int status, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define QSIM_CUDA(call)                                                   \
+    do {                                                                  \
+        cudaError_t e_ = (call);                                          \
+        if (e_ != cudaSuccess) return ::qsim::cuda_fail(e_, #call);       \
+    } while (0)
+
+// ---------------------------------------------------------------- kernel classes
+// Every launch is tagged with one class for launch counting and profiling.
+enum KernelClass {
+    KC_INIT = 0,
+    KC_DENSE,        // dense 2x2 on amplitude pairs (Algorithm 1)
+    KC_DIAG,         // diagonal / phase gates
+    KC_PERM,         // X / CNOT / Toffoli moves and antidiagonal gates
+    KC_SWAP,
+    KC_STAGED,       // multi-gate tile pass
+    KC_FUSED,        // fused k-qubit unitary apply
+    KC_FUSE_BUILD,   // FP64 fused-unitary construction
+    KC_PROB,         // probabilities
+    KC_REDUCE,       // norm / masked sums / <Z> partial reductions
+    KC_COLLAPSE,
+    KC_SAMPLE,       // block sums, scans, shot location, resolution
+    KC_BATCH,        // batched persistent circuits
+    KC_MLP,          // cost-model forward / backward / Adam
+    KC_COUNT
+};
+const char *kernel_class_name(int k);
+
+}  // namespace qsim
+
+// ---------------------------------------------------------------- handle
+struct qsim_state {
+    int n = 0;
+    int dtype = SIM_C64;
+    void *amps = nullptr;
+    size_t bytes = 0;
+    bool owns_amps = false;
+    bool owns_stream = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int num_sms = 0;
+    // FP64 reduction scratch (partials of fixed-grid reductions), owned
+    double *red_partial = nullptr;   // kRedBlocks * 4 doubles
+    double *red_out = nullptr;       // 4 doubles
+    double *host_red = nullptr;      // pinned, 4 doubles
+    // circuit upload buffers (device), grown on demand
+    void *dev_ops = nullptr;
+    size_t dev_ops_bytes = 0;
+    void *host_ops = nullptr;        // pinned staging
+    size_t host_ops_bytes = 0;
+    // instrumentation
+    uint64_t launches = 0;
+    bool profiling = false;
+    struct Mark { int cls; double bytes; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> event_pool;
+    size_t event_next = 0;
+    uint64_t prof_launches[qsim::KC_COUNT] = {0};
+    double prof_ms[qsim::KC_COUNT] = {0};
+    double prof_bytes[qsim::KC_COUNT] = {0};
+};
+
+namespace qsim {
+
+constexpr int kRedBlocks = 1216;     // 152 SMs x 8 blocks: fixed grid for deterministic FP64 sums
+constexpr int kRedThreads = 256;
+
+// Launch bracketing: call begin() before and end() after each kernel launch.
+// alg_bytes = the bytes the launch must move at minimum (what the operation
+// reads and writes of the state), used for roofline accounting.
+void launch_begin(qsim_state *s, int cls, double alg_bytes = 0.0);
+int launch_end(qsim_state *s, const char *what);
+
+// ---------------------------------------------------------------- per-gate kernels
+// Classified gate, ready for a per-gate launch.
+enum GateOp { OP_DENSE = 0, OP_DIAG, OP_DIAG_HI, OP_ANTIDIAG, OP_XPERM, OP_SWAP, OP_IDENTITY };
+
+struct PairGate {
+    int op;
+    int target;            // qubit t (first qubit of a swap)
+    int target2;           // swap partner
+    int nctrl;
+    int ctrl[2];
+    double m[8];           // A, B, C, D (re, im)
+};
+
+// Classify a 2x2 matrix (exact comparisons): identity, diagonal, phase on |1>,
+// pure X, antidiagonal or dense.
+int classify_matrix(const double m[8]);
+
+// Build the matrix of a named gate kind; returns 0 or -1 for an unknown kind.
+int gate_matrix(int kind, const double *params, const double *matrix, double out[8]);
+
+// Validate one ABI gate for an n-qubit register.
+int validate_gate(int n, const sim_gate &g, std::string *why);
+
+// Turn an ABI gate into a classified PairGate.
+PairGate make_pair_gate(const sim_gate &g);
+
+int launch_pair_gate(qsim_state *s, const PairGate &g);
+
+// ---------------------------------------------------------------- reductions
+// mode for masked FP64 sums of |a|^2
+enum RedMode { RED_NORM = 0, RED_BIT = 1, RED_EXPZ = 2 };
+int launch_init_basis(qsim_state *s, uint64_t j);
+int reduce_sums(qsim_state *s, int mode, int qubit, double out[2]);
+int launch_probabilities(qsim_state *s, void *dev_out, int out_real);
+int launch_collapse(qsim_state *s, int qubit, int outcome, double scale);
+int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
+
+// ---------------------------------------------------------------- staged / fused plans
+int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
+int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
+
+// host-side SplitMix64 draw (Steele, Lea & Flood 2014)
+uint64_t splitmix64_host(uint64_t x);
+double uniform_host(uint64_t seed, uint64_t s);
+
+// grow a device buffer owned by the handle (stream-ordered)
+int ensure_device(qsim_state *s, void **buf, size_t *cap, size_t need);
+int ensure_host_pinned(void **buf, size_t *cap, size_t need);
+
+}  // namespace qsim

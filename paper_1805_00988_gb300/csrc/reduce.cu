@@ -1,0 +1,512 @@
+// reduce.cu -- state initialisation, probabilities, FP64 reductions,
+// single-qubit collapse and shot sampling.
+//
+// Probabilities are |a_j|^2 (App. B.3).  Every sum of probabilities (norm,
+// the two halves of a single-qubit measurement, <sum Z>, the sampling CDF) is
+// accumulated in FP64 from squares taken in FP64, over a fixed grid and a
+// fixed tree, so results are bit-reproducible run to run.
+//
+// Sampling (§2.4: many outcomes from one state without re-running the gates)
+// is an inverse CDF over the FP64 prefix of |a_j|^2 that is never
+// materialised for the whole state: per-block sums, one scan over the block
+// sums, shots bucketed by block (counting sort), then one CTA per touched
+// block scans that block in shared memory and resolves its shots.  About two
+// reads of the state in total.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace qsim {
+
+namespace {
+
+// ---------------------------------------------------------------- SplitMix64
+// Steele, Lea & Flood, OOPSLA 2014: add the golden gamma, then the variant-13
+// finaliser.  Uniform draw u = (x >> 11) * 2^-53.
+__host__ __device__ __forceinline__ uint64_t smix(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+__host__ __device__ __forceinline__ double unif(uint64_t seed, uint64_t s)
+{
+    return (double)(smix(seed + s) >> 11) * 0x1.0p-53;
+}
+
+// ---------------------------------------------------------------- init
+// Zero the state with 16-byte stores and write amplitude j = 1.
+__global__ void k_init_basis(uint4 *__restrict__ st, uint64_t nvec, uint64_t jvec, uint4 jval)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nvec;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        st[i] = (i == jvec) ? jval : make_uint4(0, 0, 0, 0);
+}
+
+// ---------------------------------------------------------------- block reduce
+template <int NT>
+__device__ __forceinline__ void block_sum2(double &a, double &b, double *sh)
+{
+    // fixed-order tree: warp butterflies, then warp 0 over the warp results
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) { sh[2 * w] = a; sh[2 * w + 1] = b; }
+    __syncthreads();
+    if (w == 0) {
+        a = (l < NT / 32) ? sh[2 * l] : 0.0;
+        b = (l < NT / 32) ? sh[2 * l + 1] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+    }
+    __syncthreads();
+}
+
+template <typename R>
+__device__ __forceinline__ double sq(R re, R im)
+{
+    const double r = (double)re, i = (double)im;
+    return r * r + i * i;
+}
+
+
+// VEC amplitudes per 16-byte vector: 2 for complex64, 1 for complex128
+template <typename R> struct AV;
+template <> struct AV<float> {
+    static constexpr int VEC = 2;
+    __device__ __forceinline__ static void load(const float *st, uint64_t v, double p[2])
+    {
+        const float4 x = reinterpret_cast<const float4 *>(st)[v];
+        p[0] = sq<float>(x.x, x.y);
+        p[1] = sq<float>(x.z, x.w);
+    }
+};
+template <> struct AV<double> {
+    static constexpr int VEC = 1;
+    __device__ __forceinline__ static void load(const double *st, uint64_t v, double p[2])
+    {
+        const double2 x = reinterpret_cast<const double2 *>(st)[v];
+        p[0] = sq<double>(x.x, x.y);
+        p[1] = 0.0;
+    }
+};
+
+// Masked FP64 sums over a contiguous range per block.
+//   RED_NORM: out0 = sum |a|^2
+//   RED_BIT : out0 = sum over bit q = 0, out1 = sum over bit q = 1
+//   RED_EXPZ: out0 = sum |a_x|^2 (n - 2 popcount x)
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_masked_sum(const R *__restrict__ st, uint64_t nvec, uint64_t per,
+                                                            int mode, int q, int n, double *__restrict__ partial)
+{
+    constexpr int VEC = AV<R>::VEC;
+    __shared__ double sh[2 * kRedThreads / 32];
+    const uint64_t lo = (uint64_t)blockIdx.x * per;
+    const uint64_t hi = min(nvec, lo + per);
+    double a = 0.0, b = 0.0;
+    for (uint64_t v = lo + threadIdx.x; v < hi; v += kRedThreads) {
+        double p[2];
+        AV<R>::load(st, v, p);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const uint64_t i = v * VEC + e;
+            if (mode == RED_NORM) {
+                a += p[e];
+            } else if (mode == RED_BIT) {
+                if ((i >> q) & 1ull) b += p[e]; else a += p[e];
+            } else {
+                a += p[e] * (double)(n - 2 * __popcll(i));
+            }
+        }
+    }
+    block_sum2<kRedThreads>(a, b, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_final_sum(const double *__restrict__ partial, int nblk,
+                                                           double *__restrict__ out)
+{
+    __shared__ double sh[2 * kRedThreads / 32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblk; i += kRedThreads) {
+        a += partial[2 * i];
+        b += partial[2 * i + 1];
+    }
+    block_sum2<kRedThreads>(a, b, sh);
+    if (threadIdx.x == 0) { out[0] = a; out[1] = b; }
+}
+
+// ---------------------------------------------------------------- probabilities
+template <typename R, typename O>
+__global__ void k_probabilities(const R *__restrict__ st, uint64_t N, O *__restrict__ p)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const R re = st[2 * i], im = st[2 * i + 1];
+        if (sizeof(O) == sizeof(R)) p[i] = (O)(re * re + im * im);
+        else p[i] = (O)sq<R>(re, im);
+    }
+}
+
+// ---------------------------------------------------------------- collapse
+template <typename R>
+__global__ void k_collapse(R *__restrict__ st, uint64_t N, int q, int outcome, R scale)
+{
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        if ((int)((i >> q) & 1ull) == outcome) {
+            st[2 * i] *= scale;
+            st[2 * i + 1] *= scale;
+        } else {
+            st[2 * i] = (R)0;
+            st[2 * i + 1] = (R)0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- sampling
+constexpr int kSampleLog = 13;             // 8192 amplitudes per sampling block
+constexpr int kScanThreads = 1024;
+
+// FP64 sum of |a|^2 per block of bs amplitudes (one CTA per block).
+template <typename R>
+__global__ void __launch_bounds__(256) k_block_sums(const R *__restrict__ st, uint64_t bs, double *__restrict__ bsum)
+{
+    constexpr int VEC = AV<R>::VEC;
+    __shared__ double sh[2 * 256 / 32];
+    const uint64_t nv = bs / VEC;
+    const uint64_t lo = (uint64_t)blockIdx.x * nv;
+    double a = 0.0, b = 0.0;
+    for (uint64_t v = threadIdx.x; v < nv; v += 256) {
+        double p[2];
+        AV<R>::load(st, lo + v, p);
+        a += p[0];
+        if (VEC == 2) a += p[1];
+    }
+    block_sum2<256>(a, b, sh);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = a;
+}
+
+// Exclusive scan of nb values in one CTA: contiguous segments per thread,
+// serial inside a segment, a fixed Hillis-Steele scan over segment totals.
+template <typename T>
+__global__ void __launch_bounds__(kScanThreads) k_scan_exclusive(const T *__restrict__ in, T *__restrict__ out,
+                                                                 uint64_t nb, T *__restrict__ total)
+{
+    __shared__ T seg[kScanThreads];
+    const uint64_t per = (nb + kScanThreads - 1) / kScanThreads;
+    const uint64_t lo = (uint64_t)threadIdx.x * per;
+    const uint64_t hi = min(nb, lo + per);
+    T loc = 0;
+    for (uint64_t i = lo; i < hi; ++i) loc += in[i];
+    seg[threadIdx.x] = loc;
+    __syncthreads();
+    for (int off = 1; off < kScanThreads; off <<= 1) {
+        T v = (threadIdx.x >= (unsigned)off) ? seg[threadIdx.x - off] : (T)0;
+        __syncthreads();
+        seg[threadIdx.x] += v;
+        __syncthreads();
+    }
+    T run = (threadIdx.x > 0) ? seg[threadIdx.x - 1] : (T)0;
+    if (threadIdx.x == kScanThreads - 1) *total = seg[kScanThreads - 1];
+    T acc = 0;
+    for (uint64_t i = lo; i < hi; ++i) {
+        out[i] = run + acc;
+        acc += in[i];
+    }
+}
+
+// shot s -> block: smallest b with bexcl[b] + bsum[b] > u_s * total; none ->
+// the last block with a non-zero sum.
+__global__ void k_locate(uint64_t shots, uint64_t seed, const double *__restrict__ bexcl,
+                         const double *__restrict__ bsum, uint64_t nb, const double *__restrict__ total,
+                         uint32_t *__restrict__ shot_blk, uint32_t *__restrict__ counts, uint64_t last_nz_blk)
+{
+    const double tot = *total;
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < shots;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const double t = unif(seed, s) * tot;
+        uint64_t lo = 0, hi = nb;
+        while (lo < hi) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (bexcl[mid] + bsum[mid] > t) hi = mid; else lo = mid + 1;
+        }
+        const uint32_t b = (uint32_t)((lo < nb) ? lo : last_nz_blk);
+        shot_blk[s] = b;
+        atomicAdd(&counts[b], 1u);
+    }
+}
+
+// last block with a non-zero sum (single thread; nb scanned backwards)
+__global__ void k_last_nonzero(const double *__restrict__ bsum, uint64_t nb, uint64_t *__restrict__ out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        uint64_t b = nb;
+        while (b > 0 && !(bsum[b - 1] > 0.0)) --b;
+        *out = (b > 0) ? b - 1 : 0;
+    }
+}
+
+__global__ void k_scatter(uint64_t shots, const uint32_t *__restrict__ shot_blk, uint32_t *__restrict__ cursor,
+                          uint32_t *__restrict__ order)
+{
+    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < shots;
+         s += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t pos = atomicAdd(&cursor[shot_blk[s]], 1u);
+        order[pos] = (uint32_t)s;
+    }
+}
+
+// One CTA per block that received shots: |a|^2 of the block loaded into
+// shared memory (coalesced), inclusive FP64 scan there, then each shot takes
+// the smallest j with bexcl + C_j > u_s * total (none -> the block's last
+// non-zero amplitude).
+template <typename R>
+__global__ void __launch_bounds__(256) k_resolve(const R *__restrict__ st, uint64_t bs, uint64_t seed,
+                                                 const double *__restrict__ bexcl, const double *__restrict__ total,
+                                                 const uint32_t *__restrict__ counts,
+                                                 const uint32_t *__restrict__ offs, const uint32_t *__restrict__ order,
+                                                 uint64_t *__restrict__ out)
+{
+    constexpr int VEC = AV<R>::VEC;
+    extern __shared__ double cdf[];            // bs doubles
+    __shared__ double tsum[256];
+    __shared__ int last_nz;
+    const uint32_t cnt = counts[blockIdx.x];
+    if (cnt == 0) return;
+    if (threadIdx.x == 0) last_nz = -1;
+    __syncthreads();
+    const uint64_t base = (uint64_t)blockIdx.x * bs;
+    int my_last = -1;
+    for (uint64_t v = threadIdx.x; v < bs / VEC; v += 256) {
+        double p[2];
+        AV<R>::load(st, base / VEC + v, p);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            cdf[v * VEC + e] = p[e];
+            if (p[e] > 0.0) my_last = (int)(v * VEC + e);
+        }
+    }
+    if (my_last >= 0) atomicMax(&last_nz, my_last);
+    __syncthreads();
+    const uint64_t per = (bs + 255) / 256;
+    const uint64_t lo = threadIdx.x * per, hi = min(bs, lo + per);
+    double acc = 0.0;
+    for (uint64_t i = lo; i < hi; ++i) {
+        acc += cdf[i];
+        cdf[i] = acc;
+    }
+    tsum[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        double v = (threadIdx.x >= (unsigned)off) ? tsum[threadIdx.x - off] : 0.0;
+        __syncthreads();
+        tsum[threadIdx.x] += v;
+        __syncthreads();
+    }
+    const double pre = bexcl[blockIdx.x] + ((threadIdx.x > 0) ? tsum[threadIdx.x - 1] : 0.0);
+    for (uint64_t i = lo; i < hi; ++i) cdf[i] += pre;
+    __syncthreads();
+    const double tot = *total;
+    const uint32_t o0 = offs[blockIdx.x];
+    for (uint32_t k = threadIdx.x; k < cnt; k += 256) {
+        const uint32_t s = order[o0 + k];
+        const double t = unif(seed, s) * tot;
+        uint64_t a = 0, b = bs;
+        while (a < b) {
+            const uint64_t mid = (a + b) >> 1;
+            if (cdf[mid] > t) b = mid; else a = mid + 1;
+        }
+        const uint64_t j = (a < bs) ? a : (uint64_t)max(last_nz, 0);
+        out[s] = base + j;
+    }
+}
+
+unsigned grid_for(uint64_t work, int threads, int num_sms)
+{
+    uint64_t g = (work + threads - 1) / threads;
+    const uint64_t cap = (uint64_t)num_sms * 32;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+}  // namespace
+
+uint64_t splitmix64_host(uint64_t x) { return smix(x); }
+double uniform_host(uint64_t seed, uint64_t s) { return unif(seed, s); }
+
+int launch_init_basis(qsim_state *s, uint64_t j)
+{
+    const size_t amp = (s->dtype == SIM_C128) ? 16 : 8;
+    const uint64_t nvec = (uint64_t)(s->bytes / 16);
+    uint64_t jvec;
+    uint4 jval = make_uint4(0, 0, 0, 0);
+    if (amp == 16) {
+        jvec = j;
+        const double one = 1.0;
+        uint64_t bits;
+        memcpy(&bits, &one, 8);
+        jval.x = (uint32_t)bits; jval.y = (uint32_t)(bits >> 32);
+    } else {
+        jvec = j / 2;
+        const float one = 1.0f;
+        uint32_t bits;
+        memcpy(&bits, &one, 4);
+        if (j & 1) jval.z = bits; else jval.x = bits;
+    }
+    launch_begin(s, KC_INIT, (double)s->bytes);
+    k_init_basis<<<grid_for(nvec, 256, s->num_sms), 256, 0, s->stream>>>((uint4 *)s->amps, nvec, jvec, jval);
+    return launch_end(s, "init basis");
+}
+
+int reduce_sums(qsim_state *s, int mode, int qubit, double out[2])
+{
+    const uint64_t N = 1ull << s->n;
+    const uint64_t nvec = (s->dtype == SIM_C128) ? N : N / 2;
+    const uint64_t per = (nvec + kRedBlocks - 1) / kRedBlocks;
+    launch_begin(s, KC_REDUCE, (double)s->bytes);
+    if (s->dtype == SIM_C128)
+        k_masked_sum<double><<<kRedBlocks, kRedThreads, 0, s->stream>>>((const double *)s->amps, nvec, per, mode,
+                                                                       qubit, s->n, s->red_partial);
+    else
+        k_masked_sum<float><<<kRedBlocks, kRedThreads, 0, s->stream>>>((const float *)s->amps, nvec, per, mode,
+                                                                      qubit, s->n, s->red_partial);
+    int rc = launch_end(s, "masked sum");
+    if (rc) return rc;
+    launch_begin(s, KC_REDUCE);
+    k_final_sum<<<1, kRedThreads, 0, s->stream>>>(s->red_partial, kRedBlocks, s->red_out);
+    rc = launch_end(s, "final sum");
+    if (rc) return rc;
+    QSIM_CUDA(cudaMemcpyAsync(s->host_red, s->red_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    QSIM_CUDA(cudaStreamSynchronize(s->stream));
+    out[0] = s->host_red[0];
+    out[1] = s->host_red[1];
+    return SIM_OK;
+}
+
+int launch_probabilities(qsim_state *s, void *dev_out, int out_real)
+{
+    const uint64_t N = 1ull << s->n;
+    const unsigned g = grid_for(N, 256, s->num_sms);
+    launch_begin(s, KC_PROB, (double)s->bytes + (double)N * (out_real == SIM_F64 ? 8.0 : 4.0));
+    if (s->dtype == SIM_C128) {
+        if (out_real == SIM_F64) k_probabilities<double, double><<<g, 256, 0, s->stream>>>((const double *)s->amps, N, (double *)dev_out);
+        else k_probabilities<double, float><<<g, 256, 0, s->stream>>>((const double *)s->amps, N, (float *)dev_out);
+    } else {
+        if (out_real == SIM_F64) k_probabilities<float, double><<<g, 256, 0, s->stream>>>((const float *)s->amps, N, (double *)dev_out);
+        else k_probabilities<float, float><<<g, 256, 0, s->stream>>>((const float *)s->amps, N, (float *)dev_out);
+    }
+    return launch_end(s, "probabilities");
+}
+
+int launch_collapse(qsim_state *s, int qubit, int outcome, double scale)
+{
+    const uint64_t N = 1ull << s->n;
+    const unsigned g = grid_for(N, 256, s->num_sms);
+    launch_begin(s, KC_COLLAPSE, 1.5 * (double)s->bytes);
+    if (s->dtype == SIM_C128)
+        k_collapse<double><<<g, 256, 0, s->stream>>>((double *)s->amps, N, qubit, outcome, scale);
+    else
+        k_collapse<float><<<g, 256, 0, s->stream>>>((float *)s->amps, N, qubit, outcome, (float)scale);
+    return launch_end(s, "collapse");
+}
+
+int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device)
+{
+    if (shots == 0) return SIM_OK;
+    if (shots > 0xFFFFFFFFull) return fail(SIM_EINVAL, "sim_sample: at most 2^32 - 1 shots per call");
+    const uint64_t N = 1ull << s->n;
+    const uint64_t bs = (s->n >= kSampleLog) ? (1ull << kSampleLog) : N;
+    const uint64_t nb = N / bs;
+    // scratch: bsum, bexcl (nb doubles), counts, offs, cursor (nb u32), total, last (8 B each),
+    //          shot_blk, order (shots u32), out (shots u64 when the caller wants host output)
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    const size_t o_bsum = take(nb * 8), o_bexcl = take(nb * 8), o_tot = take(8), o_last = take(8);
+    const size_t o_cnt = take(nb * 4), o_offs = take(nb * 4), o_cur = take(nb * 4), o_u32tot = take(8);
+    const size_t o_sblk = take(shots * 4), o_order = take(shots * 4);
+    const size_t o_out = out_on_device ? 0 : take(shots * 8);
+    char *scratch = nullptr;
+    QSIM_CUDA(cudaMallocAsync((void **)&scratch, off, s->stream));
+    double *bsum = (double *)(scratch + o_bsum), *bexcl = (double *)(scratch + o_bexcl);
+    double *tot = (double *)(scratch + o_tot);
+    uint64_t *last = (uint64_t *)(scratch + o_last);
+    uint32_t *cnt = (uint32_t *)(scratch + o_cnt), *offs = (uint32_t *)(scratch + o_offs);
+    uint32_t *cur = (uint32_t *)(scratch + o_cur), *u32tot = (uint32_t *)(scratch + o_u32tot);
+    uint32_t *sblk = (uint32_t *)(scratch + o_sblk), *order = (uint32_t *)(scratch + o_order);
+    uint64_t *dout = out_on_device ? out : (uint64_t *)(scratch + o_out);
+    int rc = SIM_OK;
+    const bool c128 = s->dtype == SIM_C128;
+    do {
+        launch_begin(s, KC_SAMPLE, (double)s->bytes);
+        if (c128) k_block_sums<double><<<(unsigned)nb, 256, 0, s->stream>>>((const double *)s->amps, bs, bsum);
+        else k_block_sums<float><<<(unsigned)nb, 256, 0, s->stream>>>((const float *)s->amps, bs, bsum);
+        if ((rc = launch_end(s, "block sums"))) break;
+        launch_begin(s, KC_SAMPLE);
+        k_scan_exclusive<double><<<1, kScanThreads, 0, s->stream>>>(bsum, bexcl, nb, tot);
+        if ((rc = launch_end(s, "block scan"))) break;
+        launch_begin(s, KC_SAMPLE);
+        k_last_nonzero<<<1, 32, 0, s->stream>>>(bsum, nb, last);
+        if ((rc = launch_end(s, "last nonzero"))) break;
+        // the host needs the last non-zero block as a launch argument: read it
+        // together with the total (one small copy; the state stays on device)
+        double htot = 0.0;
+        uint64_t hlast = 0;
+        if (cudaMemcpyAsync(&htot, tot, 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&hlast, last, 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            cudaStreamSynchronize(s->stream) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "sample readback");
+            break;
+        }
+        if (!(htot > 0.0)) { rc = fail(SIM_EINVAL, "sim_sample: the state has zero norm"); break; }
+        if (cudaMemsetAsync(cnt, 0, nb * 4, s->stream) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset"); break; }
+        launch_begin(s, KC_SAMPLE);
+        k_locate<<<grid_for(shots, 256, s->num_sms), 256, 0, s->stream>>>(shots, seed, bexcl, bsum, nb, tot, sblk,
+                                                                           cnt, hlast);
+        if ((rc = launch_end(s, "locate shots"))) break;
+        launch_begin(s, KC_SAMPLE);
+        k_scan_exclusive<uint32_t><<<1, kScanThreads, 0, s->stream>>>(cnt, offs, nb, u32tot);
+        if ((rc = launch_end(s, "bucket scan"))) break;
+        if (cudaMemcpyAsync(cur, offs, nb * 4, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "cursor copy");
+            break;
+        }
+        launch_begin(s, KC_SAMPLE);
+        k_scatter<<<grid_for(shots, 256, s->num_sms), 256, 0, s->stream>>>(shots, sblk, cur, order);
+        if ((rc = launch_end(s, "scatter shots"))) break;
+        const size_t smem = bs * sizeof(double);
+        launch_begin(s, KC_SAMPLE, (double)s->bytes);
+        if (c128) {
+            cudaFuncSetAttribute(k_resolve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_resolve<double><<<(unsigned)nb, 256, smem, s->stream>>>((const double *)s->amps, bs, seed, bexcl, tot,
+                                                                      cnt, offs, order, dout);
+        } else {
+            cudaFuncSetAttribute(k_resolve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            k_resolve<float><<<(unsigned)nb, 256, smem, s->stream>>>((const float *)s->amps, bs, seed, bexcl, tot,
+                                                                     cnt, offs, order, dout);
+        }
+        if ((rc = launch_end(s, "resolve shots"))) break;
+        if (!out_on_device) {
+            if (cudaMemcpyAsync(out, dout, shots * 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "shots readback");
+                break;
+            }
+        }
+    } while (0);
+    cudaFreeAsync(scratch, s->stream);
+    if (rc == SIM_OK && !out_on_device) QSIM_CUDA(cudaStreamSynchronize(s->stream));
+    return rc;
+}
+
+}  // namespace qsim

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of the C ABI in include/qsim_gb300.h.
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  Importing this module loads ``_lib/libqsim_gb300.so`` and raises
+ImportError when it has not been built (``python -m
+paper_1805_00988_gb300.build``); there is no CPU fallback.
+
+The module-level functions keep the C names (``sim_create``,
+``sim_apply_gate`` ...).  ``State`` is a small convenience wrapper whose state
+buffer is a PyTorch CUDA tensor (PyTorch supplies device memory and the
+stream; the library never sees a torch type).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libqsim_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError("libqsim_gb300.so is not built (run python -m paper_1805_00988_gb300.build); "
+                      "the simulator has no CPU fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+SIM_C64, SIM_C128 = 0, 1
+SIM_F32, SIM_F64 = 0, 1
+SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ETIMEOUT, SIM_EUNSUPPORTED = range(6)
+SIM_PLAN_PER_GATE, SIM_PLAN_STAGED, SIM_PLAN_FUSED, SIM_PLAN_LEARNED = range(4)
+PLANS = {"per_gate": 0, "staged": 1, "fused": 2, "learned": 3}
+
+GATE_KINDS = {"u": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8,
+              "rx": 9, "ry": 10, "rz": 11, "p": 12, "u3": 13, "swap": 14}
+
+# struct sim_gate (112 bytes)
+SIM_GATE_DTYPE = np.dtype([
+    ("kind", "<i4"), ("target", "<i4"), ("target2", "<i4"), ("n_controls", "<i4"),
+    ("controls", "<i4", (2,)), ("params", "<f8", (3,)), ("matrix", "<f8", (8,)),
+])
+assert SIM_GATE_DTYPE.itemsize == 112
+
+
+class sim_plan_opts(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_int32), ("fuse_k", ctypes.c_int32),
+                ("tile_qubits", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+
+class SimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("status %d: %s" % (status, msg))
+        self.status = status
+
+
+P = ctypes.c_void_p
+_i32, _u64, _sz = ctypes.c_int, ctypes.c_uint64, ctypes.c_size_t
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("sim_create", [_i32, _i32, P, ctypes.POINTER(P)])
+_sig("sim_create_from_buffer", [_i32, _i32, P, _sz, P, ctypes.POINTER(P)])
+_sig("sim_destroy", [P])
+_sig("sim_state_info", [P, P, P, P, P])
+_sig("sim_synchronize", [P])
+_sig("sim_set_basis_state", [P, _u64])
+_sig("sim_load_state", [P, P, _i32])
+_sig("sim_copy_state", [P, P, _i32])
+_sig("sim_apply_gate", [P, P, _i32, P, _i32])
+_sig("sim_apply_circuit", [P, P, _sz, P])
+_sig("sim_probabilities", [P, P, _i32])
+_sig("sim_norm", [P, P])
+_sig("sim_measure", [P, _i32, _u64, _u64, P, P])
+_sig("sim_sample", [P, _u64, _u64, P, _i32])
+_sig("sim_expect_z_sum", [P, P])
+_sig("sim_profile_enable", [P, _i32])
+_sig("sim_profile_read", [P, _i32, P, P, P, _i32])
+_sig("sim_launch_count", [P, P])
+_sig("sim_kernel_class_name", [_i32], ctypes.c_char_p)
+_sig("sim_num_kernel_classes", [], _i32)
+_sig("sim_last_error", [], ctypes.c_char_p)
+_sig("sim_version", [], ctypes.c_char_p)
+
+
+def last_error() -> str:
+    return _lib.sim_last_error().decode()
+
+
+def check(status: int):
+    if status != SIM_OK:
+        raise SimError(status, last_error())
+
+
+def lib_handle():
+    """The loaded ctypes library (for callers that need a raw entry point)."""
+    return _lib
+
+
+# ---------------------------------------------------------------- raw entry points
+def sim_create(n: int, dtype: int = SIM_C64, stream: int = 0) -> int:
+    h = P()
+    check(_lib.sim_create(n, dtype, P(stream or None), ctypes.byref(h)))
+    return h.value
+
+
+def sim_create_from_buffer(n: int, dtype: int, dev_ptr: int, nbytes: int, stream: int = 0) -> int:
+    h = P()
+    check(_lib.sim_create_from_buffer(n, dtype, P(dev_ptr), nbytes, P(stream or None), ctypes.byref(h)))
+    return h.value
+
+
+def sim_destroy(h: int):
+    check(_lib.sim_destroy(P(h)))
+
+
+def sim_synchronize(h: int):
+    check(_lib.sim_synchronize(P(h)))
+
+
+def sim_set_basis_state(h: int, j: int):
+    check(_lib.sim_set_basis_state(P(h), j))
+
+
+def sim_load_state(h: int, src, src_is_host: bool = True):
+    check(_lib.sim_load_state(P(h), P(src), int(src_is_host)))
+
+
+def sim_copy_state(h: int, dst, dst_is_host: bool = True):
+    check(_lib.sim_copy_state(P(h), P(dst), int(dst_is_host)))
+
+
+def sim_apply_gate(h: int, U, target: int, controls=()):
+    u = np.zeros(8, dtype=np.float64)
+    m = np.asarray(U, dtype=np.complex128).reshape(2, 2)
+    u[0::2] = m.reshape(-1).real
+    u[1::2] = m.reshape(-1).imag
+    c = (ctypes.c_int * 2)(*(list(controls) + [-1, -1])[:2])
+    check(_lib.sim_apply_gate(P(h), u.ctypes.data_as(P), target, c, len(controls)))
+
+
+def to_sim_gates(gates: np.ndarray) -> np.ndarray:
+    """Convert a circuits.GATE_DTYPE array into struct sim_gate records."""
+    out = np.zeros(len(gates), dtype=SIM_GATE_DTYPE)
+    if len(gates) == 0:
+        return out
+    names = gates["name"]
+    kinds = np.zeros(len(gates), dtype=np.int32)
+    for nm, code in GATE_KINDS.items():
+        kinds[names == nm] = code
+    known = np.isin(names, list(GATE_KINDS))
+    if not np.all(known):
+        raise ValueError("unknown gate name %r" % names[~known][0])
+    out["kind"] = kinds
+    out["target"] = gates["target"]
+    out["target2"] = gates["target2"]
+    out["n_controls"] = gates["nctrl"]
+    out["controls"] = gates["ctrl"]
+    out["params"] = gates["params"]
+    out["matrix"] = gates["mat"]
+    return out
+
+
+def plan_opts(plan="per_gate", fuse_k=0, tile_qubits=0, flags=0) -> sim_plan_opts:
+    p = PLANS[plan] if isinstance(plan, str) else int(plan)
+    return sim_plan_opts(p, fuse_k, tile_qubits, flags)
+
+
+def sim_apply_circuit(h: int, sim_gates: np.ndarray, opts: sim_plan_opts = None):
+    g = np.ascontiguousarray(sim_gates, dtype=SIM_GATE_DTYPE)
+    check(_lib.sim_apply_circuit(P(h), g.ctypes.data_as(P), len(g),
+                                 ctypes.byref(opts) if opts is not None else None))
+
+
+def sim_probabilities(h: int, dev_out: int, out_real: int = SIM_F64):
+    check(_lib.sim_probabilities(P(h), P(dev_out), out_real))
+
+
+def sim_norm(h: int) -> float:
+    r = ctypes.c_double()
+    check(_lib.sim_norm(P(h), ctypes.byref(r)))
+    return r.value
+
+
+def sim_expect_z_sum(h: int) -> float:
+    r = ctypes.c_double()
+    check(_lib.sim_expect_z_sum(P(h), ctypes.byref(r)))
+    return r.value
+
+
+def sim_measure(h: int, qubit: int, seed: int, draw: int = 0):
+    m = ctypes.c_int()
+    p = ctypes.c_double()
+    check(_lib.sim_measure(P(h), qubit, seed, draw, ctypes.byref(m), ctypes.byref(p)))
+    return m.value, p.value
+
+
+def sim_sample(h: int, shots: int, seed: int, out=None, out_on_device: bool = False):
+    """Host output: returns a numpy uint64 array (or fills ``out``).  Device
+    output: ``out`` is a device pointer (int) to shots uint64."""
+    if out_on_device:
+        check(_lib.sim_sample(P(h), shots, seed, P(out), 1))
+        return out
+    arr = np.empty(shots, dtype=np.uint64) if out is None else out
+    check(_lib.sim_sample(P(h), shots, seed, arr.ctypes.data_as(P), 0))
+    return arr
+
+
+def sim_profile_enable(h: int, on: bool = True):
+    check(_lib.sim_profile_enable(P(h), int(on)))
+
+
+def sim_profile_read(h: int, reset: bool = True):
+    k = _lib.sim_num_kernel_classes()
+    launches = (ctypes.c_uint64 * k)()
+    ms = (ctypes.c_double * k)()
+    nbytes = (ctypes.c_double * k)()
+    check(_lib.sim_profile_read(P(h), k, launches, ms, nbytes, int(reset)))
+    return {_lib.sim_kernel_class_name(i).decode(): (int(launches[i]), float(ms[i]), float(nbytes[i]))
+            for i in range(k) if launches[i]}
+
+
+def sim_launch_count(h: int) -> int:
+    r = ctypes.c_uint64()
+    check(_lib.sim_launch_count(P(h), ctypes.byref(r)))
+    return r.value
+
+
+def sim_version() -> str:
+    return _lib.sim_version().decode()
+
+
+# ---------------------------------------------------------------- convenience wrapper
+class State:
+    """An n-qubit register whose amplitudes live in a PyTorch CUDA tensor.
+
+    dtype: "c64" (complex64) or "c128" (complex128).  Starts in |0...0>.
+    """
+
+    def __init__(self, n: int, dtype: str = "c64", device=None, torch_memory: bool = True):
+        import torch
+        self.n = n
+        self.dtype = SIM_C128 if dtype in ("c128", SIM_C128, np.complex128) else SIM_C64
+        self._torch = torch
+        dev = torch.device(device or "cuda")
+        self.stream = torch.cuda.current_stream(dev)
+        tdt = torch.complex128 if self.dtype == SIM_C128 else torch.complex64
+        if torch_memory:
+            self.tensor = torch.empty(2 ** n, dtype=tdt, device=dev)
+            self.h = sim_create_from_buffer(n, self.dtype, self.tensor.data_ptr(),
+                                            self.tensor.numel() * self.tensor.element_size(),
+                                            self.stream.cuda_stream)
+            sim_set_basis_state(self.h, 0)
+        else:
+            self.tensor = None
+            self.h = sim_create(n, self.dtype, self.stream.cuda_stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def np_dtype(self):
+        return np.complex128 if self.dtype == SIM_C128 else np.complex64
+
+    def set_basis(self, j: int = 0):
+        sim_set_basis_state(self.h, j)
+
+    def load(self, psi: np.ndarray):
+        a = np.ascontiguousarray(psi, dtype=self.np_dtype)
+        assert a.size == 2 ** self.n
+        sim_load_state(self.h, a.ctypes.data, True)
+
+    def state(self) -> np.ndarray:
+        out = np.empty(2 ** self.n, dtype=self.np_dtype)
+        sim_copy_state(self.h, out.ctypes.data, True)
+        return out
+
+    def apply(self, gates: np.ndarray, plan="per_gate", **kw):
+        sim_apply_circuit(self.h, to_sim_gates(gates), plan_opts(plan, **kw))
+
+    def apply_gate(self, U, target, controls=()):
+        sim_apply_gate(self.h, U, target, controls)
+
+    def probabilities(self, f64: bool = True):
+        t = self._torch.empty(2 ** self.n, dtype=self._torch.float64 if f64 else self._torch.float32,
+                              device=self.tensor.device if self.tensor is not None else "cuda")
+        sim_probabilities(self.h, t.data_ptr(), SIM_F64 if f64 else SIM_F32)
+        sim_synchronize(self.h)
+        return t.cpu().numpy()
+
+    def norm2(self) -> float:
+        return sim_norm(self.h)
+
+    def expect_z_sum(self) -> float:
+        return sim_expect_z_sum(self.h)
+
+    def measure(self, qubit: int, seed: int, draw: int = 0):
+        return sim_measure(self.h, qubit, seed, draw)
+
+    def sample(self, shots: int, seed: int) -> np.ndarray:
+        return sim_sample(self.h, shots, seed)
+
+    def synchronize(self):
+        sim_synchronize(self.h)

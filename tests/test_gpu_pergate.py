@@ -1,0 +1,244 @@
+"""GPU parity of the per-gate path, the probability / norm / <Z> reductions,
+measurement and sampling against the FP64 oracle, through the C ABI.
+
+Tolerances (derived from the arithmetic, see the precision section of the
+design notes):
+  complex128: |psi_gpu - psi_ref| <= 1e-11 * max|psi_ref| element-wise and
+              infidelity <= 1e-12;
+  complex64 : |psi_gpu - psi_ref| <= 1e-5 * max|psi_ref| element-wise and
+              infidelity <= 1e-6;
+  permutations (X, CNOT, Toffoli, SWAP and their controlled forms): bit-exact.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1805_00988_gb300 import circuits as C
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"c64": (1e-5, 1e-6), "c128": (1e-11, 1e-12)}
+
+
+@pytest.fixture(scope="module")
+def sim():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1805_00988_gb300 import build
+    build.build()
+    from paper_1805_00988_gb300 import sim as S
+    return S
+
+
+def check_state(got, ref, dt):
+    rel, inf_tol = TOL[dt]
+    got = got.astype(np.complex128)
+    scale = np.max(np.abs(ref))
+    err = np.max(np.abs(got - ref))
+    assert err <= rel * scale, (dt, err, scale)
+    import oracle
+    assert oracle.infidelity(ref, got) <= inf_tol
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 6, 9, 13])
+def test_every_kind_and_placement(sim, orc, dt, n):
+    """Every gate kind on every target, with 0..2 controls, on a random state."""
+    rng = np.random.default_rng(1000 + n)
+    psi = C.random_state(n, seed=n, dtype=np.complex128)
+    st = sim.State(n, dt)
+    for name in C.GATE_NAMES:
+        if name == "swap" and n < 2:
+            continue
+        for t in range(n):
+            others = [q for q in range(n) if q != t]
+            rng.shuffle(others)
+            used = 0
+            t2 = -1
+            if name == "swap":
+                t2 = others[0]
+                used = 1
+            nc = int(rng.integers(0, min(2, len(others) - used) + 1))
+            ctrls = tuple(int(c) for c in others[used:used + nc])
+            g = C.gate(name, t, controls=ctrls, params=tuple(rng.uniform(0, 2 * math.pi, 3)),
+                       mat=C.haar_unitary_2x2(rng), target2=t2)
+            st.load(psi)
+            st.apply(g)
+            # the oracle starts from exactly the values the GPU held
+            start = psi.astype(st.np_dtype).astype(np.complex128)
+            check_state(st.state(), orc.apply_circuit(start, g), dt)
+    st.close()
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("name,nc", [("x", 0), ("x", 1), ("x", 2), ("swap", 0), ("swap", 1), ("swap", 2)])
+def test_permutations_bit_exact(sim, orc, dt, name, nc):
+    n = 10
+    rng = np.random.default_rng(7)
+    st = sim.State(n, dt)
+    psi = C.random_state(n, seed=3).astype(st.np_dtype)
+    for _ in range(12):
+        qs = [int(v) for v in rng.permutation(n)]
+        if name == "x":
+            g = C.gate("x", qs[0], controls=qs[1:1 + nc])
+        else:
+            g = C.gate("swap", qs[0], target2=qs[1], controls=qs[2:2 + nc])
+        st.load(psi)
+        st.apply(g)
+        ref = orc.apply_circuit(psi.astype(np.complex128), g).astype(st.np_dtype)
+        assert np.array_equal(st.state().view(np.uint8), ref.view(np.uint8))
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n", [14, 17, 20])
+def test_random_circuits(sim, orc, dt, n):
+    g = C.random_gates(n, 150, seed=n)
+    st = sim.State(n, dt)
+    st.apply(g)
+    check_state(st.state(), orc.apply_circuit(orc.basis_state(n, 0), g), dt)
+    st.close()
+
+
+def test_u3_cnot_ladder_14q_c128(sim, orc):
+    """20 layers of U3 on 14 qubits + CNOT ladders, complex128, full state."""
+    g = C.u3_cnot_ladder(14, 20, seed=1234)
+    assert len(g) == 540
+    st = sim.State(14, "c128")
+    st.apply(g)
+    ref = orc.apply_circuit(orc.basis_state(14, 0), g)
+    got = st.state()
+    check_state(got, ref, "c128")
+    np.testing.assert_allclose(st.probabilities(), orc.probabilities(ref), atol=1e-14)
+    st.close()
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_qft_28q_closed_form(sim, dt):
+    """Textbook QFT on 28 qubits from a seeded random basis state, per-gate
+    kernels; sampled amplitudes against e^{2 pi i j k / N} / sqrt(N)."""
+    n = 28
+    N = 2 ** n
+    j = C.random_basis_index(n, seed=1234)
+    g = C.qft(n)
+    assert len(g) == n * (n + 1) // 2 + n // 2
+    st = sim.State(n, dt)
+    st.set_basis(j)
+    st.apply(g, plan="per_gate")
+    psi = st.tensor
+    rng = np.random.default_rng(5)
+    ks = np.concatenate([[0, 1, N - 1], rng.integers(0, N, 4093)])
+    got = psi[ks].cpu().numpy().astype(np.complex128)
+    ref = np.exp(2j * np.pi * ((j * ks) % N) / N) / math.sqrt(N)
+    rel = 2e-5 if dt == "c64" else 1e-11
+    assert np.max(np.abs(got - ref)) <= rel / math.sqrt(N)
+    assert abs(st.norm2() - 1.0) < (1e-5 if dt == "c64" else 1e-12)
+    st.close()
+
+
+def test_haar_cz_30q_mirror(sim):
+    """The 30-qubit depth-20 random circuit followed by its inverse returns
+    |0...0> (complex64, per-gate launches as timed)."""
+    n = 30
+    g = C.haar_cz(n, 20, seed=1234)
+    st = sim.State(n, "c64")
+    st.apply(g, plan="per_gate")
+    nrm = st.norm2()
+    assert abs(nrm - 1.0) < 1e-4
+    st.apply(C.inverse(g), plan="per_gate")
+    a0 = complex(st.tensor[0].item())
+    assert abs(abs(a0) ** 2 - 1.0) < 1e-4
+    st.close()
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_reductions_and_probabilities(sim, orc, dt):
+    n = 16
+    g = C.random_gates(n, 60, seed=2)
+    st = sim.State(n, dt)
+    st.apply(g)
+    got = st.state().astype(np.complex128)
+    # reductions are checked against the oracle on exactly the GPU's state
+    tol = 1e-12
+    assert abs(st.norm2() - orc.norm2(got)) < tol
+    assert abs(st.expect_z_sum() - orc.expect_z_sum(got)) < 1e-11
+    np.testing.assert_allclose(st.probabilities(True), orc.probabilities(got), rtol=1e-15, atol=1e-300)
+    p32 = st.probabilities(False)
+    np.testing.assert_allclose(p32, orc.probabilities(got), rtol=2e-6, atol=1e-30)
+    st.close()
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+def test_measure_matches_oracle(sim, orc, dt):
+    n = 12
+    g = C.random_gates(n, 80, seed=4)
+    st = sim.State(n, dt)
+    st.apply(g)
+    for draw, q in enumerate([0, 5, 11, 3]):
+        before = st.state().astype(np.complex128)
+        m, p = st.measure(q, seed=99, draw=draw)
+        m_ref, p_ref, post = orc.measure(before, q, seed=99, draw=draw)
+        assert m == m_ref
+        assert abs(p - p_ref) < 1e-12
+        check_state(st.state(), post, dt)
+    st.close()
+
+
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n", [1, 3, 12, 13, 15, 18])
+def test_sample_matches_oracle(sim, orc, dt, n):
+    """Same state (copied from the GPU), same u_s: identical indices except
+    shots whose target lies within 1e-12 of a prefix boundary."""
+    g = C.random_gates(n, 40, seed=n + 50)
+    st = sim.State(n, dt)
+    st.apply(g)
+    psi = st.state().astype(np.complex128)
+    shots = 20000
+    got = st.sample(shots, seed=321)
+    ref = orc.sample(psi, shots, seed=321)
+    diff = np.nonzero(got != ref)[0]
+    if len(diff):
+        p = np.abs(psi) ** 2
+        c = np.cumsum(p)
+        tot = c[-1]
+        for s in diff:
+            t = orc.uniform(321, int(s)) * tot
+            near = np.min(np.abs(c - t))
+            assert near <= 1e-12 * tot, (s, got[s], ref[s])
+    assert len(diff) <= 2
+    st.close()
+
+
+def test_bernstein_vazirani_worked_example(sim):
+    """App. C: n = 14, a = 101 -> every one of 1000 samples is 101."""
+    st = sim.State(14, "c64")
+    st.apply(C.bernstein_vazirani(14, 101))
+    s = st.sample(1000, seed=2018)
+    assert np.all(s == 101)
+    st.close()
+
+
+def test_errors_are_status_codes(sim):
+    st = sim.State(5, "c64")
+    for bad in (C.gate("x", 5), C.gate("x", 1, controls=(1,)), C.gate("x", 0, controls=(2, 2)),
+                C.gate("swap", 2, target2=2), C.gate("h", -1)):
+        with pytest.raises(sim.SimError) as e:
+            st.apply(bad)
+        assert e.value.status == sim.SIM_EINVAL
+    with pytest.raises(sim.SimError):
+        st.set_basis(32)
+    with pytest.raises(sim.SimError):
+        st.measure(7, seed=1)
+    st.close()
+    with pytest.raises(sim.SimError) as e:
+        sim.sim_create(34, sim.SIM_C128)     # 256 GiB does not fit
+    assert e.value.status in (sim.SIM_ENOMEM, sim.SIM_EINVAL)
+
+
+def test_launches_are_counted(sim):
+    st = sim.State(10, "c64")
+    c0 = sim.sim_launch_count(st.h)
+    st.apply(C.random_gates(10, 25, seed=1))
+    assert sim.sim_launch_count(st.h) - c0 >= 20
+    st.close()
