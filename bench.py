@@ -364,13 +364,13 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plan", default="per_gate")
+    ap.add_argument("--plan", default="staged")
     ap.add_argument("--fuse-k", type=int, default=5)
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
     ap.add_argument("--depth", type=int, default=DEPTH)
     ap.add_argument("--shots", type=int, default=SHOTS)
     ap.add_argument("--no-variants", dest="variants", action="store_false")
-    ap.add_argument("--variant-plans", default="per_gate")
+    ap.add_argument("--variant-plans", default="per_gate,staged")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

@@ -95,7 +95,8 @@ typedef struct sim_plan_opts {
  * sim_create: allocate a 2^n state on the current CUDA device and set it to
  *   |0...0> (§2.1).  n in [1, 34]; the state must fit in free device memory
  *   (SIM_ENOMEM otherwise).  stream: a cudaStream_t (NULL = the handle
- *   creates its own non-blocking stream).
+ *   creates its own non-blocking stream; pass cudaStreamLegacy to work on
+ *   the legacy default stream).
  * sim_create_from_buffer: wrap caller-owned device memory of at least
  *   2^n * sizeof(amplitude) bytes, 16-byte aligned; its contents are kept.
  * sim_destroy: free what the handle owns (not a wrapped buffer). */
@@ -142,6 +143,18 @@ int sim_norm(sim_t s, double *out);
 int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob);
 int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
 int sim_expect_z_sum(sim_t s, double *out);
+
+/* ---- plan introspection (host only, no GPU needed) ---------------------------
+ * sim_plan_describe: build the SIM_PLAN_STAGED schedule of a circuit for an
+ *   n-qubit register of the given dtype without running it.  Outputs (any may
+ *   be NULL): the number of tile passes, of encoded ops, of register-layout
+ *   changes, and the order in which the gates are applied (circuit indices;
+ *   a SWAP appears three times, lowered to three CNOT-type moves; identity
+ *   gates are dropped) -- up to order_cap entries, the full length in
+ *   *order_len.  SIM_EINVAL if no tile fits (n below 11) or a gate is invalid. */
+int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts,
+                      int64_t *passes, int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap,
+                      size_t *order_len);
 
 /* ---- instrumentation --------------------------------------------------------
  * sim_profile_enable: when on, every kernel launch of the handle is bracketed

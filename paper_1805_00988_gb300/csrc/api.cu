@@ -348,6 +348,23 @@ int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on
     return run_sample(s, shots, seed, out, out_on_device);
 }
 
+int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts,
+                      int64_t *passes, int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap,
+                      size_t *order_len)
+{
+    set_error("");
+    if (n < 1 || n > 34) return fail(SIM_EINVAL, "sim_plan_describe: n must be in [1, 34]");
+    if (n_gates && !gates) return fail(SIM_EINVAL, "sim_plan_describe: gates is NULL");
+    for (size_t k = 0; k < n_gates; ++k) {
+        std::string why;
+        if (validate_gate(n, gates[k], &why)) return fail(SIM_EINVAL, "sim_plan_describe: " + why);
+    }
+    const int plan = opts ? opts->plan : SIM_PLAN_PER_GATE;
+    if (plan != SIM_PLAN_STAGED) return fail(SIM_EUNSUPPORTED, "sim_plan_describe: only the staged plan");
+    return describe_staged(n, dtype, gates, n_gates, opts->tile_qubits, passes, ops, layout_changes, order,
+                           order_cap, order_len);
+}
+
 int sim_profile_enable(sim_t s, int on)
 {
     if (int rc = check_handle(s)) return rc;

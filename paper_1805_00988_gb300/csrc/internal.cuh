@@ -128,6 +128,8 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
 // ---------------------------------------------------------------- staged / fused plans
 int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
 int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
+int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,
+                    int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len);
 
 // host-side SplitMix64 draw (Steele, Lea & Flood 2014)
 uint64_t splitmix64_host(uint64_t x);

@@ -3,12 +3,6 @@
 
 namespace qsim {
 
-int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
-{
-    (void)s; (void)gates; (void)n_gates; (void)o;
-    return fail(SIM_EUNSUPPORTED, "staged plan not built yet");
-}
-
 int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
 {
     (void)s; (void)gates; (void)n_gates; (void)o;

@@ -1,0 +1,653 @@
+// staged.cu -- multi-gate tile passes: one HBM read + write of the state
+// applies a whole run of gates.
+//
+// Algorithm 1 (§2.3) touches the full state once per gate.  Consecutive gates
+// whose non-diagonal qubits all lie in one qubit set Q can instead be applied
+// tile by tile: a tile is the 2^M amplitudes that share the bits of every
+// qubit outside Q, so a gate on a qubit of Q only pairs amplitudes inside one
+// tile.  Q always holds the low qubits 0..4 (so a tile is made of contiguous
+// 32-amplitude chunks) plus M - 5 further qubits chosen per pass.  Diagonal
+// gates (Z, S, T, P, RZ, CZ, CP, ...) and controls never need their qubit in
+// Q: outside Q the bit is constant over the tile.
+//
+// Inside a CTA the tile lives in registers: with 256 threads each thread holds
+// 2^(M-8) amplitudes.  A register layout assigns the tile's local bits to
+// register bits and thread bits; a gate whose target is a register bit is
+// applied by each thread alone.  Layouts change through shared memory (one
+// store + one load of the tile, XOR-swizzled so every layout is free of bank
+// conflicts).  The host planner (below) forms the passes, orders the gates of
+// a pass to need few layout changes, and encodes each gate as register /
+// thread / tile masks for the layout current at that point.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kLow = 5;          // qubits 0..4 are local bits 0..4 of every tile
+constexpr int kThr = 256;        // threads per CTA
+constexpr int kThrBits = 8;
+
+enum StKind { SK_LAYOUT = 0, SK_DENSE, SK_ANTI, SK_XPERM, SK_DIAG, SK_PHASE, SK_NEG };
+
+template <typename R>
+struct __align__(16) StOp {
+    int32_t kind;      // StKind
+    int32_t arg;       // exchange ops: register bit of the target; SK_LAYOUT: new layout
+    uint32_t reg_c;    // register bits that must be 1
+    uint32_t thr_c;    // thread bits that must be 1
+    uint64_t out_c;    // global bits (outside the tile) that must be 1
+    uint32_t reg_t;    // diagonal ops: where the target bit is (exactly one of the three is set)
+    uint32_t thr_t;
+    uint64_t out_t;
+    R m[8];            // A, B, C, D
+};
+
+// ---------------------------------------------------------------- layouts
+// VEC = 2 for complex64 (the I/O layout keeps local bit 0 in registers so a
+// thread loads two neighbouring amplitudes as one 16-byte vector), 1 for
+// complex128.  Layout 0 is the I/O layout; layouts 1.. put windows of RB
+// consecutive local bits into registers.
+__host__ __device__ constexpr int n_layouts(int M, int RB) { return 1 + (M - RB + RB - 1) / RB; }
+
+__host__ __device__ constexpr int reg_local(int M, int RB, int VEC, int l, int j)
+{
+    if (l == 0) return (VEC == 2) ? (j == 0 ? 0 : M - RB + j) : (M - RB + j);
+    int s = (VEC == 2 ? 1 : 0) + RB * (l - 1);
+    if (s > M - RB) s = M - RB;
+    return s + j;
+}
+
+__host__ __device__ constexpr bool is_reg(int M, int RB, int VEC, int l, int b)
+{
+    for (int j = 0; j < RB; ++j)
+        if (reg_local(M, RB, VEC, l, j) == b) return true;
+    return false;
+}
+
+__host__ __device__ constexpr int thr_local(int M, int RB, int VEC, int l, int i)
+{
+    int c = 0;
+    for (int b = 0; b < M; ++b)
+        if (!is_reg(M, RB, VEC, l, b)) {
+            if (c == i) return b;
+            ++c;
+        }
+    return -1;
+}
+
+__host__ __device__ constexpr int reg_part(int M, int RB, int VEC, int l, int k)
+{
+    int x = 0;
+    for (int j = 0; j < RB; ++j)
+        if ((k >> j) & 1) x |= 1 << reg_local(M, RB, VEC, l, j);
+    return x;
+}
+
+// shared-memory slot of local index x (bank-conflict-free for every layout)
+template <int RB, int VEC>
+__device__ __forceinline__ int swz(int x)
+{
+    return (VEC == 2) ? (x ^ (((x >> (RB + 1)) & 7) << 1)) : (x ^ ((x >> RB) & 7));
+}
+
+struct TileGeom {
+    int n_outer;
+    int outer_pos[40];   // global qubit of outer bit i (ascending)
+    int hpos[16];        // global qubit of local bit kLow + i
+};
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+template <typename R>
+struct CoefS { R ar, ai, br, bi, cr, ci, dr, di; };
+
+template <int KIND, typename R>
+__device__ __forceinline__ void xupd(R &lr, R &li, R &hr, R &hi, const CoefS<R> &c)
+{
+    if (KIND == SK_DENSE) {
+        const R nlr = c.ar * lr - c.ai * li + (c.br * hr - c.bi * hi);
+        const R nli = c.ar * li + c.ai * lr + (c.br * hi + c.bi * hr);
+        const R nhr = c.cr * lr - c.ci * li + (c.dr * hr - c.di * hi);
+        const R nhi = c.cr * li + c.ci * lr + (c.dr * hi + c.di * hr);
+        lr = nlr; li = nli; hr = nhr; hi = nhi;
+    } else if (KIND == SK_ANTI) {
+        const R nlr = c.br * hr - c.bi * hi, nli = c.br * hi + c.bi * hr;
+        const R nhr = c.cr * lr - c.ci * li, nhi = c.cr * li + c.ci * lr;
+        lr = nlr; li = nli; hr = nhr; hi = nhi;
+    } else {  // SK_XPERM: exact exchange
+        R t = lr; lr = hr; hr = t;
+        t = li; li = hi; hi = t;
+    }
+}
+
+template <int J, int KIND, int RB, typename R>
+__device__ __forceinline__ void xop(R *vr, R *vi, uint32_t reg_c, bool tok, const CoefS<R> &c)
+{
+    if constexpr (J < RB) {
+#pragma unroll
+        for (int k = 0; k < (1 << RB); ++k) {
+            if (k & (1 << J)) continue;
+            const int k1 = k | (1 << J);
+            if (tok && (((uint32_t)k & reg_c) == reg_c)) xupd<KIND, R>(vr[k], vi[k], vr[k1], vi[k1], c);
+        }
+    }
+}
+
+template <int KIND, int RB, typename R>
+__device__ __forceinline__ void xdispatch(int j, R *vr, R *vi, uint32_t reg_c, bool tok, const CoefS<R> &c)
+{
+    switch (j) {
+    case 0: xop<0, KIND, RB>(vr, vi, reg_c, tok, c); break;
+    case 1: xop<1, KIND, RB>(vr, vi, reg_c, tok, c); break;
+    case 2: xop<2, KIND, RB>(vr, vi, reg_c, tok, c); break;
+    case 3: xop<3, KIND, RB>(vr, vi, reg_c, tok, c); break;
+    case 4: xop<4, KIND, RB>(vr, vi, reg_c, tok, c); break;
+    case 5: xop<5, KIND, RB>(vr, vi, reg_c, tok, c); break;
+    default: break;
+    }
+}
+
+template <int M, int RB, int VEC, int L, typename R>
+__device__ __forceinline__ void store_layout(const R *vr, const R *vi, R *sm, int tid)
+{
+    if constexpr (L < n_layouts(M, RB)) {
+        int tp = 0;
+#pragma unroll
+        for (int i = 0; i < kThrBits; ++i) tp |= ((tid >> i) & 1) << thr_local(M, RB, VEC, L, i);
+        if constexpr (VEC == 2 && L == 0) {
+#pragma unroll
+            for (int k = 0; k < (1 << RB); k += 2) {
+                const int p = swz<RB, VEC>(tp | reg_part(M, RB, VEC, L, k));
+                *reinterpret_cast<float4 *>(sm + 2 * p) = make_float4(vr[k], vi[k], vr[k + 1], vi[k + 1]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << RB); ++k) {
+                const int p = swz<RB, VEC>(tp | reg_part(M, RB, VEC, L, k));
+                typename V2<R>::T v;
+                v.x = vr[k];
+                v.y = vi[k];
+                *reinterpret_cast<typename V2<R>::T *>(sm + 2 * p) = v;
+            }
+        }
+    }
+}
+
+template <int M, int RB, int VEC, int L, typename R>
+__device__ __forceinline__ void load_layout(R *vr, R *vi, const R *sm, int tid)
+{
+    if constexpr (L < n_layouts(M, RB)) {
+        int tp = 0;
+#pragma unroll
+        for (int i = 0; i < kThrBits; ++i) tp |= ((tid >> i) & 1) << thr_local(M, RB, VEC, L, i);
+        if constexpr (VEC == 2 && L == 0) {
+#pragma unroll
+            for (int k = 0; k < (1 << RB); k += 2) {
+                const int p = swz<RB, VEC>(tp | reg_part(M, RB, VEC, L, k));
+                const float4 v = *reinterpret_cast<const float4 *>(sm + 2 * p);
+                vr[k] = v.x; vi[k] = v.y; vr[k + 1] = v.z; vi[k + 1] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < (1 << RB); ++k) {
+                const int p = swz<RB, VEC>(tp | reg_part(M, RB, VEC, L, k));
+                const typename V2<R>::T v = *reinterpret_cast<const typename V2<R>::T *>(sm + 2 * p);
+                vr[k] = v.x;
+                vi[k] = v.y;
+            }
+        }
+    }
+}
+
+template <int M, int RB, int VEC, typename R>
+__device__ __forceinline__ void relayout(int from, int to, R *vr, R *vi, R *sm, int tid)
+{
+    __syncthreads();
+    switch (from) {
+    case 0: store_layout<M, RB, VEC, 0>(vr, vi, sm, tid); break;
+    case 1: store_layout<M, RB, VEC, 1>(vr, vi, sm, tid); break;
+    case 2: store_layout<M, RB, VEC, 2>(vr, vi, sm, tid); break;
+    case 3: store_layout<M, RB, VEC, 3>(vr, vi, sm, tid); break;
+    default: break;
+    }
+    __syncthreads();
+    switch (to) {
+    case 0: load_layout<M, RB, VEC, 0>(vr, vi, sm, tid); break;
+    case 1: load_layout<M, RB, VEC, 1>(vr, vi, sm, tid); break;
+    case 2: load_layout<M, RB, VEC, 2>(vr, vi, sm, tid); break;
+    case 3: load_layout<M, RB, VEC, 3>(vr, vi, sm, tid); break;
+    default: break;
+    }
+}
+
+template <typename R, int M>
+__global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
+                                                   TileGeom geo)
+{
+    constexpr int VEC = (sizeof(R) == 4) ? 2 : 1;
+    constexpr int RB = M - kThrBits;
+    constexpr int RA = 1 << RB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R *sm = reinterpret_cast<R *>(smem_raw);
+    const int tid = threadIdx.x;
+
+    const uint64_t tile = (uint64_t)blockIdx.x;
+    uint64_t base = 0;
+    for (int i = 0; i < geo.n_outer; ++i) base |= ((tile >> i) & 1ull) << geo.outer_pos[i];
+
+    // global offsets in the I/O layout
+    uint64_t toff = base;
+#pragma unroll
+    for (int i = 0; i < kThrBits; ++i) {
+        const int b = thr_local(M, RB, VEC, 0, i);
+        const uint64_t g = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
+        if ((tid >> i) & 1) toff |= g;
+    }
+    uint64_t roff[RB];
+#pragma unroll
+    for (int j = 0; j < RB; ++j) {
+        const int b = reg_local(M, RB, VEC, 0, j);
+        roff[j] = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
+    }
+
+    R vr[RA], vi[RA];
+    if constexpr (VEC == 2) {
+#pragma unroll
+        for (int k = 0; k < RA; k += 2) {
+            uint64_t g = toff;
+#pragma unroll
+            for (int j = 1; j < RB; ++j)
+                if ((k >> j) & 1) g |= roff[j];
+            const float4 v = *reinterpret_cast<const float4 *>(st + 2 * g);
+            vr[k] = v.x; vi[k] = v.y; vr[k + 1] = v.z; vi[k + 1] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < RA; ++k) {
+            uint64_t g = toff;
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+                if ((k >> j) & 1) g |= roff[j];
+            const double2 v = *reinterpret_cast<const double2 *>(st + 2 * g);
+            vr[k] = (R)v.x;
+            vi[k] = (R)v.y;
+        }
+    }
+
+    int layout = 0;
+    for (int p = 0; p < nops; ++p) {
+        const int kind = ops[p].kind;
+        const int arg = ops[p].arg;
+        if (kind == SK_LAYOUT) {
+            relayout<M, RB, VEC>(layout, arg, vr, vi, sm, tid);
+            layout = arg;
+            continue;
+        }
+        const uint32_t reg_c = ops[p].reg_c;
+        const bool tok = ((tid & ops[p].thr_c) == ops[p].thr_c) && ((base & ops[p].out_c) == ops[p].out_c);
+        CoefS<R> c;
+        c.ar = ops[p].m[0]; c.ai = ops[p].m[1]; c.br = ops[p].m[2]; c.bi = ops[p].m[3];
+        c.cr = ops[p].m[4]; c.ci = ops[p].m[5]; c.dr = ops[p].m[6]; c.di = ops[p].m[7];
+        if (kind == SK_DENSE) {
+            xdispatch<SK_DENSE, RB>(arg, vr, vi, reg_c, tok, c);
+        } else if (kind == SK_ANTI) {
+            xdispatch<SK_ANTI, RB>(arg, vr, vi, reg_c, tok, c);
+        } else if (kind == SK_XPERM) {
+            xdispatch<SK_XPERM, RB>(arg, vr, vi, reg_c, tok, c);
+        } else {
+            const uint32_t reg_t = ops[p].reg_t;
+            const bool ctb = ((tid & ops[p].thr_t) != 0) || ((base & ops[p].out_t) != 0);
+#pragma unroll
+            for (int k = 0; k < RA; ++k) {
+                if (!(tok && (((uint32_t)k & reg_c) == reg_c))) continue;
+                const bool tb = ctb || (((uint32_t)k & reg_t) != 0);
+                if (kind == SK_NEG) {
+                    if (tb) { vr[k] = -vr[k]; vi[k] = -vi[k]; }
+                } else if (kind == SK_PHASE) {
+                    if (tb) {
+                        const R r = c.dr * vr[k] - c.di * vi[k], i = c.dr * vi[k] + c.di * vr[k];
+                        vr[k] = r; vi[k] = i;
+                    }
+                } else {
+                    const R fr = tb ? c.dr : c.ar, fi = tb ? c.di : c.ai;
+                    const R r = fr * vr[k] - fi * vi[k], i = fr * vi[k] + fi * vr[k];
+                    vr[k] = r; vi[k] = i;
+                }
+            }
+        }
+    }
+    // the planner always ends a pass in layout 0
+    if constexpr (VEC == 2) {
+#pragma unroll
+        for (int k = 0; k < RA; k += 2) {
+            uint64_t g = toff;
+#pragma unroll
+            for (int j = 1; j < RB; ++j)
+                if ((k >> j) & 1) g |= roff[j];
+            *reinterpret_cast<float4 *>(st + 2 * g) = make_float4(vr[k], vi[k], vr[k + 1], vi[k + 1]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < RA; ++k) {
+            uint64_t g = toff;
+#pragma unroll
+            for (int j = 0; j < RB; ++j)
+                if ((k >> j) & 1) g |= roff[j];
+            *reinterpret_cast<double2 *>(st + 2 * g) = make_double2((double)vr[k], (double)vi[k]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- host planner
+struct SGate {
+    int op;              // GateOp (no OP_SWAP / OP_IDENTITY here)
+    int target;
+    uint64_t ctrl;       // control qubits
+    double m[8];
+    int orig;            // index of the circuit gate it comes from
+    uint64_t xq() const { return (op == OP_DENSE || op == OP_ANTIDIAG || op == OP_XPERM) ? (1ull << target) : 0ull; }
+    uint64_t dq() const { return ctrl | ((op == OP_DIAG || op == OP_DIAG_HI) ? (1ull << target) : 0ull); }
+};
+
+bool commute(const SGate &a, const SGate &b)
+{
+    const uint64_t shared = (a.xq() | a.dq()) & (b.xq() | b.dq());
+    return (shared & (a.xq() | b.xq())) == 0;
+}
+
+// SWAP(a, b) with controls c = CNOT(b -> a) . X(target b; controls c + a) . CNOT(b -> a)
+void lower_gates(const sim_gate *gates, size_t n_gates, std::vector<SGate> *out)
+{
+    static const double X[8] = {0, 0, 1, 0, 1, 0, 0, 0};
+    for (size_t k = 0; k < n_gates; ++k) {
+        const PairGate p = make_pair_gate(gates[k]);
+        uint64_t cm = 0;
+        for (int c = 0; c < p.nctrl; ++c) cm |= 1ull << p.ctrl[c];
+        if (p.op == OP_IDENTITY) continue;
+        if (p.op == OP_SWAP) {
+            const int a = p.target, b = p.target2;
+            SGate g1{OP_XPERM, a, 1ull << b, {}, (int)k};
+            SGate g2{OP_XPERM, b, cm | (1ull << a), {}, (int)k};
+            memcpy(g1.m, X, sizeof X);
+            memcpy(g2.m, X, sizeof X);
+            out->push_back(g1);
+            out->push_back(g2);
+            out->push_back(g1);
+            continue;
+        }
+        SGate g{p.op, p.target, cm, {}, (int)k};
+        memcpy(g.m, p.m, sizeof g.m);
+        out->push_back(g);
+    }
+}
+
+struct Pass {
+    std::vector<int> high;      // global qubits of local bits kLow .. M-1
+    std::vector<int> members;   // gate indices (a valid order)
+};
+
+// Greedy passes: scan the remaining gates in order; a gate joins the pass if
+// it commutes with every gate skipped before it and its non-diagonal qubits
+// fit in Q (adding up to M - kLow high qubits).
+std::vector<Pass> form_passes(const std::vector<SGate> &g, int n, int M)
+{
+    std::vector<Pass> passes;
+    std::vector<char> done(g.size(), 0);
+    const uint64_t low = (1ull << kLow) - 1ull;
+    const int cap = M - kLow;
+    size_t first = 0;
+    while (first < g.size()) {
+        Pass ps;
+        uint64_t qmask = low;
+        uint64_t bx = 0, bd = 0;      // qubits where skipped gates act non-diagonally / diagonally
+        for (size_t i = first; i < g.size(); ++i) {
+            if (done[i]) continue;
+            const uint64_t x = g[i].xq(), d = g[i].dq();
+            const bool free_of_skipped = ((x & (bx | bd)) == 0) && ((d & bx) == 0);
+            bool ok = false;
+            if (free_of_skipped) {
+                const uint64_t add = x & ~qmask;
+                if ((int)ps.high.size() + __builtin_popcountll(add) <= cap) {
+                    ok = true;
+                    for (int q = 0; q < n; ++q)
+                        if ((add >> q) & 1) { ps.high.push_back(q); qmask |= 1ull << q; }
+                }
+            }
+            if (ok) {
+                ps.members.push_back((int)i);
+                done[i] = 1;
+            } else {
+                bx |= x;
+                bd |= d;
+            }
+        }
+        // fill the tile with unused qubits (lowest first)
+        for (int q = kLow; q < n && (int)ps.high.size() < cap; ++q)
+            if (!((qmask >> q) & 1)) { ps.high.push_back(q); qmask |= 1ull << q; }
+        passes.push_back(ps);
+        while (first < g.size() && done[first]) ++first;
+    }
+    return passes;
+}
+
+template <typename R>
+struct PlanBuilder {
+    int n, M, RB, VEC;
+    std::vector<StOp<R>> ops;
+    std::vector<int> order;       // circuit index of each emitted gate op
+    int layout_changes = 0;
+
+    int local_of(const Pass &ps, int q) const
+    {
+        if (q < kLow) return q;
+        for (size_t i = 0; i < ps.high.size(); ++i)
+            if (ps.high[i] == q) return kLow + (int)i;
+        return -1;
+    }
+    int reg_of(int l, int b) const
+    {
+        for (int j = 0; j < RB; ++j)
+            if (reg_local(M, RB, VEC, l, j) == b) return j;
+        return -1;
+    }
+    int thr_of(int l, int b) const
+    {
+        for (int i = 0; i < kThrBits; ++i)
+            if (thr_local(M, RB, VEC, l, i) == b) return i;
+        return -1;
+    }
+
+    void emit_gate(const Pass &ps, const SGate &g, int layout)
+    {
+        StOp<R> o;
+        memset(&o, 0, sizeof o);
+        for (int q = 0; q < n; ++q) {
+            if (!((g.ctrl >> q) & 1)) continue;
+            const int b = local_of(ps, q);
+            if (b < 0) o.out_c |= 1ull << q;
+            else if (reg_of(layout, b) >= 0) o.reg_c |= 1u << reg_of(layout, b);
+            else o.thr_c |= 1u << thr_of(layout, b);
+        }
+        for (int k = 0; k < 8; ++k) o.m[k] = (R)g.m[k];
+        const int bt = local_of(ps, g.target);
+        if (g.op == OP_DIAG || g.op == OP_DIAG_HI) {
+            if (bt < 0) o.out_t = 1ull << g.target;
+            else if (reg_of(layout, bt) >= 0) o.reg_t = 1u << reg_of(layout, bt);
+            else o.thr_t = 1u << thr_of(layout, bt);
+            const bool neg = g.m[6] == -1.0 && g.m[7] == 0.0;
+            o.kind = (g.op == OP_DIAG) ? SK_DIAG : (neg ? SK_NEG : SK_PHASE);
+        } else {
+            o.kind = (g.op == OP_DENSE) ? SK_DENSE : (g.op == OP_ANTIDIAG) ? SK_ANTI : SK_XPERM;
+            o.arg = reg_of(layout, bt);
+        }
+        ops.push_back(o);
+    }
+
+    void emit_layout(int l)
+    {
+        ++layout_changes;
+        StOp<R> o;
+        memset(&o, 0, sizeof o);
+        o.kind = SK_LAYOUT;
+        o.arg = l;
+        ops.push_back(o);
+    }
+
+    // order the pass's gates (respecting non-commuting pairs) so that
+    // consecutive exchange gates share a layout; returns the op count
+    int schedule(const Pass &ps, const std::vector<SGate> &g)
+    {
+        const size_t P = ps.members.size();
+        const size_t start = ops.size();
+        std::vector<int> indeg(P, 0);
+        std::vector<std::vector<int>> succ(P);
+        for (size_t a = 0; a < P; ++a)
+            for (size_t b = a + 1; b < P; ++b)
+                if (!commute(g[ps.members[a]], g[ps.members[b]])) {
+                    succ[a].push_back((int)b);
+                    indeg[b]++;
+                }
+        std::vector<char> emitted(P, 0);
+        const int NL = n_layouts(M, RB);
+        int layout = 0;
+        size_t left = P;
+        auto fits = [&](int i, int l) {
+            const SGate &s = g[ps.members[i]];
+            if (!s.xq()) return true;
+            return reg_of(l, local_of(ps, s.target)) >= 0;
+        };
+        while (left) {
+            int pick = -1;
+            for (size_t i = 0; i < P && pick < 0; ++i)
+                if (!emitted[i] && indeg[i] == 0 && fits((int)i, layout)) pick = (int)i;
+            if (pick < 0) {
+                int best = -1, bestc = -1;
+                for (int l = 0; l < NL; ++l) {
+                    if (l == layout) continue;
+                    int c = 0;
+                    for (size_t i = 0; i < P; ++i)
+                        if (!emitted[i] && indeg[i] == 0 && fits((int)i, l)) ++c;
+                    if (c > bestc) { bestc = c; best = l; }
+                }
+                emit_layout(best);
+                layout = best;
+                continue;
+            }
+            emit_gate(ps, g[ps.members[pick]], layout);
+            order.push_back(g[ps.members[pick]].orig);
+            emitted[pick] = 1;
+            --left;
+            for (int s2 : succ[pick]) indeg[s2]--;
+        }
+        if (layout != 0) emit_layout(0);
+        return (int)(ops.size() - start);
+    }
+};
+
+template <typename R, int M>
+int launch_staged(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &geo)
+{
+    const size_t smem = ((size_t)1 << M) * 2 * sizeof(R);
+    static bool attr_set = false;   // per template instance
+    if (!attr_set) {
+        QSIM_CUDA(cudaFuncSetAttribute(k_staged<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    const uint64_t tiles = 1ull << (s->n - M);
+    launch_begin(s, KC_STAGED, 2.0 * (double)s->bytes);
+    k_staged<R, M><<<(unsigned)tiles, kThr, smem, s->stream>>>((R *)s->amps, dops, nops, geo);
+    return launch_end(s, "staged pass");
+}
+
+template <typename R>
+int run_staged(qsim_state *s, const std::vector<SGate> &g, int M)
+{
+    const int VEC = sizeof(R) == 4 ? 2 : 1;
+    std::vector<Pass> passes = form_passes(g, s->n, M);
+    PlanBuilder<R> pb{s->n, M, M - kThrBits, VEC, {}, {}, 0};
+    std::vector<int> counts;
+    for (const Pass &ps : passes) counts.push_back(pb.schedule(ps, g));
+    const size_t bytes = pb.ops.size() * sizeof(StOp<R>);
+    if (int rc = ensure_host_pinned(&s->host_ops, &s->host_ops_bytes, bytes)) return rc;
+    if (int rc = ensure_device(s, &s->dev_ops, &s->dev_ops_bytes, bytes)) return rc;
+    memcpy(s->host_ops, pb.ops.data(), bytes);
+    QSIM_CUDA(cudaMemcpyAsync(s->dev_ops, s->host_ops, bytes, cudaMemcpyHostToDevice, s->stream));
+    const StOp<R> *dops = (const StOp<R> *)s->dev_ops;
+    size_t off = 0;
+    for (size_t p = 0; p < passes.size(); ++p) {
+        TileGeom geo;
+        memset(&geo, 0, sizeof geo);
+        uint64_t q = (1ull << kLow) - 1ull;
+        for (size_t i = 0; i < passes[p].high.size(); ++i) {
+            geo.hpos[i] = passes[p].high[i];
+            q |= 1ull << passes[p].high[i];
+        }
+        for (int b = 0; b < s->n; ++b)
+            if (!((q >> b) & 1)) geo.outer_pos[geo.n_outer++] = b;
+        int rc;
+        switch (M) {
+        case 11: rc = launch_staged<R, 11>(s, dops + off, counts[p], geo); break;
+        case 12: rc = launch_staged<R, 12>(s, dops + off, counts[p], geo); break;
+        case 13:
+            if constexpr (sizeof(R) == 4) rc = launch_staged<R, 13>(s, dops + off, counts[p], geo);
+            else rc = fail(SIM_EINVAL, "staged: complex128 tiles are at most 12 qubits");
+            break;
+        default: rc = fail(SIM_EINVAL, "staged: unsupported tile size");
+        }
+        if (rc) return rc;
+        off += counts[p];
+    }
+    // the pinned staging buffer is reused by the next call: wait for the copy
+    QSIM_CUDA(cudaStreamSynchronize(s->stream));
+    return SIM_OK;
+}
+
+}  // namespace
+
+int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,
+                    int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len)
+{
+    const bool c128 = dtype == SIM_C128;
+    int M = tile_qubits ? tile_qubits : (c128 ? 12 : 13);
+    if (M > n || M < 11 || M > (c128 ? 12 : 13)) return fail(SIM_EINVAL, "describe: no staged tile fits");
+    std::vector<SGate> g;
+    lower_gates(gates, n_gates, &g);
+    std::vector<Pass> ps = form_passes(g, n, M);
+    PlanBuilder<double> pb{n, M, M - kThrBits, c128 ? 1 : 2, {}, {}, 0};
+    for (const Pass &p : ps) pb.schedule(p, g);
+    if (passes) *passes = (int64_t)ps.size();
+    if (ops) *ops = (int64_t)pb.ops.size();
+    if (layout_changes) *layout_changes = pb.layout_changes;
+    if (order_len) *order_len = pb.order.size();
+    if (order)
+        for (size_t i = 0; i < pb.order.size() && i < order_cap; ++i) order[i] = pb.order[i];
+    return SIM_OK;
+}
+
+int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
+{
+    const bool c128 = s->dtype == SIM_C128;
+    int M = o.tile_qubits ? o.tile_qubits : (c128 ? 12 : 13);
+    if (M > s->n) M = (s->n >= 11) ? 11 : 0;
+    if (c128 && M > 12) M = 12;
+    if (M != 0 && (M < 11 || M > 13)) return fail(SIM_EINVAL, "staged: tile_qubits must be 11, 12 or 13");
+    if (M == 0) {
+        // the state is smaller than a tile: one launch per gate
+        for (size_t k = 0; k < n_gates; ++k)
+            if (int rc = launch_pair_gate(s, make_pair_gate(gates[k]))) return rc;
+        return SIM_OK;
+    }
+    std::vector<SGate> g;
+    lower_gates(gates, n_gates, &g);
+    if (g.empty()) return SIM_OK;
+    return c128 ? run_staged<double>(s, g, M) : run_staged<float>(s, g, M);
+}
+
+}  // namespace qsim

@@ -30,6 +30,7 @@ SIM_F32, SIM_F64 = 0, 1
 SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ETIMEOUT, SIM_EUNSUPPORTED = range(6)
 SIM_PLAN_PER_GATE, SIM_PLAN_STAGED, SIM_PLAN_FUSED, SIM_PLAN_LEARNED = range(4)
 PLANS = {"per_gate": 0, "staged": 1, "fused": 2, "learned": 3}
+CUDA_STREAM_LEGACY = 1      # cudaStreamLegacy
 
 GATE_KINDS = {"u": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8,
               "rx": 9, "ry": 10, "rz": 11, "p": 12, "u3": 13, "swap": 14}
@@ -211,6 +212,22 @@ def sim_sample(h: int, shots: int, seed: int, out=None, out_on_device: bool = Fa
     return arr
 
 
+_sig("sim_plan_describe", [_i32, _i32, P, _sz, P, P, P, P, P, _sz, P])
+
+
+def sim_plan_describe(n: int, dtype: int, sim_gates: np.ndarray, opts: sim_plan_opts):
+    """Host-only: (passes, ops, layout_changes, order) of the staged schedule."""
+    g = np.ascontiguousarray(sim_gates, dtype=SIM_GATE_DTYPE)
+    passes, ops, lc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    ln = ctypes.c_size_t()
+    check(_lib.sim_plan_describe(n, dtype, g.ctypes.data_as(P), len(g), ctypes.byref(opts), ctypes.byref(passes),
+                                 ctypes.byref(ops), ctypes.byref(lc), None, 0, ctypes.byref(ln)))
+    order = np.zeros(ln.value, dtype=np.int32)
+    check(_lib.sim_plan_describe(n, dtype, g.ctypes.data_as(P), len(g), ctypes.byref(opts), None, None, None,
+                                 order.ctypes.data_as(P), len(order), ctypes.byref(ln)))
+    return passes.value, ops.value, lc.value, order
+
+
 def sim_profile_enable(h: int, on: bool = True):
     check(_lib.sim_profile_enable(P(h), int(on)))
 
@@ -249,16 +266,19 @@ class State:
         self._torch = torch
         dev = torch.device(device or "cuda")
         self.stream = torch.cuda.current_stream(dev)
+        # torch's default stream has handle 0; the ABI reads 0 as "make your
+        # own stream", so the legacy default stream is passed explicitly.
+        self.stream_handle = self.stream.cuda_stream or CUDA_STREAM_LEGACY
         tdt = torch.complex128 if self.dtype == SIM_C128 else torch.complex64
         if torch_memory:
             self.tensor = torch.empty(2 ** n, dtype=tdt, device=dev)
             self.h = sim_create_from_buffer(n, self.dtype, self.tensor.data_ptr(),
                                             self.tensor.numel() * self.tensor.element_size(),
-                                            self.stream.cuda_stream)
+                                            self.stream_handle)
             sim_set_basis_state(self.h, 0)
         else:
             self.tensor = None
-            self.h = sim_create(n, self.dtype, self.stream.cuda_stream)
+            self.h = sim_create(n, self.dtype, self.stream_handle)
 
     def close(self):
         if getattr(self, "h", None):
