@@ -210,7 +210,7 @@ def run_ours(args, rank, world, local_rank):
     gates = C.haar_cz(n, depth, seed=SEED)
     sg = sim.to_sim_gates(gates)
     plan = args.plan
-    opts = sim.plan_opts(plan, fuse_k=args.fuse_k)
+    opts = sim.plan_opts(plan, fuse_k=args.fuse_k, tile_qubits=args.tile)
     st = sim.State(n, "c64", device=dev)
     stream = st.stream
     shot_buf = torch.empty(shots, dtype=torch.int64, device=dev)
@@ -296,7 +296,8 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded Haar/CZ circuit)",
             "config": {"workload": workload_name(n, depth), "n_qubits": n, "depth": depth,
-                       "gates": int(len(gates)), "state": "complex64", "plan": plan, "shots": shots,
+                       "gates": int(len(gates)), "state": "complex64", "plan": plan, "tile_qubits": args.tile,
+                       "shots": shots,
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (8 GiB state vs 129 MB L2); no flush"},
             "hbm_gbs": world * step_bytes / (ms_per_step / 1e3) / 1e9,
@@ -346,14 +347,15 @@ def run_variants(args, sim, C, gates, sg, dev, st_c64, peaks):
     t128 = timed(ref, sim.plan_opts("per_gate"), 1)
     out["per_gate_c128"] = {"ms": t128, "gates_per_s": len(gates) / (t128 / 1e3), "infidelity": 0.0,
                             "note": "reference state for the complex64 infidelities"}
-    for plan in args.variant_plans:
+    for spec in args.variant_plans:
+        plan, _, tile = spec.partition(":")
         try:
-            opts = sim.plan_opts(plan, fuse_k=args.fuse_k)
+            opts = sim.plan_opts(plan, fuse_k=args.fuse_k, tile_qubits=int(tile or 0))
             t = timed(st_c64, opts, 2)
             inf = infidelity_torch(st_c64.tensor, ref.tensor)
-            out[plan + "_c64"] = {"ms": t, "gates_per_s": len(gates) / (t / 1e3), "infidelity": inf}
+            out[spec + "_c64"] = {"ms": t, "gates_per_s": len(gates) / (t / 1e3), "infidelity": inf}
         except sim.SimError as e:
-            out[plan + "_c64"] = {"error": str(e)}
+            out[spec + "_c64"] = {"error": str(e)}
     ref.close()
     return out
 
@@ -366,6 +368,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--plan", default="staged")
     ap.add_argument("--fuse-k", type=int, default=5)
+    ap.add_argument("--tile", type=int, default=0, help="tile qubits of the staged plan (0 = library default)")
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
     ap.add_argument("--depth", type=int, default=DEPTH)
     ap.add_argument("--shots", type=int, default=SHOTS)

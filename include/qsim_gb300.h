@@ -173,6 +173,13 @@ int sim_launch_count(sim_t s, uint64_t *out);
 const char *sim_kernel_class_name(int k);
 int sim_num_kernel_classes(void);
 
+/* sim_measure_fma_peak: measured FMA throughput of the current device in
+ *   TFLOP/s (2 flops per FMA) -- which = 0: FP32 fma, 1: packed FP32
+ *   fma.rn.f32x2, 2: FP64 fma.  A few milliseconds of GPU work on the legacy
+ *   default stream; synchronises.  Used as the arithmetic roofline of kernels
+ *   that are not bound by HBM. */
+int sim_measure_fma_peak(int which, double *tflops);
+
 /* Thread-local description of the last failure (empty string if none). */
 const char *sim_last_error(void);
 /* Library version string. */

@@ -3,6 +3,7 @@
 // thread-local message on failure; nothing throws across the boundary.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -154,6 +155,12 @@ int sim_create(int n, int dtype, void *stream, sim_t *out)
     int rc = init_handle(s, stream);
     if (rc) { free_handle(s); return rc; }
     size_t free_b = 0, total_b = 0;
+    // QSIM_INJECT_ENOMEM (host-side fault injection for tests): behave as if
+    // the device had no free memory, without touching the GPU allocator
+    if (getenv("QSIM_INJECT_ENOMEM") != nullptr) {
+        free_handle(s);
+        return fail(SIM_ENOMEM, "sim_create: state does not fit in free device memory (injected)");
+    }
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && s->bytes > free_b) {
         free_handle(s);
         return fail(SIM_ENOMEM, "sim_create: state does not fit in free device memory");

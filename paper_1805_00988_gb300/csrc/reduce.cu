@@ -77,26 +77,35 @@ __device__ __forceinline__ double sq(R re, R im)
 }
 
 
-// VEC amplitudes per 16-byte vector: 2 for complex64, 1 for complex128
+// VEC amplitudes per 16-byte vector: 2 for complex64, 1 for complex128.
+// raw() issues the load only; sq2() turns it into |a|^2 in FP64.  Callers
+// issue a batch of raw loads before any arithmetic so that each thread keeps
+// several 16-byte requests in flight.
 template <typename R> struct AV;
 template <> struct AV<float> {
     static constexpr int VEC = 2;
-    __device__ __forceinline__ static void load(const float *st, uint64_t v, double p[2])
+    using Raw = float4;
+    __device__ __forceinline__ static Raw raw(const float *st, uint64_t v) { return reinterpret_cast<const float4 *>(st)[v]; }
+    __device__ __forceinline__ static void sq2(const Raw &x, double p[2])
     {
-        const float4 x = reinterpret_cast<const float4 *>(st)[v];
         p[0] = sq<float>(x.x, x.y);
         p[1] = sq<float>(x.z, x.w);
     }
+    __device__ __forceinline__ static void load(const float *st, uint64_t v, double p[2]) { sq2(raw(st, v), p); }
 };
 template <> struct AV<double> {
     static constexpr int VEC = 1;
-    __device__ __forceinline__ static void load(const double *st, uint64_t v, double p[2])
+    using Raw = double2;
+    __device__ __forceinline__ static Raw raw(const double *st, uint64_t v) { return reinterpret_cast<const double2 *>(st)[v]; }
+    __device__ __forceinline__ static void sq2(const Raw &x, double p[2])
     {
-        const double2 x = reinterpret_cast<const double2 *>(st)[v];
         p[0] = sq<double>(x.x, x.y);
         p[1] = 0.0;
     }
+    __device__ __forceinline__ static void load(const double *st, uint64_t v, double p[2]) { sq2(raw(st, v), p); }
 };
+
+constexpr int kBatch = 8;     // 16-byte loads in flight per thread
 
 // Masked FP64 sums over a contiguous range per block.
 //   RED_NORM: out0 = sum |a|^2
@@ -111,9 +120,7 @@ __global__ void __launch_bounds__(kRedThreads) k_masked_sum(const R *__restrict_
     const uint64_t lo = (uint64_t)blockIdx.x * per;
     const uint64_t hi = min(nvec, lo + per);
     double a = 0.0, b = 0.0;
-    for (uint64_t v = lo + threadIdx.x; v < hi; v += kRedThreads) {
-        double p[2];
-        AV<R>::load(st, v, p);
+    auto add = [&](uint64_t v, const double p[2]) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const uint64_t i = v * VEC + e;
@@ -125,6 +132,23 @@ __global__ void __launch_bounds__(kRedThreads) k_masked_sum(const R *__restrict_
                 a += p[e] * (double)(n - 2 * __popcll(i));
             }
         }
+    };
+    uint64_t v = lo + threadIdx.x;
+    for (; v + (uint64_t)(kBatch - 1) * kRedThreads < hi; v += (uint64_t)kBatch * kRedThreads) {
+        typename AV<R>::Raw x[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) x[u] = AV<R>::raw(st, v + (uint64_t)u * kRedThreads);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            double p[2];
+            AV<R>::sq2(x[u], p);
+            add(v + (uint64_t)u * kRedThreads, p);
+        }
+    }
+    for (; v < hi; v += kRedThreads) {
+        double p[2];
+        AV<R>::load(st, v, p);
+        add(v, p);
     }
     block_sum2<kRedThreads>(a, b, sh);
     if (threadIdx.x == 0) {
@@ -187,7 +211,20 @@ __global__ void __launch_bounds__(256) k_block_sums(const R *__restrict__ st, ui
     const uint64_t nv = bs / VEC;
     const uint64_t lo = (uint64_t)blockIdx.x * nv;
     double a = 0.0, b = 0.0;
-    for (uint64_t v = threadIdx.x; v < nv; v += 256) {
+    uint64_t v = threadIdx.x;
+    for (; v + (kBatch - 1) * 256 < nv; v += kBatch * 256) {
+        typename AV<R>::Raw x[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) x[u] = AV<R>::raw(st, lo + v + u * 256);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            double p[2];
+            AV<R>::sq2(x[u], p);
+            a += p[0];
+            if (VEC == 2) a += p[1];
+        }
+    }
+    for (; v < nv; v += 256) {
         double p[2];
         AV<R>::load(st, lo + v, p);
         a += p[0];
@@ -288,14 +325,29 @@ __global__ void __launch_bounds__(256) k_resolve(const R *__restrict__ st, uint6
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * bs;
     int my_last = -1;
-    for (uint64_t v = threadIdx.x; v < bs / VEC; v += 256) {
-        double p[2];
-        AV<R>::load(st, base / VEC + v, p);
+    auto put = [&](uint64_t v, const double p[2]) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             cdf[v * VEC + e] = p[e];
             if (p[e] > 0.0) my_last = (int)(v * VEC + e);
         }
+    };
+    uint64_t v = threadIdx.x;
+    for (; v + (kBatch - 1) * 256 < bs / VEC; v += kBatch * 256) {
+        typename AV<R>::Raw x[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) x[u] = AV<R>::raw(st, base / VEC + v + u * 256);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            double p[2];
+            AV<R>::sq2(x[u], p);
+            put(v + u * 256, p);
+        }
+    }
+    for (; v < bs / VEC; v += 256) {
+        double p[2];
+        AV<R>::load(st, base / VEC + v, p);
+        put(v, p);
     }
     if (my_last >= 0) atomicMax(&last_nz, my_last);
     __syncthreads();

@@ -38,12 +38,14 @@ template <typename R>
 struct __align__(16) StOp {
     int32_t kind;      // StKind
     int32_t arg;       // exchange ops: register bit of the target; SK_LAYOUT: new layout
-    uint32_t reg_c;    // register bits that must be 1
     uint32_t thr_c;    // thread bits that must be 1
+    int32_t plain;     // exchange ops: no condition of any kind
     uint64_t out_c;    // global bits (outside the tile) that must be 1
-    uint32_t reg_t;    // diagonal ops: where the target bit is (exactly one of the three is set)
-    uint32_t thr_t;
-    uint64_t out_t;
+    uint64_t km_c;     // bit k: register k satisfies the register-bit conditions
+    uint64_t km_t;     // diagonal ops, bit k: the target bit of register k is 1
+    uint32_t thr_t;    // diagonal ops: thread bit of the target (0 if not a thread bit)
+    uint32_t pad;
+    uint64_t out_t;    // diagonal ops: global bit of the target (0 if inside the tile)
     R m[8];            // A, B, C, D
 };
 
@@ -90,7 +92,7 @@ __host__ __device__ constexpr int reg_part(int M, int RB, int VEC, int l, int k)
 
 // shared-memory slot of local index x (bank-conflict-free for every layout)
 template <int RB, int VEC>
-__device__ __forceinline__ int swz(int x)
+__host__ __device__ constexpr int swz(int x)
 {
     return (VEC == 2) ? (x ^ (((x >> (RB + 1)) & 7) << 1)) : (x ^ ((x >> RB) & 7));
 }
@@ -105,8 +107,83 @@ template <typename R> struct V2;
 template <> struct V2<float> { using T = float2; };
 template <> struct V2<double> { using T = double2; };
 
+// ---------------------------------------------------------------- registers
+// Amplitudes of a thread.  complex64 keeps them as float2 packs along
+// register bit 0 so that two amplitude pairs go through one packed FP32x2
+// instruction (fma.rn.f32x2); complex128 keeps plain doubles.
+template <typename R, int RA> struct Regs;
+template <int RA> struct Regs<float, RA> {
+    float2 r[RA / 2], i[RA / 2];
+    __device__ __forceinline__ float &re(int k) { return (k & 1) ? r[k >> 1].y : r[k >> 1].x; }
+    __device__ __forceinline__ float &im(int k) { return (k & 1) ? i[k >> 1].y : i[k >> 1].x; }
+};
+template <int RA> struct Regs<double, RA> {
+    double r[RA], i[RA];
+    __device__ __forceinline__ double &re(int k) { return r[k]; }
+    __device__ __forceinline__ double &im(int k) { return i[k]; }
+};
+
 template <typename R>
 struct CoefS { R ar, ai, br, bi, cr, ci, dr, di; };
+
+// packed FP32x2 helpers (PTX fma / mul on 64-bit register pairs, sm_100+)
+__device__ __forceinline__ uint64_t pk(float2 v)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(uint64_t v)
+{
+    float2 r;
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ uint64_t pfma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t pmul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+struct PCoef { uint64_t ar, ai, nai, br, bi, nbi, cr, ci, nci, dr, di, ndi; };
+
+__device__ __forceinline__ PCoef make_pcoef(const CoefS<float> &c)
+{
+    PCoef p;
+    p.ar = pk(make_float2(c.ar, c.ar)); p.ai = pk(make_float2(c.ai, c.ai)); p.nai = pk(make_float2(-c.ai, -c.ai));
+    p.br = pk(make_float2(c.br, c.br)); p.bi = pk(make_float2(c.bi, c.bi)); p.nbi = pk(make_float2(-c.bi, -c.bi));
+    p.cr = pk(make_float2(c.cr, c.cr)); p.ci = pk(make_float2(c.ci, c.ci)); p.nci = pk(make_float2(-c.ci, -c.ci));
+    p.dr = pk(make_float2(c.dr, c.dr)); p.di = pk(make_float2(c.di, c.di)); p.ndi = pk(make_float2(-c.di, -c.di));
+    return p;
+}
+
+// two amplitude pairs at once: lanes x / y are independent pairs
+template <int KIND>
+__device__ __forceinline__ void pupd(float2 &Lr, float2 &Li, float2 &Hr, float2 &Hi, const PCoef &c)
+{
+    const uint64_t lr = pk(Lr), li = pk(Li), hr = pk(Hr), hi = pk(Hi);
+    if (KIND == SK_DENSE) {
+        Lr = upk(pfma(c.ar, lr, pfma(c.nai, li, pfma(c.br, hr, pmul(c.nbi, hi)))));
+        Li = upk(pfma(c.ar, li, pfma(c.ai, lr, pfma(c.br, hi, pmul(c.bi, hr)))));
+        Hr = upk(pfma(c.cr, lr, pfma(c.nci, li, pfma(c.dr, hr, pmul(c.ndi, hi)))));
+        Hi = upk(pfma(c.cr, li, pfma(c.ci, lr, pfma(c.dr, hi, pmul(c.di, hr)))));
+    } else if (KIND == SK_ANTI) {
+        Lr = upk(pfma(c.br, hr, pmul(c.nbi, hi)));
+        Li = upk(pfma(c.br, hi, pmul(c.bi, hr)));
+        Hr = upk(pfma(c.cr, lr, pmul(c.nci, li)));
+        Hi = upk(pfma(c.cr, li, pmul(c.ci, lr)));
+    } else {
+        float2 t = Lr; Lr = Hr; Hr = t;
+        t = Li; Li = Hi; Hi = t;
+    }
+}
 
 template <int KIND, typename R>
 __device__ __forceinline__ void xupd(R &lr, R &li, R &hr, R &hi, const CoefS<R> &c)
@@ -127,102 +204,142 @@ __device__ __forceinline__ void xupd(R &lr, R &li, R &hr, R &hi, const CoefS<R> 
     }
 }
 
-template <int J, int KIND, int RB, typename R>
-__device__ __forceinline__ void xop(R *vr, R *vi, uint32_t reg_c, bool tok, const CoefS<R> &c)
+// Exchange op on register bit J.  PLAIN: no condition at all.  Otherwise the
+// amplitude pair (k, k | 2^J) is updated when bit k of `act` is set.
+template <int J, int KIND, bool PLAIN, typename R, int RA>
+__device__ __forceinline__ void xop(Regs<R, RA> &v, uint64_t act, const CoefS<R> &c)
 {
+    constexpr int RB = __builtin_ctz(RA);
     if constexpr (J < RB) {
+        if constexpr (sizeof(R) == 4 && J >= 1) {
+            // packed: packs p and p | 2^(J-1) hold pairs (2p, 2p + 2^J) and (2p + 1, 2p + 1 + 2^J)
+            const PCoef pc = make_pcoef(c);
 #pragma unroll
-        for (int k = 0; k < (1 << RB); ++k) {
-            if (k & (1 << J)) continue;
-            const int k1 = k | (1 << J);
-            if (tok && (((uint32_t)k & reg_c) == reg_c)) xupd<KIND, R>(vr[k], vi[k], vr[k1], vi[k1], c);
+            for (int p = 0; p < RA / 2; ++p) {
+                if (p & (1 << (J - 1))) continue;
+                const int q = p | (1 << (J - 1));
+                if (PLAIN) {
+                    pupd<KIND>(v.r[p], v.i[p], v.r[q], v.i[q], pc);
+                } else {
+                    const bool a0 = (act >> (2 * p)) & 1, a1 = (act >> (2 * p + 1)) & 1;
+                    if (a0 && a1) {
+                        pupd<KIND>(v.r[p], v.i[p], v.r[q], v.i[q], pc);
+                    } else {
+                        if (a0) xupd<KIND, R>(v.r[p].x, v.i[p].x, v.r[q].x, v.i[q].x, c);
+                        if (a1) xupd<KIND, R>(v.r[p].y, v.i[p].y, v.r[q].y, v.i[q].y, c);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < RA; ++k) {
+                if (k & (1 << J)) continue;
+                const int k1 = k | (1 << J);
+                if (PLAIN || ((act >> k) & 1)) xupd<KIND, R>(v.re(k), v.im(k), v.re(k1), v.im(k1), c);
+            }
         }
     }
 }
 
-template <int KIND, int RB, typename R>
-__device__ __forceinline__ void xdispatch(int j, R *vr, R *vi, uint32_t reg_c, bool tok, const CoefS<R> &c)
+template <int KIND, bool PLAIN, typename R, int RA>
+__device__ __forceinline__ void xdispatch(int j, Regs<R, RA> &v, uint64_t act, const CoefS<R> &c)
 {
     switch (j) {
-    case 0: xop<0, KIND, RB>(vr, vi, reg_c, tok, c); break;
-    case 1: xop<1, KIND, RB>(vr, vi, reg_c, tok, c); break;
-    case 2: xop<2, KIND, RB>(vr, vi, reg_c, tok, c); break;
-    case 3: xop<3, KIND, RB>(vr, vi, reg_c, tok, c); break;
-    case 4: xop<4, KIND, RB>(vr, vi, reg_c, tok, c); break;
-    case 5: xop<5, KIND, RB>(vr, vi, reg_c, tok, c); break;
+    case 0: xop<0, KIND, PLAIN>(v, act, c); break;
+    case 1: xop<1, KIND, PLAIN>(v, act, c); break;
+    case 2: xop<2, KIND, PLAIN>(v, act, c); break;
+    case 3: xop<3, KIND, PLAIN>(v, act, c); break;
+    case 4: xop<4, KIND, PLAIN>(v, act, c); break;
+    case 5: xop<5, KIND, PLAIN>(v, act, c); break;
     default: break;
     }
 }
 
-template <int M, int RB, int VEC, int L, typename R>
-__device__ __forceinline__ void store_layout(const R *vr, const R *vi, R *sm, int tid)
+template <int M, int RB, int VEC, int L, typename R, int RA>
+__device__ __forceinline__ void store_layout(Regs<R, RA> &v, R *sm, int tid)
 {
     if constexpr (L < n_layouts(M, RB)) {
         int tp = 0;
 #pragma unroll
         for (int i = 0; i < kThrBits; ++i) tp |= ((tid >> i) & 1) << thr_local(M, RB, VEC, L, i);
+        const int tps = swz<RB, VEC>(tp);   // swz is linear over XOR: swz(tp ^ r) = swz(tp) ^ swz(r)
         if constexpr (VEC == 2 && L == 0) {
 #pragma unroll
-            for (int k = 0; k < (1 << RB); k += 2) {
-                const int p = swz<RB, VEC>(tp | reg_part(M, RB, VEC, L, k));
-                *reinterpret_cast<float4 *>(sm + 2 * p) = make_float4(vr[k], vi[k], vr[k + 1], vi[k + 1]);
+            for (int k = 0; k < RA; k += 2) {
+                const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
+                *reinterpret_cast<float4 *>(sm + 2 * p) = make_float4(v.re(k), v.im(k), v.re(k + 1), v.im(k + 1));
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < (1 << RB); ++k) {
-                const int p = swz<RB, VEC>(tp | reg_part(M, RB, VEC, L, k));
-                typename V2<R>::T v;
-                v.x = vr[k];
-                v.y = vi[k];
-                *reinterpret_cast<typename V2<R>::T *>(sm + 2 * p) = v;
+            for (int k = 0; k < RA; ++k) {
+                const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
+                typename V2<R>::T t;
+                t.x = v.re(k);
+                t.y = v.im(k);
+                *reinterpret_cast<typename V2<R>::T *>(sm + 2 * p) = t;
             }
         }
     }
 }
 
-template <int M, int RB, int VEC, int L, typename R>
-__device__ __forceinline__ void load_layout(R *vr, R *vi, const R *sm, int tid)
+template <int M, int RB, int VEC, int L, typename R, int RA>
+__device__ __forceinline__ void load_layout(Regs<R, RA> &v, const R *sm, int tid)
 {
     if constexpr (L < n_layouts(M, RB)) {
         int tp = 0;
 #pragma unroll
         for (int i = 0; i < kThrBits; ++i) tp |= ((tid >> i) & 1) << thr_local(M, RB, VEC, L, i);
+        const int tps = swz<RB, VEC>(tp);   // swz is linear over XOR: swz(tp ^ r) = swz(tp) ^ swz(r)
         if constexpr (VEC == 2 && L == 0) {
 #pragma unroll
-            for (int k = 0; k < (1 << RB); k += 2) {
-                const int p = swz<RB, VEC>(tp | reg_part(M, RB, VEC, L, k));
-                const float4 v = *reinterpret_cast<const float4 *>(sm + 2 * p);
-                vr[k] = v.x; vi[k] = v.y; vr[k + 1] = v.z; vi[k + 1] = v.w;
+            for (int k = 0; k < RA; k += 2) {
+                const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
+                const float4 t = *reinterpret_cast<const float4 *>(sm + 2 * p);
+                v.re(k) = t.x; v.im(k) = t.y; v.re(k + 1) = t.z; v.im(k + 1) = t.w;
             }
         } else {
 #pragma unroll
-            for (int k = 0; k < (1 << RB); ++k) {
-                const int p = swz<RB, VEC>(tp | reg_part(M, RB, VEC, L, k));
-                const typename V2<R>::T v = *reinterpret_cast<const typename V2<R>::T *>(sm + 2 * p);
-                vr[k] = v.x;
-                vi[k] = v.y;
+            for (int k = 0; k < RA; ++k) {
+                const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
+                const typename V2<R>::T t = *reinterpret_cast<const typename V2<R>::T *>(sm + 2 * p);
+                v.re(k) = t.x;
+                v.im(k) = t.y;
             }
         }
     }
 }
 
-template <int M, int RB, int VEC, typename R>
-__device__ __forceinline__ void relayout(int from, int to, R *vr, R *vi, R *sm, int tid)
+// Sign flips (CZ, Z, CCZ) commute with every diagonal op, so they are
+// collected in a per-thread mask (bit k: negate register k) and applied only
+// before the next op that mixes registers (exchange, layout change, store).
+template <typename R, int RA>
+__device__ __forceinline__ void flush_neg(Regs<R, RA> &v, uint64_t &m)
+{
+    if (m) {
+#pragma unroll
+        for (int k = 0; k < RA; ++k)
+            if ((m >> k) & 1) { v.re(k) = -v.re(k); v.im(k) = -v.im(k); }
+        m = 0;
+    }
+}
+
+template <int M, int RB, int VEC, typename R, int RA>
+__device__ __forceinline__ void relayout(int from, int to, Regs<R, RA> &v, R *sm, int tid)
 {
     __syncthreads();
     switch (from) {
-    case 0: store_layout<M, RB, VEC, 0>(vr, vi, sm, tid); break;
-    case 1: store_layout<M, RB, VEC, 1>(vr, vi, sm, tid); break;
-    case 2: store_layout<M, RB, VEC, 2>(vr, vi, sm, tid); break;
-    case 3: store_layout<M, RB, VEC, 3>(vr, vi, sm, tid); break;
+    case 0: store_layout<M, RB, VEC, 0>(v, sm, tid); break;
+    case 1: store_layout<M, RB, VEC, 1>(v, sm, tid); break;
+    case 2: store_layout<M, RB, VEC, 2>(v, sm, tid); break;
+    case 3: store_layout<M, RB, VEC, 3>(v, sm, tid); break;
     default: break;
     }
     __syncthreads();
     switch (to) {
-    case 0: load_layout<M, RB, VEC, 0>(vr, vi, sm, tid); break;
-    case 1: load_layout<M, RB, VEC, 1>(vr, vi, sm, tid); break;
-    case 2: load_layout<M, RB, VEC, 2>(vr, vi, sm, tid); break;
-    case 3: load_layout<M, RB, VEC, 3>(vr, vi, sm, tid); break;
+    case 0: load_layout<M, RB, VEC, 0>(v, sm, tid); break;
+    case 1: load_layout<M, RB, VEC, 1>(v, sm, tid); break;
+    case 2: load_layout<M, RB, VEC, 2>(v, sm, tid); break;
+    case 3: load_layout<M, RB, VEC, 3>(v, sm, tid); break;
     default: break;
     }
 }
@@ -257,7 +374,7 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
         roff[j] = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
     }
 
-    R vr[RA], vi[RA];
+    Regs<R, RA> v;
     if constexpr (VEC == 2) {
 #pragma unroll
         for (int k = 0; k < RA; k += 2) {
@@ -265,8 +382,8 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
 #pragma unroll
             for (int j = 1; j < RB; ++j)
                 if ((k >> j) & 1) g |= roff[j];
-            const float4 v = *reinterpret_cast<const float4 *>(st + 2 * g);
-            vr[k] = v.x; vi[k] = v.y; vr[k + 1] = v.z; vi[k + 1] = v.w;
+            const float4 t = *reinterpret_cast<const float4 *>(st + 2 * g);
+            v.re(k) = t.x; v.im(k) = t.y; v.re(k + 1) = t.z; v.im(k + 1) = t.w;
         }
     } else {
 #pragma unroll
@@ -275,54 +392,70 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
 #pragma unroll
             for (int j = 0; j < RB; ++j)
                 if ((k >> j) & 1) g |= roff[j];
-            const double2 v = *reinterpret_cast<const double2 *>(st + 2 * g);
-            vr[k] = (R)v.x;
-            vi[k] = (R)v.y;
+            const double2 t = *reinterpret_cast<const double2 *>(st + 2 * g);
+            v.re(k) = (R)t.x;
+            v.im(k) = (R)t.y;
         }
     }
 
     int layout = 0;
+    uint64_t negm = 0;
     for (int p = 0; p < nops; ++p) {
         const int kind = ops[p].kind;
         const int arg = ops[p].arg;
         if (kind == SK_LAYOUT) {
-            relayout<M, RB, VEC>(layout, arg, vr, vi, sm, tid);
+            flush_neg(v, negm);
+            relayout<M, RB, VEC>(layout, arg, v, sm, tid);
             layout = arg;
             continue;
         }
-        const uint32_t reg_c = ops[p].reg_c;
         const bool tok = ((tid & ops[p].thr_c) == ops[p].thr_c) && ((base & ops[p].out_c) == ops[p].out_c);
         CoefS<R> c;
         c.ar = ops[p].m[0]; c.ai = ops[p].m[1]; c.br = ops[p].m[2]; c.bi = ops[p].m[3];
         c.cr = ops[p].m[4]; c.ci = ops[p].m[5]; c.dr = ops[p].m[6]; c.di = ops[p].m[7];
-        if (kind == SK_DENSE) {
-            xdispatch<SK_DENSE, RB>(arg, vr, vi, reg_c, tok, c);
-        } else if (kind == SK_ANTI) {
-            xdispatch<SK_ANTI, RB>(arg, vr, vi, reg_c, tok, c);
-        } else if (kind == SK_XPERM) {
-            xdispatch<SK_XPERM, RB>(arg, vr, vi, reg_c, tok, c);
+        if (kind <= SK_XPERM) {
+            flush_neg(v, negm);
+            const bool plain = ops[p].plain != 0;
+            const uint64_t act = tok ? ops[p].km_c : 0ull;
+            if (kind == SK_DENSE) {
+                if (plain) xdispatch<SK_DENSE, true>(arg, v, act, c);
+                else xdispatch<SK_DENSE, false>(arg, v, act, c);
+            } else if (kind == SK_ANTI) {
+                if (plain) xdispatch<SK_ANTI, true>(arg, v, act, c);
+                else xdispatch<SK_ANTI, false>(arg, v, act, c);
+            } else {
+                if (plain) xdispatch<SK_XPERM, true>(arg, v, act, c);
+                else xdispatch<SK_XPERM, false>(arg, v, act, c);
+            }
         } else {
-            const uint32_t reg_t = ops[p].reg_t;
+            // diagonal: registers whose condition holds (km_c) and whose
+            // target bit is 1 (km_t); the thread / tile part of the target
+            // bit is ctb
             const bool ctb = ((tid & ops[p].thr_t) != 0) || ((base & ops[p].out_t) != 0);
+            const uint64_t cond = tok ? ops[p].km_c : 0ull;
+            const uint64_t one = ctb ? cond : (cond & ops[p].km_t);
+            if (kind == SK_NEG) {
+                negm ^= one;
+            } else if (kind == SK_PHASE) {
 #pragma unroll
-            for (int k = 0; k < RA; ++k) {
-                if (!(tok && (((uint32_t)k & reg_c) == reg_c))) continue;
-                const bool tb = ctb || (((uint32_t)k & reg_t) != 0);
-                if (kind == SK_NEG) {
-                    if (tb) { vr[k] = -vr[k]; vi[k] = -vi[k]; }
-                } else if (kind == SK_PHASE) {
-                    if (tb) {
-                        const R r = c.dr * vr[k] - c.di * vi[k], i = c.dr * vi[k] + c.di * vr[k];
-                        vr[k] = r; vi[k] = i;
+                for (int k = 0; k < RA; ++k)
+                    if ((one >> k) & 1) {
+                        const R r = c.dr * v.re(k) - c.di * v.im(k), i = c.dr * v.im(k) + c.di * v.re(k);
+                        v.re(k) = r; v.im(k) = i;
                     }
-                } else {
-                    const R fr = tb ? c.dr : c.ar, fi = tb ? c.di : c.ai;
-                    const R r = fr * vr[k] - fi * vi[k], i = fr * vi[k] + fi * vr[k];
-                    vr[k] = r; vi[k] = i;
-                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < RA; ++k)
+                    if ((cond >> k) & 1) {
+                        const bool tb = (one >> k) & 1;
+                        const R fr = tb ? c.dr : c.ar, fi = tb ? c.di : c.ai;
+                        const R r = fr * v.re(k) - fi * v.im(k), i = fr * v.im(k) + fi * v.re(k);
+                        v.re(k) = r; v.im(k) = i;
+                    }
             }
         }
     }
+    flush_neg(v, negm);
     // the planner always ends a pass in layout 0
     if constexpr (VEC == 2) {
 #pragma unroll
@@ -331,7 +464,7 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
 #pragma unroll
             for (int j = 1; j < RB; ++j)
                 if ((k >> j) & 1) g |= roff[j];
-            *reinterpret_cast<float4 *>(st + 2 * g) = make_float4(vr[k], vi[k], vr[k + 1], vi[k + 1]);
+            *reinterpret_cast<float4 *>(st + 2 * g) = make_float4(v.re(k), v.im(k), v.re(k + 1), v.im(k + 1));
         }
     } else {
 #pragma unroll
@@ -340,7 +473,7 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
 #pragma unroll
             for (int j = 0; j < RB; ++j)
                 if ((k >> j) & 1) g |= roff[j];
-            *reinterpret_cast<double2 *>(st + 2 * g) = make_double2((double)vr[k], (double)vi[k]);
+            *reinterpret_cast<double2 *>(st + 2 * g) = make_double2((double)v.re(k), (double)v.im(k));
         }
     }
 }
@@ -468,18 +601,19 @@ struct PlanBuilder {
     {
         StOp<R> o;
         memset(&o, 0, sizeof o);
+        uint32_t reg_c = 0, reg_t = 0;
         for (int q = 0; q < n; ++q) {
             if (!((g.ctrl >> q) & 1)) continue;
             const int b = local_of(ps, q);
             if (b < 0) o.out_c |= 1ull << q;
-            else if (reg_of(layout, b) >= 0) o.reg_c |= 1u << reg_of(layout, b);
+            else if (reg_of(layout, b) >= 0) reg_c |= 1u << reg_of(layout, b);
             else o.thr_c |= 1u << thr_of(layout, b);
         }
         for (int k = 0; k < 8; ++k) o.m[k] = (R)g.m[k];
         const int bt = local_of(ps, g.target);
         if (g.op == OP_DIAG || g.op == OP_DIAG_HI) {
             if (bt < 0) o.out_t = 1ull << g.target;
-            else if (reg_of(layout, bt) >= 0) o.reg_t = 1u << reg_of(layout, bt);
+            else if (reg_of(layout, bt) >= 0) reg_t = 1u << reg_of(layout, bt);
             else o.thr_t = 1u << thr_of(layout, bt);
             const bool neg = g.m[6] == -1.0 && g.m[7] == 0.0;
             o.kind = (g.op == OP_DIAG) ? SK_DIAG : (neg ? SK_NEG : SK_PHASE);
@@ -487,6 +621,12 @@ struct PlanBuilder {
             o.kind = (g.op == OP_DENSE) ? SK_DENSE : (g.op == OP_ANTIDIAG) ? SK_ANTI : SK_XPERM;
             o.arg = reg_of(layout, bt);
         }
+        const int RA = 1 << RB;
+        for (int k = 0; k < RA; ++k) {
+            if (((uint32_t)k & reg_c) == reg_c) o.km_c |= 1ull << k;
+            if ((uint32_t)k & reg_t) o.km_t |= 1ull << k;
+        }
+        o.plain = (reg_c == 0 && o.thr_c == 0 && o.out_c == 0) ? 1 : 0;
         ops.push_back(o);
     }
 
@@ -615,7 +755,7 @@ int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int
                     int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len)
 {
     const bool c128 = dtype == SIM_C128;
-    int M = tile_qubits ? tile_qubits : (c128 ? 12 : 13);
+    int M = tile_qubits ? tile_qubits : (c128 ? 11 : 13);
     if (M > n || M < 11 || M > (c128 ? 12 : 13)) return fail(SIM_EINVAL, "describe: no staged tile fits");
     std::vector<SGate> g;
     lower_gates(gates, n_gates, &g);
@@ -634,7 +774,7 @@ int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int
 int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
 {
     const bool c128 = s->dtype == SIM_C128;
-    int M = o.tile_qubits ? o.tile_qubits : (c128 ? 12 : 13);
+    int M = o.tile_qubits ? o.tile_qubits : (c128 ? 11 : 13);
     if (M > s->n) M = (s->n >= 11) ? 11 : 0;
     if (c128 && M > 12) M = 12;
     if (M != 0 && (M < 11 || M > 13)) return fail(SIM_EINVAL, "staged: tile_qubits must be 11, 12 or 13");

@@ -232,8 +232,17 @@ def test_errors_are_status_codes(sim):
         st.measure(7, seed=1)
     st.close()
     with pytest.raises(sim.SimError) as e:
-        sim.sim_create(34, sim.SIM_C128)     # 256 GiB does not fit
-    assert e.value.status in (sim.SIM_ENOMEM, sim.SIM_EINVAL)
+        sim.sim_create(35, sim.SIM_C64)
+    assert e.value.status == sim.SIM_EINVAL
+    # allocation failure, injected on the host (the GPU allocator is not driven out of memory)
+    import os
+    os.environ["QSIM_INJECT_ENOMEM"] = "1"
+    try:
+        with pytest.raises(sim.SimError) as e:
+            sim.sim_create(20, sim.SIM_C64)
+        assert e.value.status == sim.SIM_ENOMEM
+    finally:
+        del os.environ["QSIM_INJECT_ENOMEM"]
 
 
 def test_launches_are_counted(sim):
