@@ -348,9 +348,12 @@ def run_variants(args, sim, C, gates, sg, dev, st_c64, peaks):
     out["per_gate_c128"] = {"ms": t128, "gates_per_s": len(gates) / (t128 / 1e3), "infidelity": 0.0,
                             "note": "reference state for the complex64 infidelities"}
     for spec in args.variant_plans:
-        plan, _, tile = spec.partition(":")
+        plan, _, num = spec.partition(":")
         try:
-            opts = sim.plan_opts(plan, fuse_k=args.fuse_k, tile_qubits=int(tile or 0))
+            if plan == "fused":
+                opts = sim.plan_opts(plan, fuse_k=int(num or args.fuse_k))
+            else:
+                opts = sim.plan_opts(plan, fuse_k=args.fuse_k, tile_qubits=int(num or 0))
             t = timed(st_c64, opts, 2)
             inf = infidelity_torch(st_c64.tensor, ref.tensor)
             out[spec + "_c64"] = {"ms": t, "gates_per_s": len(gates) / (t / 1e3), "infidelity": inf}

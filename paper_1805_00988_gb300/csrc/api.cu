@@ -105,6 +105,8 @@ static int init_handle(qsim_state *s, void *stream)
     QSIM_CUDA(cudaMalloc((void **)&s->red_partial, sizeof(double) * 2 * kRedBlocks));
     QSIM_CUDA(cudaMalloc((void **)&s->red_out, sizeof(double) * 4));
     QSIM_CUDA(cudaMallocHost((void **)&s->host_red, sizeof(double) * 4));
+    QSIM_CUDA(cudaMalloc((void **)&s->dev_status, sizeof(int) * 4));
+    QSIM_CUDA(cudaMemset(s->dev_status, 0, sizeof(int) * 4));
     return SIM_OK;
 }
 
@@ -116,6 +118,7 @@ static void free_handle(qsim_state *s)
     if (s->red_partial) cudaFree(s->red_partial);
     if (s->red_out) cudaFree(s->red_out);
     if (s->host_red) cudaFreeHost(s->host_red);
+    if (s->dev_status) cudaFree(s->dev_status);
     if (s->dev_ops) cudaFree(s->dev_ops);
     if (s->host_ops) cudaFreeHost(s->host_ops);
     for (cudaEvent_t e : s->event_pool) cudaEventDestroy(e);
@@ -367,7 +370,13 @@ int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, c
         if (validate_gate(n, gates[k], &why)) return fail(SIM_EINVAL, "sim_plan_describe: " + why);
     }
     const int plan = opts ? opts->plan : SIM_PLAN_PER_GATE;
-    if (plan != SIM_PLAN_STAGED) return fail(SIM_EUNSUPPORTED, "sim_plan_describe: only the staged plan");
+    if (plan == SIM_PLAN_FUSED) {
+        if (ops) *ops = 0;
+        if (layout_changes) *layout_changes = 0;
+        if (order_len) *order_len = 0;
+        return describe_fused(n, gates, n_gates, opts->fuse_k ? opts->fuse_k : 5, passes);
+    }
+    if (plan != SIM_PLAN_STAGED) return fail(SIM_EUNSUPPORTED, "sim_plan_describe: staged or fused plans only");
     return describe_staged(n, dtype, gates, n_gates, opts->tile_qubits, passes, ops, layout_changes, order,
                            order_cap, order_len);
 }

@@ -1,0 +1,474 @@
+// fused.cu -- gates fused into k-qubit unitaries, built in FP64 on the GPU and
+// applied to the state as a real GEMM on the tcgen05 tensor cores.
+//
+// The full-operator view of §1.3.2 (U_t = I (x) ... (x) U (x) ... (x) I) is
+// exact but needs a 2^n x 2^n matrix; restricted to a block of k qubits it is
+// a 2^k x 2^k unitary U_blk = G_m ... G_1 of the block's gates.  With the
+// block qubits as the fast index, the state is a matrix X [rows x 2^k] and the
+// block applies out = X U_blk^T: a GEMM.  Storing each row interleaved
+// (re, im) makes it a real GEMM with K = N = 2^(k+1):
+//     D[r, 2i+b] = sum_{j,a} X[r, 2j+a] * W[2j+a, 2i+b],
+//     W[2j, 2i] = W[2j+1, 2i+1] = Re U_ij,  W[2j+1, 2i] = -Im U_ij,  W[2j, 2i+1] = Im U_ij,
+// so the complex64 state is read and written in place, without de-interleaving.
+//
+// Precision: kind::tf32 keeps 10 mantissa bits, too few for an infidelity of
+// 1e-6 over ~100 blocks.  Both operands are split x = x_hi + x_lo with x_hi
+// the TF32 truncation of x, and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is
+// accumulated in FP32 in tensor memory (3xTF32; Ootomo & Yokota 2022).  U_blk
+// itself is formed in FP64 (k_fuse_build) before the split.
+//
+// Apply kernel: one CTA of 128 threads per 128 rows (MMA M = 128); thread r
+// owns row r: it gathers the row's 2^k amplitudes (coalesced across threads),
+// writes A_hi / A_lo in shared memory in the canonical no-swizzle K-major
+// layout (8-row x 16-byte core matrices), one thread issues the MMAs, the
+// commit arrives on an mbarrier, and each warp reads its 32 TMEM lanes back
+// (tcgen05.ld 32x32b) and scatters the row.  Every wait is bounded; on a
+// timeout the kernel records SIM_ETIMEOUT in a device status word, frees its
+// tensor memory and returns.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kRows = 128;              // MMA M, rows per CTA
+constexpr int kNChunk = 64;             // N columns per MMA sequence
+constexpr long long kSpinLimit = 1ll << 22;   // mbarrier polls before a wait gives up
+
+struct FGate {                          // one gate of a block, in block-local qubits
+    int32_t target;
+    uint32_t ctrl;
+    double m[8];
+};
+
+// ------------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);              // start address >> 4      (bits 0-13)
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;           // leading byte offset >> 4 (bits 16-29)
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;           // stride byte offset >> 4  (bits 32-45)
+    d |= (uint64_t)1 << 46;                                // descriptor version 1     (bits 46-47)
+    return d;                                              // base offset 0, no swizzle
+}
+
+__host__ __device__ constexpr uint32_t make_idesc_tf32(int M, int N)
+{
+    return (1u << 4)                        // D format F32
+           | (2u << 7)                      // A format TF32
+           | (2u << 10)                     // B format TF32
+           | ((uint32_t)(N >> 3) << 17)     // N / 8
+           | ((uint32_t)(M >> 4) << 24);    // M / 16   (A, B K-major; no negate, no sparsity)
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: false after kSpinLimit polls
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+{
+    for (long long i = 0; i < kSpinLimit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__host__ __device__ __forceinline__ float tf32_trunc(float x)
+{
+#ifdef __CUDA_ARCH__
+    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+#else
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u &= 0xFFFFE000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+#endif
+}
+
+// byte offset of element (row, kk) in a K-major no-swizzle operand of K columns
+__host__ __device__ __forceinline__ uint32_t kmajor_off(uint32_t row, uint32_t kk, uint32_t K)
+{
+    return (((row >> 3) * (K >> 2) + (kk >> 2)) << 7) + ((row & 7) << 4) + ((kk & 3) << 2);
+}
+
+// ------------------------------------------------------------------ FP64 builder
+// One CTA per block: U = G_m ... G_1 applied to the identity column by column
+// in FP64 (the columns are 2^k-amplitude states of the block's qubits), then
+// W (the real form) split into TF32 hi / lo in the B-operand layout:
+// per N-chunk of kNChunk columns, [hi | lo], each chunk N_C x K K-major.
+template <int KQ>
+__global__ void __launch_bounds__(256) k_fuse_build(const FGate *__restrict__ gates, const int *__restrict__ goff,
+                                                    float *__restrict__ bout)
+{
+    constexpr int D = 1 << KQ;
+    constexpr int K = 2 * D;
+    constexpr int NC = K < kNChunk ? K : kNChunk;
+    extern __shared__ double2 U[];          // U[i * D + c], row i, column c
+    const int blk = blockIdx.x;
+    for (int e = threadIdx.x; e < D * D; e += 256) U[e] = make_double2((e / D) == (e % D) ? 1.0 : 0.0, 0.0);
+    __syncthreads();
+    for (int g = goff[blk]; g < goff[blk + 1]; ++g) {
+        const int t = gates[g].target;
+        const uint32_t cm = gates[g].ctrl;
+        const double ar = gates[g].m[0], ai = gates[g].m[1], br = gates[g].m[2], bi = gates[g].m[3];
+        const double cr = gates[g].m[4], ci = gates[g].m[5], dr = gates[g].m[6], di = gates[g].m[7];
+        for (int e = threadIdx.x; e < D * (D / 2); e += 256) {
+            const int c = e / (D / 2), p = e % (D / 2);
+            const int i0 = ((p >> t) << (t + 1)) | (p & ((1 << t) - 1));
+            if (((uint32_t)i0 & cm) != cm) continue;
+            const int i1 = i0 | (1 << t);
+            const double2 a = U[i0 * D + c], b = U[i1 * D + c];
+            U[i0 * D + c] = make_double2(ar * a.x - ai * a.y + br * b.x - bi * b.y, ar * a.y + ai * a.x + br * b.y + bi * b.x);
+            U[i1 * D + c] = make_double2(cr * a.x - ci * a.y + dr * b.x - di * b.y, cr * a.y + ci * a.x + dr * b.y + di * b.x);
+        }
+        __syncthreads();
+    }
+    float *out = bout + (size_t)blk * 2 * K * K;
+    for (int e = threadIdx.x; e < K * K; e += 256) {
+        const int n = e / K, kk = e % K;            // B_store[n][kk] = W[kk][n]
+        const int i = n >> 1, b = n & 1, j = kk >> 1, a = kk & 1;
+        const double2 u = U[i * D + j];
+        const double w = (a == b) ? u.x : (a == 1 ? -u.y : u.y);
+        const float hi = tf32_trunc((float)w);
+        const float lo = (float)(w - (double)hi);
+        const int ch = n / NC, nl = n % NC;
+        float *chunk = out + (size_t)ch * 2 * NC * K;
+        const uint32_t off = kmajor_off(nl, kk, K) >> 2;
+        chunk[off] = hi;
+        chunk[NC * K + off] = lo;
+    }
+}
+
+// ------------------------------------------------------------------ apply
+struct ApplyArgs {
+    int nq;             // qubits of the block (KQ)
+    int pos[8];         // global qubits of the block, ascending (local bit i <-> pos[i])
+    uint64_t rows;      // 2^(n - KQ)
+};
+
+template <int KQ>
+__global__ void __launch_bounds__(kRows, 1) k_fused_apply(float *__restrict__ st, const float *__restrict__ bmat,
+                                                          ApplyArgs a, int *__restrict__ status)
+{
+    constexpr int D = 1 << KQ;
+    constexpr int K = 2 * D;
+    constexpr int NC = K < kNChunk ? K : kNChunk;
+    constexpr int NCH = K / NC;
+    constexpr uint32_t NCOLS = (K < 32) ? 32 : K;              // TMEM columns (power of two >= 32)
+    constexpr uint32_t SBO = (K / 4) * 128;                    // 8-row group stride, bytes
+    constexpr uint32_t IDESC = make_idesc_tf32(kRows, NC);
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *a_hi = reinterpret_cast<float *>(smem);              // kRows x K
+    float *a_lo = a_hi + kRows * K;
+    float *b_s = a_lo + kRows * K;                              // [hi | lo] NC x K each
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    __shared__ uint64_t dep[D];
+    __shared__ int failed;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    // a CTA that timed out already: the rest of the launch stops at once
+    if (*reinterpret_cast<volatile int *>(status) != 0) return;
+    if (warp == 0) tmem_alloc(&tslot, NCOLS);
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        failed = 0;
+    }
+    for (int c = tid; c < D; c += kRows) {
+        uint64_t o = 0;
+        for (int i = 0; i < KQ; ++i)
+            if ((c >> i) & 1) o |= 1ull << a.pos[i];
+        dep[c] = o;
+    }
+    __syncthreads();
+
+    // row tid: base index = global row with zero bits inserted at the block positions
+    const uint64_t R = (uint64_t)blockIdx.x * kRows + tid;
+    uint64_t base = R;
+#pragma unroll
+    for (int i = 0; i < KQ; ++i) {
+        const int p = a.pos[i];
+        base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1ull));
+    }
+    const bool live = R < a.rows;
+    for (int c = 0; c < D; ++c) {
+        float2 v = make_float2(0.f, 0.f);
+        if (live) v = *reinterpret_cast<const float2 *>(st + 2 * (base | dep[c]));
+        const float hr = tf32_trunc(v.x), hi = tf32_trunc(v.y);
+        const uint32_t off = kmajor_off(tid, 2 * c, K);        // (re, im) share one 16-byte row chunk
+        *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_hi) + off) = make_float2(hr, hi);
+        *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_lo) + off) = make_float2(v.x - hr, v.y - hi);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = tslot;
+
+    for (int ch = 0; ch < NCH; ++ch) {
+        // B chunk: hi and lo, copied as 16-byte vectors
+        const float4 *src = reinterpret_cast<const float4 *>(bmat + (size_t)ch * 2 * NC * K);
+        float4 *dst = reinterpret_cast<float4 *>(b_s);
+        for (int e = tid; e < 2 * NC * K / 4; e += kRows) dst[e] = src[e];
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo);
+            const uint32_t sb_hi = smem_u32(b_s), sb_lo = smem_u32(b_s + NC * K);
+            const uint32_t d = taddr + (uint32_t)(ch * NC);
+#pragma unroll 1
+            for (int ks = 0; ks < K / 8; ++ks) {
+                const uint32_t ko = (uint32_t)ks * 256;       // two 16-byte core-matrix columns per K = 8
+                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC, ks > 0);
+                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_lo + ko, 128, SBO), IDESC, 1);
+                mma_tf32(d, make_desc(sa_lo + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC, 1);
+            }
+            mma_commit(&bar);
+        }
+        if (!mbar_wait_bounded(&bar, (uint32_t)(ch & 1))) failed = 1;
+        tc_fence_after();
+        __syncthreads();
+        if (failed) break;
+    }
+
+    if (!failed) {
+        // each warp reads its 32 lanes (= rows 32w .. 32w+31) column block by column block
+        const uint32_t lane_base = taddr + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int col = 0; col < K; col += 16) {
+            float v[16];
+            tmem_ld16(lane_base + (uint32_t)col, v);
+            if (live) {
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int c = col / 2 + e;
+                    *reinterpret_cast<float2 *>(st + 2 * (base | dep[c])) = make_float2(v[2 * e], v[2 * e + 1]);
+                }
+            }
+        }
+    } else {
+        if (tid == 0) atomicExch(status, SIM_ETIMEOUT);
+        // give MMAs still in flight one more bounded wait before the memory is released
+        mbar_wait_bounded(&bar, 0u);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, NCOLS);
+}
+
+template <int KQ>
+size_t apply_smem_bytes()
+{
+    constexpr int K = 2 << KQ;
+    constexpr int NC = K < kNChunk ? K : kNChunk;
+    return (size_t)(2 * kRows * K + 2 * NC * K) * sizeof(float);
+}
+
+// ------------------------------------------------------------------ host planner
+struct Block {
+    uint64_t qmask;
+    std::vector<int> members;
+};
+
+// Greedy fixed-k blocks: scan the remaining gates; a gate joins the block if
+// it commutes with every gate skipped before it and the union of qubits stays
+// within k.
+std::vector<Block> form_blocks(const std::vector<SGate> &g, int k)
+{
+    std::vector<Block> blocks;
+    std::vector<char> done(g.size(), 0);
+    size_t first = 0;
+    while (first < g.size()) {
+        Block b{0, {}};
+        uint64_t bx = 0, bd = 0;
+        for (size_t i = first; i < g.size(); ++i) {
+            if (done[i]) continue;
+            const uint64_t x = g[i].xq(), d = g[i].dq();
+            const bool free_of_skipped = ((x & (bx | bd)) == 0) && ((d & bx) == 0);
+            if (free_of_skipped && __builtin_popcountll(b.qmask | x | d) <= k) {
+                b.qmask |= x | d;
+                b.members.push_back((int)i);
+                done[i] = 1;
+            } else {
+                bx |= x;
+                bd |= d;
+            }
+        }
+        blocks.push_back(b);
+        while (first < g.size() && done[first]) ++first;
+    }
+    return blocks;
+}
+
+template <int KQ>
+int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Block> &blocks)
+{
+    constexpr int K = 2 << KQ;
+    const int n = s->n;
+    // pad every block to KQ qubits (identity on the added ones)
+    std::vector<std::vector<int>> pos(blocks.size());
+    std::vector<FGate> fg;
+    std::vector<int> goff(1, 0);
+    for (size_t b = 0; b < blocks.size(); ++b) {
+        uint64_t q = blocks[b].qmask;
+        for (int extra = 0; extra < n && __builtin_popcountll(q) < KQ; ++extra) q |= 1ull << extra;
+        for (int i = 0; i < n; ++i)
+            if ((q >> i) & 1) pos[b].push_back(i);
+        auto loc = [&](int qubit) {
+            for (int i = 0; i < KQ; ++i)
+                if (pos[b][i] == qubit) return i;
+            return -1;
+        };
+        for (int m : blocks[b].members) {
+            FGate f;
+            f.target = loc(g[m].target);
+            f.ctrl = 0;
+            for (int c = 0; c < n; ++c)
+                if ((g[m].ctrl >> c) & 1) f.ctrl |= 1u << loc(c);
+            memcpy(f.m, g[m].m, sizeof f.m);
+            fg.push_back(f);
+        }
+        goff.push_back((int)fg.size());
+    }
+    const size_t nb = blocks.size();
+    const size_t bytes_g = fg.size() * sizeof(FGate), bytes_o = goff.size() * sizeof(int);
+    const size_t bytes_b = nb * 2 * (size_t)K * K * sizeof(float);
+    const size_t o_g = 0, o_o = (bytes_g + 255) & ~(size_t)255, o_b = (o_o + bytes_o + 255) & ~(size_t)255;
+    const size_t total = o_b + bytes_b;
+    if (int rc = ensure_host_pinned(&s->host_ops, &s->host_ops_bytes, o_b)) return rc;
+    char *scratch = nullptr;
+    QSIM_CUDA(cudaMallocAsync((void **)&scratch, total, s->stream));
+    memcpy((char *)s->host_ops + o_g, fg.data(), bytes_g);
+    memcpy((char *)s->host_ops + o_o, goff.data(), bytes_o);
+    int rc = SIM_OK;
+    do {
+        if (cudaMemcpyAsync(scratch, s->host_ops, o_b, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "fused upload");
+            break;
+        }
+        if (cudaMemsetAsync(s->dev_status, 0, sizeof(int), s->stream) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "status reset");
+            break;
+        }
+        const size_t smb = (size_t)(1 << KQ) * (1 << KQ) * sizeof(double2);
+        cudaFuncSetAttribute(k_fuse_build<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
+        launch_begin(s, KC_FUSE_BUILD, (double)bytes_b);
+        k_fuse_build<KQ><<<(unsigned)nb, 256, smb, s->stream>>>((const FGate *)(scratch + o_g),
+                                                                 (const int *)(scratch + o_o), (float *)(scratch + o_b));
+        if ((rc = launch_end(s, "fused build"))) break;
+        const size_t sma = apply_smem_bytes<KQ>();
+        cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
+        const uint64_t rows = 1ull << (n - KQ);
+        for (size_t b = 0; b < nb && rc == SIM_OK; ++b) {
+            ApplyArgs a{};
+            a.nq = KQ;
+            for (int i = 0; i < KQ; ++i) a.pos[i] = pos[b][i];
+            a.rows = rows;
+            launch_begin(s, KC_FUSED, 2.0 * (double)s->bytes);
+            k_fused_apply<KQ><<<(unsigned)((rows + kRows - 1) / kRows), kRows, sma, s->stream>>>(
+                (float *)s->amps, (const float *)(scratch + o_b) + b * 2 * (size_t)K * K, a, s->dev_status);
+            rc = launch_end(s, "fused apply");
+        }
+    } while (0);
+    cudaFreeAsync(scratch, s->stream);
+    int hstatus = 0;
+    QSIM_CUDA(cudaMemcpyAsync(&hstatus, s->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    QSIM_CUDA(cudaStreamSynchronize(s->stream));
+    if (rc == SIM_OK && hstatus != 0) rc = fail(SIM_ETIMEOUT, "fused apply: a tensor-core wait gave up");
+    return rc;
+}
+
+}  // namespace
+
+int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out)
+{
+    std::vector<SGate> g;
+    lower_gates(gates, n_gates, &g);
+    std::vector<Block> b = form_blocks(g, k);
+    if (blocks_out) *blocks_out = (int64_t)b.size();
+    (void)n;
+    return SIM_OK;
+}
+
+int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
+{
+    if (s->dtype != SIM_C64) return fail(SIM_EUNSUPPORTED, "fused plan: complex64 states only (TF32 tensor cores)");
+    int k = o.fuse_k ? o.fuse_k : 5;
+    if (k < 3 || k > 6) return fail(SIM_EINVAL, "fused plan: fuse_k must be in 3..6");
+    if (s->n < k + 7) return fail(SIM_EINVAL, "fused plan: needs n >= fuse_k + 7 (one CTA covers 128 rows)");
+    std::vector<SGate> g;
+    lower_gates(gates, n_gates, &g);
+    if (g.empty()) return SIM_OK;
+    std::vector<Block> blocks = form_blocks(g, k);
+    switch (k) {
+    case 3: return run_fused<3>(s, g, blocks);
+    case 4: return run_fused<4>(s, g, blocks);
+    case 5: return run_fused<5>(s, g, blocks);
+    default: return run_fused<6>(s, g, blocks);
+    }
+}
+
+}  // namespace qsim

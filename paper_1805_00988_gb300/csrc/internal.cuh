@@ -60,6 +60,7 @@ struct qsim_state {
     double *red_partial = nullptr;   // kRedBlocks * 4 doubles
     double *red_out = nullptr;       // 4 doubles
     double *host_red = nullptr;      // pinned, 4 doubles
+    int *dev_status = nullptr;       // device status word of bounded waits (0 = ok)
     // circuit upload buffers (device), grown on demand
     void *dev_ops = nullptr;
     size_t dev_ops_bytes = 0;
@@ -125,9 +126,28 @@ int launch_probabilities(qsim_state *s, void *dev_out, int out_real);
 int launch_collapse(qsim_state *s, int qubit, int outcome, double scale);
 int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
 
+// ---------------------------------------------------------------- plan lowering
+// A circuit gate reduced to what the tile and block planners need: a 2x2
+// matrix on one target with a set of control qubits.  SWAP is lowered to
+// three CNOT-type moves; identity gates are dropped.
+struct SGate {
+    int op;              // GateOp (no OP_SWAP / OP_IDENTITY here)
+    int target;
+    uint64_t ctrl;       // control qubits
+    double m[8];
+    int orig;            // index of the circuit gate it comes from
+    uint64_t xq() const { return (op == OP_DENSE || op == OP_ANTIDIAG || op == OP_XPERM) ? (1ull << target) : 0ull; }
+    uint64_t dq() const { return ctrl | ((op == OP_DIAG || op == OP_DIAG_HI) ? (1ull << target) : 0ull); }
+};
+
+// true when the two gates commute: every shared qubit is acted on diagonally by both
+bool commute(const SGate &a, const SGate &b);
+void lower_gates(const sim_gate *gates, size_t n_gates, std::vector<SGate> *out);
+
 // ---------------------------------------------------------------- staged / fused plans
 int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
 int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
+int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out);
 int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,
                     int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len);
 

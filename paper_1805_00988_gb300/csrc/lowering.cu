@@ -1,0 +1,41 @@
+// lowering.cu -- circuit gates to the planners' gate form.
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace qsim {
+
+bool commute(const SGate &a, const SGate &b)
+{
+    const uint64_t shared = (a.xq() | a.dq()) & (b.xq() | b.dq());
+    return (shared & (a.xq() | b.xq())) == 0;
+}
+
+// SWAP(a, b) with controls c = CNOT(b -> a) . X(target b; controls c + a) . CNOT(b -> a)
+void lower_gates(const sim_gate *gates, size_t n_gates, std::vector<SGate> *out)
+{
+    static const double X[8] = {0, 0, 1, 0, 1, 0, 0, 0};
+    for (size_t k = 0; k < n_gates; ++k) {
+        const PairGate p = make_pair_gate(gates[k]);
+        uint64_t cm = 0;
+        for (int c = 0; c < p.nctrl; ++c) cm |= 1ull << p.ctrl[c];
+        if (p.op == OP_IDENTITY) continue;
+        if (p.op == OP_SWAP) {
+            const int a = p.target, b = p.target2;
+            SGate g1{OP_XPERM, a, 1ull << b, {}, (int)k};
+            SGate g2{OP_XPERM, b, cm | (1ull << a), {}, (int)k};
+            memcpy(g1.m, X, sizeof X);
+            memcpy(g2.m, X, sizeof X);
+            out->push_back(g1);
+            out->push_back(g2);
+            out->push_back(g1);
+            continue;
+        }
+        SGate g{p.op, p.target, cm, {}, (int)k};
+        memcpy(g.m, p.m, sizeof g.m);
+        out->push_back(g);
+    }
+}
+
+}  // namespace qsim

@@ -3,10 +3,5 @@
 
 namespace qsim {
 
-int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
-{
-    (void)s; (void)gates; (void)n_gates; (void)o;
-    return fail(SIM_EUNSUPPORTED, "fused plan not built yet");
-}
 
 }  // namespace qsim

@@ -113,14 +113,49 @@ template <> struct V2<double> { using T = double2; };
 // instruction (fma.rn.f32x2); complex128 keeps plain doubles.
 template <typename R, int RA> struct Regs;
 template <int RA> struct Regs<float, RA> {
-    float2 r[RA / 2], i[RA / 2];
-    __device__ __forceinline__ float &re(int k) { return (k & 1) ? r[k >> 1].y : r[k >> 1].x; }
-    __device__ __forceinline__ float &im(int k) { return (k & 1) ? i[k >> 1].y : i[k >> 1].x; }
+    // pack p = (amplitude 2p, amplitude 2p + 1) as one 64-bit register pair
+    uint64_t r[RA / 2], i[RA / 2];
+    __device__ __forceinline__ static float lo(uint64_t x)
+    {
+        float a, b;
+        asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+        return a;
+    }
+    __device__ __forceinline__ static float hi(uint64_t x)
+    {
+        float a, b;
+        asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+        return b;
+    }
+    __device__ __forceinline__ static uint64_t mk(float a, float b)
+    {
+        uint64_t x;
+        asm("mov.b64 %0, {%1,%2};" : "=l"(x) : "f"(a), "f"(b));
+        return x;
+    }
+    __device__ __forceinline__ float getr(int k) const { return (k & 1) ? hi(r[k >> 1]) : lo(r[k >> 1]); }
+    __device__ __forceinline__ float geti(int k) const { return (k & 1) ? hi(i[k >> 1]) : lo(i[k >> 1]); }
+    __device__ __forceinline__ void setr(int k, float v)
+    {
+        r[k >> 1] = (k & 1) ? mk(lo(r[k >> 1]), v) : mk(v, hi(r[k >> 1]));
+    }
+    __device__ __forceinline__ void seti(int k, float v)
+    {
+        i[k >> 1] = (k & 1) ? mk(lo(i[k >> 1]), v) : mk(v, hi(i[k >> 1]));
+    }
+    // both amplitudes of pack p at once
+    __device__ __forceinline__ void set2(int p, float r0, float i0, float r1, float i1)
+    {
+        r[p] = mk(r0, r1);
+        i[p] = mk(i0, i1);
+    }
 };
 template <int RA> struct Regs<double, RA> {
     double r[RA], i[RA];
-    __device__ __forceinline__ double &re(int k) { return r[k]; }
-    __device__ __forceinline__ double &im(int k) { return i[k]; }
+    __device__ __forceinline__ double getr(int k) const { return r[k]; }
+    __device__ __forceinline__ double geti(int k) const { return i[k]; }
+    __device__ __forceinline__ void setr(int k, double v) { r[k] = v; }
+    __device__ __forceinline__ void seti(int k, double v) { i[k] = v; }
 };
 
 template <typename R>
@@ -166,22 +201,23 @@ __device__ __forceinline__ PCoef make_pcoef(const CoefS<float> &c)
 
 // two amplitude pairs at once: lanes x / y are independent pairs
 template <int KIND>
-__device__ __forceinline__ void pupd(float2 &Lr, float2 &Li, float2 &Hr, float2 &Hi, const PCoef &c)
+__device__ __forceinline__ void pupd(uint64_t &lr, uint64_t &li, uint64_t &hr, uint64_t &hi, const PCoef &c)
 {
-    const uint64_t lr = pk(Lr), li = pk(Li), hr = pk(Hr), hi = pk(Hi);
     if (KIND == SK_DENSE) {
-        Lr = upk(pfma(c.ar, lr, pfma(c.nai, li, pfma(c.br, hr, pmul(c.nbi, hi)))));
-        Li = upk(pfma(c.ar, li, pfma(c.ai, lr, pfma(c.br, hi, pmul(c.bi, hr)))));
-        Hr = upk(pfma(c.cr, lr, pfma(c.nci, li, pfma(c.dr, hr, pmul(c.ndi, hi)))));
-        Hi = upk(pfma(c.cr, li, pfma(c.ci, lr, pfma(c.dr, hi, pmul(c.di, hr)))));
+        const uint64_t nlr = pfma(c.ar, lr, pfma(c.nai, li, pfma(c.br, hr, pmul(c.nbi, hi))));
+        const uint64_t nli = pfma(c.ar, li, pfma(c.ai, lr, pfma(c.br, hi, pmul(c.bi, hr))));
+        const uint64_t nhr = pfma(c.cr, lr, pfma(c.nci, li, pfma(c.dr, hr, pmul(c.ndi, hi))));
+        const uint64_t nhi = pfma(c.cr, li, pfma(c.ci, lr, pfma(c.dr, hi, pmul(c.di, hr))));
+        lr = nlr; li = nli; hr = nhr; hi = nhi;
     } else if (KIND == SK_ANTI) {
-        Lr = upk(pfma(c.br, hr, pmul(c.nbi, hi)));
-        Li = upk(pfma(c.br, hi, pmul(c.bi, hr)));
-        Hr = upk(pfma(c.cr, lr, pmul(c.nci, li)));
-        Hi = upk(pfma(c.cr, li, pmul(c.ci, lr)));
+        const uint64_t nlr = pfma(c.br, hr, pmul(c.nbi, hi));
+        const uint64_t nli = pfma(c.br, hi, pmul(c.bi, hr));
+        const uint64_t nhr = pfma(c.cr, lr, pmul(c.nci, li));
+        const uint64_t nhi = pfma(c.cr, li, pmul(c.ci, lr));
+        lr = nlr; li = nli; hr = nhr; hi = nhi;
     } else {
-        float2 t = Lr; Lr = Hr; Hr = t;
-        t = Li; Li = Hi; Hi = t;
+        uint64_t t = lr; lr = hr; hr = t;
+        t = li; li = hi; hi = t;
     }
 }
 
@@ -224,9 +260,11 @@ __device__ __forceinline__ void xop(Regs<R, RA> &v, uint64_t act, const CoefS<R>
                     const bool a0 = (act >> (2 * p)) & 1, a1 = (act >> (2 * p + 1)) & 1;
                     if (a0 && a1) {
                         pupd<KIND>(v.r[p], v.i[p], v.r[q], v.i[q], pc);
-                    } else {
-                        if (a0) xupd<KIND, R>(v.r[p].x, v.i[p].x, v.r[q].x, v.i[q].x, c);
-                        if (a1) xupd<KIND, R>(v.r[p].y, v.i[p].y, v.r[q].y, v.i[q].y, c);
+                    } else if (a0 || a1) {
+                        const int k = 2 * p + (a0 ? 0 : 1), k1 = 2 * q + (a0 ? 0 : 1);
+                        R lr = v.getr(k), li = v.geti(k), hr = v.getr(k1), hi = v.geti(k1);
+                        xupd<KIND, R>(lr, li, hr, hi, c);
+                        v.setr(k, lr); v.seti(k, li); v.setr(k1, hr); v.seti(k1, hi);
                     }
                 }
             }
@@ -235,7 +273,11 @@ __device__ __forceinline__ void xop(Regs<R, RA> &v, uint64_t act, const CoefS<R>
             for (int k = 0; k < RA; ++k) {
                 if (k & (1 << J)) continue;
                 const int k1 = k | (1 << J);
-                if (PLAIN || ((act >> k) & 1)) xupd<KIND, R>(v.re(k), v.im(k), v.re(k1), v.im(k1), c);
+                if (PLAIN || ((act >> k) & 1)) {
+                    R lr = v.getr(k), li = v.geti(k), hr = v.getr(k1), hi = v.geti(k1);
+                    xupd<KIND, R>(lr, li, hr, hi, c);
+                    v.setr(k, lr); v.seti(k, li); v.setr(k1, hr); v.seti(k1, hi);
+                }
             }
         }
     }
@@ -267,15 +309,15 @@ __device__ __forceinline__ void store_layout(Regs<R, RA> &v, R *sm, int tid)
 #pragma unroll
             for (int k = 0; k < RA; k += 2) {
                 const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
-                *reinterpret_cast<float4 *>(sm + 2 * p) = make_float4(v.re(k), v.im(k), v.re(k + 1), v.im(k + 1));
+                *reinterpret_cast<float4 *>(sm + 2 * p) = make_float4(v.getr(k), v.geti(k), v.getr(k + 1), v.geti(k + 1));
             }
         } else {
 #pragma unroll
             for (int k = 0; k < RA; ++k) {
                 const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
                 typename V2<R>::T t;
-                t.x = v.re(k);
-                t.y = v.im(k);
+                t.x = v.getr(k);
+                t.y = v.geti(k);
                 *reinterpret_cast<typename V2<R>::T *>(sm + 2 * p) = t;
             }
         }
@@ -295,15 +337,15 @@ __device__ __forceinline__ void load_layout(Regs<R, RA> &v, const R *sm, int tid
             for (int k = 0; k < RA; k += 2) {
                 const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
                 const float4 t = *reinterpret_cast<const float4 *>(sm + 2 * p);
-                v.re(k) = t.x; v.im(k) = t.y; v.re(k + 1) = t.z; v.im(k + 1) = t.w;
+                v.set2(k >> 1, t.x, t.y, t.z, t.w);
             }
         } else {
 #pragma unroll
             for (int k = 0; k < RA; ++k) {
                 const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
                 const typename V2<R>::T t = *reinterpret_cast<const typename V2<R>::T *>(sm + 2 * p);
-                v.re(k) = t.x;
-                v.im(k) = t.y;
+                v.setr(k, t.x);
+                v.seti(k, t.y);
             }
         }
     }
@@ -318,7 +360,7 @@ __device__ __forceinline__ void flush_neg(Regs<R, RA> &v, uint64_t &m)
     if (m) {
 #pragma unroll
         for (int k = 0; k < RA; ++k)
-            if ((m >> k) & 1) { v.re(k) = -v.re(k); v.im(k) = -v.im(k); }
+            if ((m >> k) & 1) { v.setr(k, -v.getr(k)); v.seti(k, -v.geti(k)); }
         m = 0;
     }
 }
@@ -345,7 +387,8 @@ __device__ __forceinline__ void relayout(int from, int to, Regs<R, RA> &v, R *sm
 }
 
 template <typename R, int M>
-__global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
+__global__ void __launch_bounds__(kThr, (sizeof(R) == 4 && M >= 13) ? 1 : 2)
+k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
                                                    TileGeom geo)
 {
     constexpr int VEC = (sizeof(R) == 4) ? 2 : 1;
@@ -383,7 +426,7 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
             for (int j = 1; j < RB; ++j)
                 if ((k >> j) & 1) g |= roff[j];
             const float4 t = *reinterpret_cast<const float4 *>(st + 2 * g);
-            v.re(k) = t.x; v.im(k) = t.y; v.re(k + 1) = t.z; v.im(k + 1) = t.w;
+            v.set2(k >> 1, t.x, t.y, t.z, t.w);
         }
     } else {
 #pragma unroll
@@ -393,8 +436,8 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
             for (int j = 0; j < RB; ++j)
                 if ((k >> j) & 1) g |= roff[j];
             const double2 t = *reinterpret_cast<const double2 *>(st + 2 * g);
-            v.re(k) = (R)t.x;
-            v.im(k) = (R)t.y;
+            v.setr(k, (R)t.x);
+            v.seti(k, (R)t.y);
         }
     }
 
@@ -440,8 +483,9 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
 #pragma unroll
                 for (int k = 0; k < RA; ++k)
                     if ((one >> k) & 1) {
-                        const R r = c.dr * v.re(k) - c.di * v.im(k), i = c.dr * v.im(k) + c.di * v.re(k);
-                        v.re(k) = r; v.im(k) = i;
+                        const R vr = v.getr(k), vi = v.geti(k);
+                        v.setr(k, c.dr * vr - c.di * vi);
+                        v.seti(k, c.dr * vi + c.di * vr);
                     }
             } else {
 #pragma unroll
@@ -449,8 +493,9 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
                     if ((cond >> k) & 1) {
                         const bool tb = (one >> k) & 1;
                         const R fr = tb ? c.dr : c.ar, fi = tb ? c.di : c.ai;
-                        const R r = fr * v.re(k) - fi * v.im(k), i = fr * v.im(k) + fi * v.re(k);
-                        v.re(k) = r; v.im(k) = i;
+                        const R vr = v.getr(k), vi = v.geti(k);
+                        v.setr(k, fr * vr - fi * vi);
+                        v.seti(k, fr * vi + fi * vr);
                     }
             }
         }
@@ -464,7 +509,7 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
 #pragma unroll
             for (int j = 1; j < RB; ++j)
                 if ((k >> j) & 1) g |= roff[j];
-            *reinterpret_cast<float4 *>(st + 2 * g) = make_float4(v.re(k), v.im(k), v.re(k + 1), v.im(k + 1));
+            *reinterpret_cast<float4 *>(st + 2 * g) = make_float4(v.getr(k), v.geti(k), v.getr(k + 1), v.geti(k + 1));
         }
     } else {
 #pragma unroll
@@ -473,54 +518,12 @@ __global__ void __launch_bounds__(kThr, 2) k_staged(R *__restrict__ st, const St
 #pragma unroll
             for (int j = 0; j < RB; ++j)
                 if ((k >> j) & 1) g |= roff[j];
-            *reinterpret_cast<double2 *>(st + 2 * g) = make_double2((double)v.re(k), (double)v.im(k));
+            *reinterpret_cast<double2 *>(st + 2 * g) = make_double2((double)v.getr(k), (double)v.geti(k));
         }
     }
 }
 
 // ---------------------------------------------------------------- host planner
-struct SGate {
-    int op;              // GateOp (no OP_SWAP / OP_IDENTITY here)
-    int target;
-    uint64_t ctrl;       // control qubits
-    double m[8];
-    int orig;            // index of the circuit gate it comes from
-    uint64_t xq() const { return (op == OP_DENSE || op == OP_ANTIDIAG || op == OP_XPERM) ? (1ull << target) : 0ull; }
-    uint64_t dq() const { return ctrl | ((op == OP_DIAG || op == OP_DIAG_HI) ? (1ull << target) : 0ull); }
-};
-
-bool commute(const SGate &a, const SGate &b)
-{
-    const uint64_t shared = (a.xq() | a.dq()) & (b.xq() | b.dq());
-    return (shared & (a.xq() | b.xq())) == 0;
-}
-
-// SWAP(a, b) with controls c = CNOT(b -> a) . X(target b; controls c + a) . CNOT(b -> a)
-void lower_gates(const sim_gate *gates, size_t n_gates, std::vector<SGate> *out)
-{
-    static const double X[8] = {0, 0, 1, 0, 1, 0, 0, 0};
-    for (size_t k = 0; k < n_gates; ++k) {
-        const PairGate p = make_pair_gate(gates[k]);
-        uint64_t cm = 0;
-        for (int c = 0; c < p.nctrl; ++c) cm |= 1ull << p.ctrl[c];
-        if (p.op == OP_IDENTITY) continue;
-        if (p.op == OP_SWAP) {
-            const int a = p.target, b = p.target2;
-            SGate g1{OP_XPERM, a, 1ull << b, {}, (int)k};
-            SGate g2{OP_XPERM, b, cm | (1ull << a), {}, (int)k};
-            memcpy(g1.m, X, sizeof X);
-            memcpy(g2.m, X, sizeof X);
-            out->push_back(g1);
-            out->push_back(g2);
-            out->push_back(g1);
-            continue;
-        }
-        SGate g{p.op, p.target, cm, {}, (int)k};
-        memcpy(g.m, p.m, sizeof g.m);
-        out->push_back(g);
-    }
-}
-
 struct Pass {
     std::vector<int> high;      // global qubits of local bits kLow .. M-1
     std::vector<int> members;   // gate indices (a valid order)

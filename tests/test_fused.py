@@ -1,0 +1,100 @@
+"""The fused plan: gates grouped into blocks of at most k qubits, each block's
+2^k x 2^k unitary formed in FP64 on the GPU and applied with TF32-split
+tensor-core GEMMs (complex64 states).  Tolerance as for complex64:
+|psi - ref| <= 1e-5 max|ref| element-wise and infidelity <= 1e-6."""
+import numpy as np
+import pytest
+
+from paper_1805_00988_gb300 import circuits as C
+
+
+def test_block_counts_cpu():
+    from paper_1805_00988_gb300 import sim
+    g = sim.to_sim_gates(C.haar_cz(30, 20, seed=1234))
+    counts = [sim.sim_plan_describe(30, 0, g, sim.plan_opts("fused", fuse_k=k))[0] for k in (3, 4, 5, 6)]
+    # larger blocks never need more of them
+    assert counts == sorted(counts, reverse=True)
+    assert counts[-1] < 900
+
+
+@pytest.fixture(scope="module")
+def gsim():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1805_00988_gb300 import sim as S
+    return S
+
+
+def check(orc, got, ref):
+    got = got.astype(np.complex128)
+    err = np.max(np.abs(got - ref))
+    assert err <= 1e-5 * np.max(np.abs(ref)), err
+    assert orc.infidelity(ref, got) <= 1e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
+def test_fused_single_block(gsim, orc, k):
+    """One Hadamard on each of k qubits: one block, one GEMM."""
+    n = k + 8
+    g = C.concat([C.gate("h", q) for q in range(k)])
+    st = gsim.State(n, "c64")
+    psi = C.random_state(n, seed=k)
+    st.load(psi)
+    st.apply(g, plan="fused", fuse_k=k)
+    check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))
+    st.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n,k", [(10, 3), (12, 4), (13, 5), (14, 6), (16, 3), (18, 5), (20, 6)])
+def test_fused_random_circuits(gsim, orc, n, k):
+    g = C.concat([C.random_gates(n, 300, seed=n * 10 + k), C.qft(n)])
+    st = gsim.State(n, "c64")
+    psi = C.random_state(n, seed=n)
+    st.load(psi)
+    st.apply(g, plan="fused", fuse_k=k)
+    check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))
+    st.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [4, 6])
+def test_fused_haar_cz_20q(gsim, orc, k):
+    n = 20
+    g = C.haar_cz(n, 20, seed=1234)
+    st = gsim.State(n, "c64")
+    st.apply(g, plan="fused", fuse_k=k)
+    check(orc, st.state(), orc.apply_circuit(orc.basis_state(n, 0), g))
+    st.close()
+
+
+@pytest.mark.gpu
+def test_fused_rejects_c128_and_small(gsim):
+    st = gsim.State(12, "c128")
+    with pytest.raises(gsim.SimError) as e:
+        st.apply(C.qft(12), plan="fused", fuse_k=4)
+    assert e.value.status == gsim.SIM_EUNSUPPORTED
+    st.close()
+    st = gsim.State(9, "c64")
+    with pytest.raises(gsim.SimError):
+        st.apply(C.qft(9), plan="fused", fuse_k=4)
+    st.close()
+
+
+@pytest.mark.gpu
+def test_fused_haar_cz_30q_vs_c128(gsim):
+    import torch
+    n = 30
+    g = C.haar_cz(n, 20, seed=1234)
+    a = gsim.State(n, "c64")
+    a.apply(g, plan="fused", fuse_k=5)
+    b = gsim.State(n, "c128")
+    b.apply(g, plan="staged")
+    ip = torch.zeros((), dtype=torch.complex128, device="cuda")
+    for o in range(0, 2 ** n, 1 << 26):
+        ip += torch.vdot(a.tensor[o:o + (1 << 26)].to(torch.complex128), b.tensor[o:o + (1 << 26)])
+    assert 1.0 - abs(ip.item()) ** 2 / a.norm2() <= 1e-6
+    a.close()
+    b.close()
