@@ -144,6 +144,77 @@ int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, 
 int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
 int sim_expect_z_sum(sim_t s, double *out);
 
+/* ---- batches of small circuits ---------------------------------------------
+ * Many independent registers, each started in |0...0> (§2.1), each with its
+ * own gate list applied by Algorithm 1 (§2.3), each returning
+ * <sum_i Z_i> = sum_x |a_x|^2 (n - 2 popcount x) (FP64 accumulation).
+ *
+ * sim_batch_create: plan and upload `count` circuits (complex64 states).
+ *   n_qubits[c] in [1, 24]; the gates of circuit c are
+ *   gates[gate_offsets[c] .. gate_offsets[c+1]) (count + 1 offsets, non-
+ *   decreasing).  All host arrays are copied.  The run is captured once as a
+ *   CUDA graph (a reset kernel + one persistent kernel with a device work
+ *   queue); stream as in sim_create.  SIM_EINVAL for invalid circuits,
+ *   SIM_ENOMEM if the scratch (one state per circuit above 13 qubits, 8 B per
+ *   amplitude, plus plan data) does not fit.
+ * sim_batch_run: launch the graph; expz_out gets `count` doubles (device
+ *   memory when out_on_device, else host memory); synchronises the stream.
+ *   SIM_ETIMEOUT if a bounded device-side wait gave up (about one second);
+ *   the CUDA context stays usable.
+ * sim_batch_info: items in the work queue, passes, encoded ops, device bytes
+ *   held, persistent grid size (any output may be NULL).
+ * sim_batch_destroy: release everything the batch holds. */
+typedef struct qsim_batch *sim_batch_t;
+int sim_batch_create(int count, const int32_t *n_qubits, const int64_t *gate_offsets, const sim_gate *gates,
+                     void *stream, sim_batch_t *out);
+int sim_batch_run(sim_batch_t b, double *expz_out, int out_on_device);
+int sim_batch_info(sim_batch_t b, int64_t *items, int64_t *passes, int64_t *ops, int64_t *scratch_bytes, int *grid);
+int sim_batch_destroy(sim_batch_t b);
+
+/* ---- plan cost model ---------------------------------------------------------
+ * A small MLP (d_in -> hidden -> hidden -> 1, ReLU) trained on the GPU by the
+ * library's own forward / backward / Adam kernels to predict the log of a
+ * circuit segment's run time under each plan variant (there is no paper
+ * counterpart: the paper applies every gate with its own kernel launch).
+ * Parameters: one FP32 vector W1 (d_in x hidden, row-major), b1, W2, b2,
+ * W3 (hidden x 1), b3 -- sim_mlp_param_count() floats.
+ *
+ * sim_mlp_create: zero parameters; d_in, hidden in [1, 256]; stream as in
+ *   sim_create.
+ * sim_mlp_set_params / get_params: host arrays of sim_mlp_param_count floats
+ *   (set also clears the Adam moments).
+ * sim_mlp_forward: y[r] for rows r of x (rows x d_in, row-major); x and y
+ *   device pointers when on_device, else host.
+ * sim_mlp_loss_grad: L = mean (y - t)^2 and dL/dparams (host, may be NULL).
+ * sim_mlp_train: `steps` full-batch Adam steps (beta1 0.9, beta2 0.999,
+ *   eps 1e-8, learning rate lr); *final_loss (may be NULL) after the last.
+ * sim_set_cost_model: SIM_PLAN_LEARNED on this handle consults model m (NULL
+ *   = no model: the greedy fixed-k plan is used).  The model must outlive the
+ *   handle's use of it. */
+typedef struct qsim_mlp *sim_mlp_t;
+int sim_mlp_param_count(int d_in, int hidden);
+int sim_mlp_create(int d_in, int hidden, void *stream, sim_mlp_t *out);
+int sim_mlp_destroy(sim_mlp_t m);
+int sim_mlp_set_params(sim_mlp_t m, const float *params);
+int sim_mlp_get_params(sim_mlp_t m, float *params);
+int sim_mlp_forward(sim_mlp_t m, const float *x, int64_t rows, float *y, int on_device);
+int sim_mlp_loss_grad(sim_mlp_t m, const float *x, const float *t, int64_t rows, int on_device, float *loss,
+                      float *grad);
+int sim_mlp_train(sim_mlp_t m, const float *x, const float *t, int64_t rows, int steps, float lr, int on_device,
+                  float *final_loss);
+int sim_set_cost_model(sim_t s, sim_mlp_t m);
+
+/* sim_plan_features: the cost model's input row for a segment of gates on an
+ *   n-qubit register under plan variant v (0 per-gate, 1 staged 12-qubit
+ *   tiles, 2 staged 13-qubit tiles, 3..6 fused with k = 3..6): SIM_FEATURES
+ *   floats into out.  Host only. */
+#define SIM_FEATURES 16
+#define SIM_VARIANTS 7
+int sim_plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int variant, float *out);
+/* sim_last_plan: the variant the last SIM_PLAN_LEARNED call chose for each
+ *   window of gates (up to cap entries; the count in *len). */
+int sim_last_plan(sim_t s, int32_t *variants, size_t cap, size_t *len);
+
 /* ---- plan introspection (host only, no GPU needed) ---------------------------
  * sim_plan_describe: build the SIM_PLAN_STAGED schedule of a circuit for an
  *   n-qubit register of the given dtype without running it.  Outputs (any may

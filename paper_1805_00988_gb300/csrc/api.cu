@@ -299,8 +299,9 @@ int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_
     case SIM_PLAN_STAGED:
         return apply_circuit_staged(s, gates, n_gates, o);
     case SIM_PLAN_FUSED:
-    case SIM_PLAN_LEARNED:
         return apply_circuit_fused(s, gates, n_gates, o);
+    case SIM_PLAN_LEARNED:
+        return apply_circuit_learned(s, gates, n_gates, o);
     default:
         return fail(SIM_EINVAL, "sim_apply_circuit: unknown plan");
     }

@@ -37,7 +37,7 @@ namespace {
 
 constexpr int kRows = 128;              // MMA M, rows per CTA
 constexpr int kNChunk = 64;             // N columns per MMA sequence
-constexpr long long kSpinLimit = 1ll << 22;   // mbarrier polls before a wait gives up
+constexpr unsigned long long kWaitNs = 200000000ull;   // 0.2 s: a tensor-core wait gives up after this
 
 struct FGate {                          // one gate of a block, in block-local qubits
     int32_t target;
@@ -96,12 +96,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// bounded wait: false after kSpinLimit polls
+__device__ __forceinline__ unsigned long long gtimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: false once kWaitNs of wall time have passed
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
 {
-    for (long long i = 0; i < kSpinLimit; ++i)
+    const unsigned long long t0 = gtimer_ns();
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-    return false;
+        if (gtimer_ns() - t0 > kWaitNs) return false;
+    }
 }
 
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
@@ -331,6 +339,7 @@ size_t apply_smem_bytes()
 struct Block {
     uint64_t qmask;
     std::vector<int> members;
+    bool wide = false;        // one gate on more than k qubits: applied by a per-gate launch
 };
 
 // Greedy fixed-k blocks: scan the remaining gates; a gate joins the block if
@@ -357,6 +366,13 @@ std::vector<Block> form_blocks(const std::vector<SGate> &g, int k)
                 bd |= d;
             }
         }
+        if (b.members.empty()) {
+            // the first remaining gate alone spans more than k qubits
+            b.qmask = g[first].xq() | g[first].dq();
+            b.members.push_back((int)first);
+            b.wide = true;
+            done[first] = 1;
+        }
         blocks.push_back(b);
         while (first < g.size() && done[first]) ++first;
     }
@@ -373,6 +389,10 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
     std::vector<FGate> fg;
     std::vector<int> goff(1, 0);
     for (size_t b = 0; b < blocks.size(); ++b) {
+        if (blocks[b].wide) {
+            goff.push_back((int)fg.size());
+            continue;
+        }
         uint64_t q = blocks[b].qmask;
         for (int extra = 0; extra < n && __builtin_popcountll(q) < KQ; ++extra) q |= 1ull << extra;
         for (int i = 0; i < n; ++i)
@@ -423,6 +443,10 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
         cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
         const uint64_t rows = 1ull << (n - KQ);
         for (size_t b = 0; b < nb && rc == SIM_OK; ++b) {
+            if (blocks[b].wide) {
+                rc = launch_sgate(s, g[blocks[b].members[0]]);
+                continue;
+            }
             ApplyArgs a{};
             a.nq = KQ;
             for (int i = 0; i < KQ; ++i) a.pos[i] = pos[b][i];

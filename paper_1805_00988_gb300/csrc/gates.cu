@@ -15,6 +15,7 @@
 // HBM-bound.  A target on bit 0 (complex64) loads the pair as one 16-byte
 // vector.
 #include <cmath>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -318,18 +319,36 @@ int op_class(int op)
 
 }  // namespace
 
+static int launch_pair_impl(qsim_state *s, const PairGate &g, uint64_t cm);
+
 int launch_pair_gate(qsim_state *s, const PairGate &g)
 {
+    uint64_t cm = 0;
+    for (int k = 0; k < g.nctrl; ++k) cm |= 1ull << g.ctrl[k];
+    return launch_pair_impl(s, g, cm);
+}
+
+int launch_sgate(qsim_state *s, const SGate &sg)
+{
+    PairGate g{};
+    g.op = sg.op;
+    g.target = sg.target;
+    g.target2 = -1;
+    g.nctrl = 0;
+    memcpy(g.m, sg.m, sizeof g.m);
+    return launch_pair_impl(s, g, sg.ctrl);
+}
+
+static int launch_pair_impl(qsim_state *s, const PairGate &g, uint64_t cm)
+{
     if (g.op == OP_IDENTITY) return SIM_OK;
+    if (__builtin_popcountll(cm) > 3) return fail(SIM_EUNSUPPORTED, "per-gate launch: at most 3 controls");
     PairArgs a{};
     int pos[4], np = 0;
     pos[np++] = g.target;
     if (g.op == OP_SWAP) pos[np++] = g.target2;
-    uint64_t cm = 0;
-    for (int k = 0; k < g.nctrl; ++k) {
-        pos[np++] = g.ctrl[k];
-        cm |= 1ull << g.ctrl[k];
-    }
+    for (int q = 0; q < 64 && np < 4; ++q)
+        if ((cm >> q) & 1) pos[np++] = q;
     for (int i = 1; i < np; ++i)            // insertion sort, ascending
         for (int j = i; j > 0 && pos[j - 1] > pos[j]; --j) {
             int t = pos[j]; pos[j] = pos[j - 1]; pos[j - 1] = t;

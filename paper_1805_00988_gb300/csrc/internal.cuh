@@ -61,6 +61,8 @@ struct qsim_state {
     double *red_out = nullptr;       // 4 doubles
     double *host_red = nullptr;      // pinned, 4 doubles
     int *dev_status = nullptr;       // device status word of bounded waits (0 = ok)
+    void *cost_model = nullptr;      // qsim_mlp used by SIM_PLAN_LEARNED (not owned)
+    std::vector<int> last_plan;      // variant chosen per window by the last learned plan
     // circuit upload buffers (device), grown on demand
     void *dev_ops = nullptr;
     size_t dev_ops_bytes = 0;
@@ -144,9 +146,14 @@ struct SGate {
 bool commute(const SGate &a, const SGate &b);
 void lower_gates(const sim_gate *gates, size_t n_gates, std::vector<SGate> *out);
 
+// one lowered gate (up to 3 controls) as its own per-gate launch
+int launch_sgate(qsim_state *s, const SGate &g);
+
 // ---------------------------------------------------------------- staged / fused plans
 int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
 int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
+int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
+int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out);
 int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out);
 int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,
                     int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len);

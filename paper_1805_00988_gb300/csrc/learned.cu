@@ -1,0 +1,161 @@
+// learned.cu -- SIM_PLAN_LEARNED: the circuit is cut into windows of
+// consecutive gates; for every window and every feasible plan variant the
+// host computes a feature row, the cost model (mlp.cu) predicts the log run
+// time of all rows in one batched forward pass on the GPU, and each window is
+// applied with its cheapest variant.  Without a model the greedy fixed-k tile
+// planner (the staged plan) is used: it is both the fallback and the judge the
+// learned plans are measured against.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+extern "C" int sim_mlp_forward(qsim_mlp *m, const float *x, int64_t rows, float *y, int on_device);
+
+namespace qsim {
+
+namespace {
+
+struct Window {
+    size_t first, count;
+};
+
+int variant_opts(int v, sim_plan_opts *o)
+{
+    memset(o, 0, sizeof *o);
+    if (v == 0) { o->plan = SIM_PLAN_PER_GATE; return 0; }
+    if (v == 1 || v == 2) { o->plan = SIM_PLAN_STAGED; o->tile_qubits = (v == 1) ? 12 : 13; return 0; }
+    if (v >= 3 && v <= 6) { o->plan = SIM_PLAN_FUSED; o->fuse_k = v; return 0; }
+    return -1;
+}
+
+bool feasible(int n, int dtype, int v)
+{
+    if (v == 0) return true;
+    if (v == 1) return n >= 12 && dtype == SIM_C64 ? true : (v == 1 && n >= 12 && dtype == SIM_C128);
+    if (v == 2) return n >= 13 && dtype == SIM_C64;
+    return dtype == SIM_C64 && n >= v + 7;
+}
+
+}  // namespace
+
+int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out)
+{
+    if (!feasible(n, dtype, v)) return SIM_EUNSUPPORTED;
+    std::vector<SGate> g;
+    lower_gates(gates, n_gates, &g);
+    double dense = 0, ctrlx = 0, diag = 0;
+    uint64_t touched = 0;
+    for (const SGate &s : g) {
+        touched |= s.xq() | s.dq();
+        if (s.xq()) (s.ctrl ? ctrlx : dense) += 1;
+        else diag += 1;
+    }
+    const double m = (double)g.size();
+    double launches = m, ops = 0, lc = 0;
+    if (v == 1 || v == 2) {
+        int64_t p = 0, o = 0, l = 0;
+        if (describe_staged(n, dtype, gates, n_gates, v == 1 ? 12 : 13, &p, &o, &l, nullptr, 0, nullptr)) return SIM_EINVAL;
+        launches = (double)p;
+        ops = (double)o;
+        lc = (double)l;
+    } else if (v >= 3) {
+        int64_t b = 0;
+        describe_fused(n, gates, n_gates, v, &b);
+        launches = (double)b;
+    }
+    for (int i = 0; i < SIM_FEATURES; ++i) out[i] = 0.f;
+    out[0] = (float)(n / 32.0);
+    out[1] = (float)(std::log2(m + 1.0) / 12.0);
+    out[2] = (float)(m > 0 ? dense / m : 0);
+    out[3] = (float)(m > 0 ? diag / m : 0);
+    out[4] = (float)(m > 0 ? ctrlx / m : 0);
+    out[5] = (float)(__builtin_popcountll(touched) / (double)n);
+    out[6 + v] = 1.f;
+    out[13] = (float)(std::log2(launches + 1.0) / 12.0);
+    out[14] = (float)(std::log2(ops + 1.0) / 14.0);
+    out[15] = (float)(lc / (ops + 1.0));
+    return SIM_OK;
+}
+
+int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
+{
+    if (!s->cost_model) {
+        sim_plan_opts st{};
+        st.plan = SIM_PLAN_STAGED;
+        st.tile_qubits = o.tile_qubits;
+        return apply_circuit_staged(s, gates, n_gates, st);
+    }
+    // windows of about three layers of single-qubit gates
+    const size_t W = (size_t)std::max(64, 3 * s->n);
+    std::vector<Window> win;
+    for (size_t f = 0; f < n_gates; f += W) win.push_back(Window{f, std::min(W, n_gates - f)});
+    std::vector<float> rows;
+    std::vector<std::pair<size_t, int>> who;
+    for (size_t w = 0; w < win.size(); ++w)
+        for (int v = 0; v < SIM_VARIANTS; ++v) {
+            float f[SIM_FEATURES];
+            if (plan_features(s->n, s->dtype, gates + win[w].first, win[w].count, v, f) != SIM_OK) continue;
+            rows.insert(rows.end(), f, f + SIM_FEATURES);
+            who.push_back({w, v});
+        }
+    std::vector<float> pred(who.size());
+    if (int rc = sim_mlp_forward((qsim_mlp *)s->cost_model, rows.data(), (int64_t)who.size(), pred.data(), 0)) return rc;
+    std::vector<int> best(win.size(), -1);
+    std::vector<float> bestp(win.size(), 0.f);
+    for (size_t r = 0; r < who.size(); ++r) {
+        const size_t w = who[r].first;
+        if (best[w] < 0 || pred[r] < bestp[w]) { best[w] = who[r].second; bestp[w] = pred[r]; }
+    }
+    s->last_plan.assign(best.begin(), best.end());
+    for (size_t w = 0; w < win.size(); ++w) {
+        sim_plan_opts vo;
+        variant_opts(best[w] < 0 ? 0 : best[w], &vo);
+        int rc;
+        if (vo.plan == SIM_PLAN_PER_GATE) {
+            rc = SIM_OK;
+            for (size_t k = 0; k < win[w].count && rc == SIM_OK; ++k)
+                rc = launch_pair_gate(s, make_pair_gate(gates[win[w].first + k]));
+        } else if (vo.plan == SIM_PLAN_STAGED) {
+            rc = apply_circuit_staged(s, gates + win[w].first, win[w].count, vo);
+        } else {
+            rc = apply_circuit_fused(s, gates + win[w].first, win[w].count, vo);
+        }
+        if (rc) return rc;
+    }
+    return SIM_OK;
+}
+
+}  // namespace qsim
+
+using namespace qsim;
+
+extern "C" int sim_plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int variant, float *out)
+{
+    set_error("");
+    if (n < 1 || n > 34 || !out || variant < 0 || variant >= SIM_VARIANTS || (n_gates && !gates))
+        return fail(SIM_EINVAL, "sim_plan_features: bad arguments");
+    for (size_t k = 0; k < n_gates; ++k) {
+        std::string why;
+        if (validate_gate(n, gates[k], &why)) return fail(SIM_EINVAL, "sim_plan_features: " + why);
+    }
+    const int rc = plan_features(n, dtype, gates, n_gates, variant, out);
+    if (rc == SIM_EUNSUPPORTED) return fail(rc, "sim_plan_features: variant not feasible for this register");
+    return rc;
+}
+
+extern "C" int sim_set_cost_model(sim_t s, qsim_mlp *m)
+{
+    if (!s) return fail(SIM_EINVAL, "sim_set_cost_model: null handle");
+    s->cost_model = m;
+    return SIM_OK;
+}
+
+extern "C" int sim_last_plan(sim_t s, int32_t *variants, size_t cap, size_t *len)
+{
+    if (!s) return fail(SIM_EINVAL, "sim_last_plan: null handle");
+    if (len) *len = s->last_plan.size();
+    for (size_t i = 0; variants && i < cap && i < s->last_plan.size(); ++i) variants[i] = s->last_plan[i];
+    return SIM_OK;
+}

@@ -1,0 +1,618 @@
+// tile.cuh -- the register-resident tile machinery shared by the staged
+// pass kernel and the batched persistent kernel: register layouts, the
+// encoded gate ops, their application to a tile, and the host pass planner.
+// See staged.cu for the design.
+#pragma once
+
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace qsim {
+namespace {
+
+
+constexpr int kLow = 5;          // qubits 0..4 are local bits 0..4 of every tile
+constexpr int kThr = 256;        // threads per CTA
+constexpr int kThrBits = 8;
+
+enum StKind { SK_LAYOUT = 0, SK_DENSE, SK_ANTI, SK_XPERM, SK_DIAG, SK_PHASE, SK_NEG };
+
+template <typename R>
+struct __align__(16) StOp {
+    int32_t kind;      // StKind
+    int32_t arg;       // exchange ops: register bit of the target; SK_LAYOUT: new layout
+    uint32_t thr_c;    // thread bits that must be 1
+    int32_t plain;     // exchange ops: no condition of any kind
+    uint64_t out_c;    // global bits (outside the tile) that must be 1
+    uint64_t km_c;     // bit k: register k satisfies the register-bit conditions
+    uint64_t km_t;     // diagonal ops, bit k: the target bit of register k is 1
+    uint32_t thr_t;    // diagonal ops: thread bit of the target (0 if not a thread bit)
+    uint32_t pad;
+    uint64_t out_t;    // diagonal ops: global bit of the target (0 if inside the tile)
+    R m[8];            // A, B, C, D
+};
+
+// ---------------------------------------------------------------- layouts
+// VEC = 2 for complex64 (the I/O layout keeps local bit 0 in registers so a
+// thread loads two neighbouring amplitudes as one 16-byte vector), 1 for
+// complex128.  Layout 0 is the I/O layout; layouts 1.. put windows of RB
+// consecutive local bits into registers.
+__host__ __device__ constexpr int n_layouts(int M, int RB) { return 1 + (M - RB + RB - 1) / RB; }
+
+__host__ __device__ constexpr int reg_local(int M, int RB, int VEC, int l, int j)
+{
+    if (l == 0) return (VEC == 2) ? (j == 0 ? 0 : M - RB + j) : (M - RB + j);
+    int s = (VEC == 2 ? 1 : 0) + RB * (l - 1);
+    if (s > M - RB) s = M - RB;
+    return s + j;
+}
+
+__host__ __device__ constexpr bool is_reg(int M, int RB, int VEC, int l, int b)
+{
+    for (int j = 0; j < RB; ++j)
+        if (reg_local(M, RB, VEC, l, j) == b) return true;
+    return false;
+}
+
+__host__ __device__ constexpr int thr_local(int M, int RB, int VEC, int l, int i)
+{
+    int c = 0;
+    for (int b = 0; b < M; ++b)
+        if (!is_reg(M, RB, VEC, l, b)) {
+            if (c == i) return b;
+            ++c;
+        }
+    return -1;
+}
+
+__host__ __device__ constexpr int reg_part(int M, int RB, int VEC, int l, int k)
+{
+    int x = 0;
+    for (int j = 0; j < RB; ++j)
+        if ((k >> j) & 1) x |= 1 << reg_local(M, RB, VEC, l, j);
+    return x;
+}
+
+// shared-memory slot of local index x (bank-conflict-free for every layout)
+template <int RB, int VEC>
+__host__ __device__ constexpr int swz(int x)
+{
+    return (VEC == 2) ? (x ^ (((x >> (RB + 1)) & 7) << 1)) : (x ^ ((x >> RB) & 7));
+}
+
+struct TileGeom {
+    int n_outer;
+    int outer_pos[40];   // global qubit of outer bit i (ascending)
+    int hpos[16];        // global qubit of local bit kLow + i
+};
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+// ---------------------------------------------------------------- registers
+// Amplitudes of a thread.  complex64 keeps them as float2 packs along
+// register bit 0 so that two amplitude pairs go through one packed FP32x2
+// instruction (fma.rn.f32x2); complex128 keeps plain doubles.
+template <typename R, int RA> struct Regs;
+template <int RA> struct Regs<float, RA> {
+    // pack p = (amplitude 2p, amplitude 2p + 1) as one 64-bit register pair
+    uint64_t r[RA / 2], i[RA / 2];
+    __device__ __forceinline__ static float lo(uint64_t x)
+    {
+        float a, b;
+        asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+        return a;
+    }
+    __device__ __forceinline__ static float hi(uint64_t x)
+    {
+        float a, b;
+        asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+        return b;
+    }
+    __device__ __forceinline__ static uint64_t mk(float a, float b)
+    {
+        uint64_t x;
+        asm("mov.b64 %0, {%1,%2};" : "=l"(x) : "f"(a), "f"(b));
+        return x;
+    }
+    __device__ __forceinline__ float getr(int k) const { return (k & 1) ? hi(r[k >> 1]) : lo(r[k >> 1]); }
+    __device__ __forceinline__ float geti(int k) const { return (k & 1) ? hi(i[k >> 1]) : lo(i[k >> 1]); }
+    __device__ __forceinline__ void setr(int k, float v)
+    {
+        r[k >> 1] = (k & 1) ? mk(lo(r[k >> 1]), v) : mk(v, hi(r[k >> 1]));
+    }
+    __device__ __forceinline__ void seti(int k, float v)
+    {
+        i[k >> 1] = (k & 1) ? mk(lo(i[k >> 1]), v) : mk(v, hi(i[k >> 1]));
+    }
+    // both amplitudes of pack p at once
+    __device__ __forceinline__ void set2(int p, float r0, float i0, float r1, float i1)
+    {
+        r[p] = mk(r0, r1);
+        i[p] = mk(i0, i1);
+    }
+};
+template <int RA> struct Regs<double, RA> {
+    double r[RA], i[RA];
+    __device__ __forceinline__ double getr(int k) const { return r[k]; }
+    __device__ __forceinline__ double geti(int k) const { return i[k]; }
+    __device__ __forceinline__ void setr(int k, double v) { r[k] = v; }
+    __device__ __forceinline__ void seti(int k, double v) { i[k] = v; }
+};
+
+template <typename R>
+struct CoefS { R ar, ai, br, bi, cr, ci, dr, di; };
+
+// packed FP32x2 helpers (PTX fma / mul on 64-bit register pairs, sm_100+)
+__device__ __forceinline__ uint64_t pk(float2 v)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(v.x), "f"(v.y));
+    return r;
+}
+__device__ __forceinline__ float2 upk(uint64_t v)
+{
+    float2 r;
+    asm("mov.b64 {%0,%1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+__device__ __forceinline__ uint64_t pfma(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t pmul(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+struct PCoef { uint64_t ar, ai, nai, br, bi, nbi, cr, ci, nci, dr, di, ndi; };
+
+__device__ __forceinline__ PCoef make_pcoef(const CoefS<float> &c)
+{
+    PCoef p;
+    p.ar = pk(make_float2(c.ar, c.ar)); p.ai = pk(make_float2(c.ai, c.ai)); p.nai = pk(make_float2(-c.ai, -c.ai));
+    p.br = pk(make_float2(c.br, c.br)); p.bi = pk(make_float2(c.bi, c.bi)); p.nbi = pk(make_float2(-c.bi, -c.bi));
+    p.cr = pk(make_float2(c.cr, c.cr)); p.ci = pk(make_float2(c.ci, c.ci)); p.nci = pk(make_float2(-c.ci, -c.ci));
+    p.dr = pk(make_float2(c.dr, c.dr)); p.di = pk(make_float2(c.di, c.di)); p.ndi = pk(make_float2(-c.di, -c.di));
+    return p;
+}
+
+// two amplitude pairs at once: lanes x / y are independent pairs
+template <int KIND>
+__device__ __forceinline__ void pupd(uint64_t &lr, uint64_t &li, uint64_t &hr, uint64_t &hi, const PCoef &c)
+{
+    if (KIND == SK_DENSE) {
+        const uint64_t nlr = pfma(c.ar, lr, pfma(c.nai, li, pfma(c.br, hr, pmul(c.nbi, hi))));
+        const uint64_t nli = pfma(c.ar, li, pfma(c.ai, lr, pfma(c.br, hi, pmul(c.bi, hr))));
+        const uint64_t nhr = pfma(c.cr, lr, pfma(c.nci, li, pfma(c.dr, hr, pmul(c.ndi, hi))));
+        const uint64_t nhi = pfma(c.cr, li, pfma(c.ci, lr, pfma(c.dr, hi, pmul(c.di, hr))));
+        lr = nlr; li = nli; hr = nhr; hi = nhi;
+    } else if (KIND == SK_ANTI) {
+        const uint64_t nlr = pfma(c.br, hr, pmul(c.nbi, hi));
+        const uint64_t nli = pfma(c.br, hi, pmul(c.bi, hr));
+        const uint64_t nhr = pfma(c.cr, lr, pmul(c.nci, li));
+        const uint64_t nhi = pfma(c.cr, li, pmul(c.ci, lr));
+        lr = nlr; li = nli; hr = nhr; hi = nhi;
+    } else {
+        uint64_t t = lr; lr = hr; hr = t;
+        t = li; li = hi; hi = t;
+    }
+}
+
+template <int KIND, typename R>
+__device__ __forceinline__ void xupd(R &lr, R &li, R &hr, R &hi, const CoefS<R> &c)
+{
+    if (KIND == SK_DENSE) {
+        const R nlr = c.ar * lr - c.ai * li + (c.br * hr - c.bi * hi);
+        const R nli = c.ar * li + c.ai * lr + (c.br * hi + c.bi * hr);
+        const R nhr = c.cr * lr - c.ci * li + (c.dr * hr - c.di * hi);
+        const R nhi = c.cr * li + c.ci * lr + (c.dr * hi + c.di * hr);
+        lr = nlr; li = nli; hr = nhr; hi = nhi;
+    } else if (KIND == SK_ANTI) {
+        const R nlr = c.br * hr - c.bi * hi, nli = c.br * hi + c.bi * hr;
+        const R nhr = c.cr * lr - c.ci * li, nhi = c.cr * li + c.ci * lr;
+        lr = nlr; li = nli; hr = nhr; hi = nhi;
+    } else {  // SK_XPERM: exact exchange
+        R t = lr; lr = hr; hr = t;
+        t = li; li = hi; hi = t;
+    }
+}
+
+// Exchange op on register bit J.  PLAIN: no condition at all.  Otherwise the
+// amplitude pair (k, k | 2^J) is updated when bit k of `act` is set.
+template <int J, int KIND, bool PLAIN, typename R, int RA>
+__device__ __forceinline__ void xop(Regs<R, RA> &v, uint64_t act, const CoefS<R> &c)
+{
+    constexpr int RB = __builtin_ctz(RA);
+    if constexpr (J < RB) {
+        if constexpr (sizeof(R) == 4 && J >= 1) {
+            // packed: packs p and p | 2^(J-1) hold pairs (2p, 2p + 2^J) and (2p + 1, 2p + 1 + 2^J)
+            const PCoef pc = make_pcoef(c);
+#pragma unroll
+            for (int p = 0; p < RA / 2; ++p) {
+                if (p & (1 << (J - 1))) continue;
+                const int q = p | (1 << (J - 1));
+                if (PLAIN) {
+                    pupd<KIND>(v.r[p], v.i[p], v.r[q], v.i[q], pc);
+                } else {
+                    const bool a0 = (act >> (2 * p)) & 1, a1 = (act >> (2 * p + 1)) & 1;
+                    if (a0 && a1) {
+                        pupd<KIND>(v.r[p], v.i[p], v.r[q], v.i[q], pc);
+                    } else if (a0 || a1) {
+                        const int k = 2 * p + (a0 ? 0 : 1), k1 = 2 * q + (a0 ? 0 : 1);
+                        R lr = v.getr(k), li = v.geti(k), hr = v.getr(k1), hi = v.geti(k1);
+                        xupd<KIND, R>(lr, li, hr, hi, c);
+                        v.setr(k, lr); v.seti(k, li); v.setr(k1, hr); v.seti(k1, hi);
+                    }
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < RA; ++k) {
+                if (k & (1 << J)) continue;
+                const int k1 = k | (1 << J);
+                if (PLAIN || ((act >> k) & 1)) {
+                    R lr = v.getr(k), li = v.geti(k), hr = v.getr(k1), hi = v.geti(k1);
+                    xupd<KIND, R>(lr, li, hr, hi, c);
+                    v.setr(k, lr); v.seti(k, li); v.setr(k1, hr); v.seti(k1, hi);
+                }
+            }
+        }
+    }
+}
+
+template <int KIND, bool PLAIN, typename R, int RA>
+__device__ __forceinline__ void xdispatch(int j, Regs<R, RA> &v, uint64_t act, const CoefS<R> &c)
+{
+    switch (j) {
+    case 0: xop<0, KIND, PLAIN>(v, act, c); break;
+    case 1: xop<1, KIND, PLAIN>(v, act, c); break;
+    case 2: xop<2, KIND, PLAIN>(v, act, c); break;
+    case 3: xop<3, KIND, PLAIN>(v, act, c); break;
+    case 4: xop<4, KIND, PLAIN>(v, act, c); break;
+    case 5: xop<5, KIND, PLAIN>(v, act, c); break;
+    default: break;
+    }
+}
+
+template <int M, int RB, int VEC, int L, typename R, int RA>
+__device__ __forceinline__ void store_layout(Regs<R, RA> &v, R *sm, int tid)
+{
+    if constexpr (L < n_layouts(M, RB)) {
+        int tp = 0;
+#pragma unroll
+        for (int i = 0; i < kThrBits; ++i) tp |= ((tid >> i) & 1) << thr_local(M, RB, VEC, L, i);
+        const int tps = swz<RB, VEC>(tp);   // swz is linear over XOR: swz(tp ^ r) = swz(tp) ^ swz(r)
+        if constexpr (VEC == 2 && L == 0) {
+#pragma unroll
+            for (int k = 0; k < RA; k += 2) {
+                const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
+                *reinterpret_cast<float4 *>(sm + 2 * p) = make_float4(v.getr(k), v.geti(k), v.getr(k + 1), v.geti(k + 1));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < RA; ++k) {
+                const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
+                typename V2<R>::T t;
+                t.x = v.getr(k);
+                t.y = v.geti(k);
+                *reinterpret_cast<typename V2<R>::T *>(sm + 2 * p) = t;
+            }
+        }
+    }
+}
+
+template <int M, int RB, int VEC, int L, typename R, int RA>
+__device__ __forceinline__ void load_layout(Regs<R, RA> &v, const R *sm, int tid)
+{
+    if constexpr (L < n_layouts(M, RB)) {
+        int tp = 0;
+#pragma unroll
+        for (int i = 0; i < kThrBits; ++i) tp |= ((tid >> i) & 1) << thr_local(M, RB, VEC, L, i);
+        const int tps = swz<RB, VEC>(tp);   // swz is linear over XOR: swz(tp ^ r) = swz(tp) ^ swz(r)
+        if constexpr (VEC == 2 && L == 0) {
+#pragma unroll
+            for (int k = 0; k < RA; k += 2) {
+                const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
+                const float4 t = *reinterpret_cast<const float4 *>(sm + 2 * p);
+                v.set2(k >> 1, t.x, t.y, t.z, t.w);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < RA; ++k) {
+                const int p = tps ^ swz<RB, VEC>(reg_part(M, RB, VEC, L, k));
+                const typename V2<R>::T t = *reinterpret_cast<const typename V2<R>::T *>(sm + 2 * p);
+                v.setr(k, t.x);
+                v.seti(k, t.y);
+            }
+        }
+    }
+}
+
+// Sign flips (CZ, Z, CCZ) commute with every diagonal op, so they are
+// collected in a per-thread mask (bit k: negate register k) and applied only
+// before the next op that mixes registers (exchange, layout change, store).
+template <typename R, int RA>
+__device__ __forceinline__ void flush_neg(Regs<R, RA> &v, uint64_t &m)
+{
+    if (m) {
+#pragma unroll
+        for (int k = 0; k < RA; ++k)
+            if ((m >> k) & 1) { v.setr(k, -v.getr(k)); v.seti(k, -v.geti(k)); }
+        m = 0;
+    }
+}
+
+template <int M, int RB, int VEC, typename R, int RA>
+__device__ __forceinline__ void relayout(int from, int to, Regs<R, RA> &v, R *sm, int tid)
+{
+    __syncthreads();
+    switch (from) {
+    case 0: store_layout<M, RB, VEC, 0>(v, sm, tid); break;
+    case 1: store_layout<M, RB, VEC, 1>(v, sm, tid); break;
+    case 2: store_layout<M, RB, VEC, 2>(v, sm, tid); break;
+    case 3: store_layout<M, RB, VEC, 3>(v, sm, tid); break;
+    default: break;
+    }
+    __syncthreads();
+    switch (to) {
+    case 0: load_layout<M, RB, VEC, 0>(v, sm, tid); break;
+    case 1: load_layout<M, RB, VEC, 1>(v, sm, tid); break;
+    case 2: load_layout<M, RB, VEC, 2>(v, sm, tid); break;
+    case 3: load_layout<M, RB, VEC, 3>(v, sm, tid); break;
+    default: break;
+    }
+}
+
+// Apply an encoded op list to the registers of one tile (the whole body of a
+// pass between the global load and store).  base = global index bits of the
+// tile outside Q; sm = the tile's shared memory (2^M amplitudes).
+template <typename R, int M>
+__device__ __forceinline__ void apply_ops(Regs<R, (1 << (M - kThrBits))> &v, const StOp<R> *__restrict__ ops, int nops,
+                                          uint64_t base, int tid, R *sm)
+{
+    constexpr int VEC = (sizeof(R) == 4) ? 2 : 1;
+    constexpr int RB = M - kThrBits;
+    constexpr int RA = 1 << RB;
+    int layout = 0;
+    uint64_t negm = 0;
+    for (int p = 0; p < nops; ++p) {
+        const int kind = ops[p].kind;
+        const int arg = ops[p].arg;
+        if (kind == SK_LAYOUT) {
+            flush_neg(v, negm);
+            relayout<M, RB, VEC>(layout, arg, v, sm, tid);
+            layout = arg;
+            continue;
+        }
+        const bool tok = ((tid & ops[p].thr_c) == ops[p].thr_c) && ((base & ops[p].out_c) == ops[p].out_c);
+        CoefS<R> c;
+        c.ar = ops[p].m[0]; c.ai = ops[p].m[1]; c.br = ops[p].m[2]; c.bi = ops[p].m[3];
+        c.cr = ops[p].m[4]; c.ci = ops[p].m[5]; c.dr = ops[p].m[6]; c.di = ops[p].m[7];
+        if (kind <= SK_XPERM) {
+            flush_neg(v, negm);
+            const bool plain = ops[p].plain != 0;
+            const uint64_t act = tok ? ops[p].km_c : 0ull;
+            if (kind == SK_DENSE) {
+                if (plain) xdispatch<SK_DENSE, true>(arg, v, act, c);
+                else xdispatch<SK_DENSE, false>(arg, v, act, c);
+            } else if (kind == SK_ANTI) {
+                if (plain) xdispatch<SK_ANTI, true>(arg, v, act, c);
+                else xdispatch<SK_ANTI, false>(arg, v, act, c);
+            } else {
+                if (plain) xdispatch<SK_XPERM, true>(arg, v, act, c);
+                else xdispatch<SK_XPERM, false>(arg, v, act, c);
+            }
+        } else {
+            // diagonal: registers whose condition holds (km_c) and whose
+            // target bit is 1 (km_t); the thread / tile part of the target
+            // bit is ctb
+            const bool ctb = ((tid & ops[p].thr_t) != 0) || ((base & ops[p].out_t) != 0);
+            const uint64_t cond = tok ? ops[p].km_c : 0ull;
+            const uint64_t one = ctb ? cond : (cond & ops[p].km_t);
+            if (kind == SK_NEG) {
+                negm ^= one;
+            } else if (kind == SK_PHASE) {
+#pragma unroll
+                for (int k = 0; k < RA; ++k)
+                    if ((one >> k) & 1) {
+                        const R vr = v.getr(k), vi = v.geti(k);
+                        v.setr(k, c.dr * vr - c.di * vi);
+                        v.seti(k, c.dr * vi + c.di * vr);
+                    }
+            } else {
+#pragma unroll
+                for (int k = 0; k < RA; ++k)
+                    if ((cond >> k) & 1) {
+                        const bool tb = (one >> k) & 1;
+                        const R fr = tb ? c.dr : c.ar, fi = tb ? c.di : c.ai;
+                        const R vr = v.getr(k), vi = v.geti(k);
+                        v.setr(k, fr * vr - fi * vi);
+                        v.seti(k, fr * vi + fi * vr);
+                    }
+            }
+        }
+    }
+    flush_neg(v, negm);
+}
+
+// ---------------------------------------------------------------- host planner
+struct Pass {
+    std::vector<int> high;      // global qubits of local bits kLow .. M-1
+    std::vector<int> members;   // gate indices (a valid order)
+};
+
+// Greedy passes: scan the remaining gates in order; a gate joins the pass if
+// it commutes with every gate skipped before it and its non-diagonal qubits
+// fit in Q (adding up to M - kLow high qubits).
+std::vector<Pass> form_passes(const std::vector<SGate> &g, int n, int M)
+{
+    std::vector<Pass> passes;
+    std::vector<char> done(g.size(), 0);
+    const uint64_t low = (1ull << kLow) - 1ull;
+    const int cap = M - kLow;
+    size_t first = 0;
+    while (first < g.size()) {
+        Pass ps;
+        uint64_t qmask = low;
+        uint64_t bx = 0, bd = 0;      // qubits where skipped gates act non-diagonally / diagonally
+        for (size_t i = first; i < g.size(); ++i) {
+            if (done[i]) continue;
+            const uint64_t x = g[i].xq(), d = g[i].dq();
+            const bool free_of_skipped = ((x & (bx | bd)) == 0) && ((d & bx) == 0);
+            bool ok = false;
+            if (free_of_skipped) {
+                const uint64_t add = x & ~qmask;
+                if ((int)ps.high.size() + __builtin_popcountll(add) <= cap) {
+                    ok = true;
+                    for (int q = 0; q < n; ++q)
+                        if ((add >> q) & 1) { ps.high.push_back(q); qmask |= 1ull << q; }
+                }
+            }
+            if (ok) {
+                ps.members.push_back((int)i);
+                done[i] = 1;
+            } else {
+                bx |= x;
+                bd |= d;
+            }
+        }
+        // fill the tile with unused qubits (lowest first)
+        for (int q = kLow; q < n && (int)ps.high.size() < cap; ++q)
+            if (!((qmask >> q) & 1)) { ps.high.push_back(q); qmask |= 1ull << q; }
+        passes.push_back(ps);
+        while (first < g.size() && done[first]) ++first;
+    }
+    return passes;
+}
+
+template <typename R>
+struct PlanBuilder {
+    int n, M, RB, VEC;
+    std::vector<StOp<R>> ops;
+    std::vector<int> order;       // circuit index of each emitted gate op
+    int layout_changes = 0;
+
+    int local_of(const Pass &ps, int q) const
+    {
+        if (q < kLow) return q;
+        for (size_t i = 0; i < ps.high.size(); ++i)
+            if (ps.high[i] == q) return kLow + (int)i;
+        return -1;
+    }
+    int reg_of(int l, int b) const
+    {
+        for (int j = 0; j < RB; ++j)
+            if (reg_local(M, RB, VEC, l, j) == b) return j;
+        return -1;
+    }
+    int thr_of(int l, int b) const
+    {
+        for (int i = 0; i < kThrBits; ++i)
+            if (thr_local(M, RB, VEC, l, i) == b) return i;
+        return -1;
+    }
+
+    void emit_gate(const Pass &ps, const SGate &g, int layout)
+    {
+        StOp<R> o;
+        memset(&o, 0, sizeof o);
+        uint32_t reg_c = 0, reg_t = 0;
+        for (int q = 0; q < n; ++q) {
+            if (!((g.ctrl >> q) & 1)) continue;
+            const int b = local_of(ps, q);
+            if (b < 0) o.out_c |= 1ull << q;
+            else if (reg_of(layout, b) >= 0) reg_c |= 1u << reg_of(layout, b);
+            else o.thr_c |= 1u << thr_of(layout, b);
+        }
+        for (int k = 0; k < 8; ++k) o.m[k] = (R)g.m[k];
+        const int bt = local_of(ps, g.target);
+        if (g.op == OP_DIAG || g.op == OP_DIAG_HI) {
+            if (bt < 0) o.out_t = 1ull << g.target;
+            else if (reg_of(layout, bt) >= 0) reg_t = 1u << reg_of(layout, bt);
+            else o.thr_t = 1u << thr_of(layout, bt);
+            const bool neg = g.m[6] == -1.0 && g.m[7] == 0.0;
+            o.kind = (g.op == OP_DIAG) ? SK_DIAG : (neg ? SK_NEG : SK_PHASE);
+        } else {
+            o.kind = (g.op == OP_DENSE) ? SK_DENSE : (g.op == OP_ANTIDIAG) ? SK_ANTI : SK_XPERM;
+            o.arg = reg_of(layout, bt);
+        }
+        const int RA = 1 << RB;
+        for (int k = 0; k < RA; ++k) {
+            if (((uint32_t)k & reg_c) == reg_c) o.km_c |= 1ull << k;
+            if ((uint32_t)k & reg_t) o.km_t |= 1ull << k;
+        }
+        o.plain = (reg_c == 0 && o.thr_c == 0 && o.out_c == 0) ? 1 : 0;
+        ops.push_back(o);
+    }
+
+    void emit_layout(int l)
+    {
+        ++layout_changes;
+        StOp<R> o;
+        memset(&o, 0, sizeof o);
+        o.kind = SK_LAYOUT;
+        o.arg = l;
+        ops.push_back(o);
+    }
+
+    // order the pass's gates (respecting non-commuting pairs) so that
+    // consecutive exchange gates share a layout; returns the op count
+    int schedule(const Pass &ps, const std::vector<SGate> &g)
+    {
+        const size_t P = ps.members.size();
+        const size_t start = ops.size();
+        std::vector<int> indeg(P, 0);
+        std::vector<std::vector<int>> succ(P);
+        for (size_t a = 0; a < P; ++a)
+            for (size_t b = a + 1; b < P; ++b)
+                if (!commute(g[ps.members[a]], g[ps.members[b]])) {
+                    succ[a].push_back((int)b);
+                    indeg[b]++;
+                }
+        std::vector<char> emitted(P, 0);
+        const int NL = n_layouts(M, RB);
+        int layout = 0;
+        size_t left = P;
+        auto fits = [&](int i, int l) {
+            const SGate &s = g[ps.members[i]];
+            if (!s.xq()) return true;
+            return reg_of(l, local_of(ps, s.target)) >= 0;
+        };
+        while (left) {
+            int pick = -1;
+            for (size_t i = 0; i < P && pick < 0; ++i)
+                if (!emitted[i] && indeg[i] == 0 && fits((int)i, layout)) pick = (int)i;
+            if (pick < 0) {
+                int best = -1, bestc = -1;
+                for (int l = 0; l < NL; ++l) {
+                    if (l == layout) continue;
+                    int c = 0;
+                    for (size_t i = 0; i < P; ++i)
+                        if (!emitted[i] && indeg[i] == 0 && fits((int)i, l)) ++c;
+                    if (c > bestc) { bestc = c; best = l; }
+                }
+                emit_layout(best);
+                layout = best;
+                continue;
+            }
+            emit_gate(ps, g[ps.members[pick]], layout);
+            order.push_back(g[ps.members[pick]].orig);
+            emitted[pick] = 1;
+            --left;
+            for (int s2 : succ[pick]) indeg[s2]--;
+        }
+        if (layout != 0) emit_layout(0);
+        return (int)(ops.size() - start);
+    }
+};
+
+}  // namespace
+}  // namespace qsim

@@ -335,3 +335,152 @@ class State:
 
     def synchronize(self):
         sim_synchronize(self.h)
+
+
+# ---------------------------------------------------------------- batches
+_sig("sim_batch_create", [_i32, P, P, P, P, ctypes.POINTER(P)])
+_sig("sim_batch_run", [P, P, _i32])
+_sig("sim_batch_info", [P, P, P, P, P, P])
+_sig("sim_batch_destroy", [P])
+
+
+class Batch:
+    """Many independent circuits, each from |0...0>, returning <sum_i Z_i>
+    per circuit (one persistent launch replayed from a CUDA graph)."""
+
+    def __init__(self, n_qubits, offsets, gates, stream: int = 0):
+        self.n = np.ascontiguousarray(n_qubits, dtype=np.int32)
+        self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        sg = np.ascontiguousarray(to_sim_gates(gates) if gates.dtype != SIM_GATE_DTYPE else gates,
+                                  dtype=SIM_GATE_DTYPE)
+        h = P()
+        check(_lib.sim_batch_create(len(self.n), self.n.ctypes.data_as(P), self.offsets.ctypes.data_as(P),
+                                    sg.ctypes.data_as(P), P(stream or CUDA_STREAM_LEGACY), ctypes.byref(h)))
+        self.h = h.value
+
+    def run(self) -> np.ndarray:
+        out = np.zeros(len(self.n), dtype=np.float64)
+        check(_lib.sim_batch_run(P(self.h), out.ctypes.data_as(P), 0))
+        return out
+
+    def info(self):
+        items, passes, ops, nbytes = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        grid = ctypes.c_int()
+        check(_lib.sim_batch_info(P(self.h), ctypes.byref(items), ctypes.byref(passes), ctypes.byref(ops),
+                                  ctypes.byref(nbytes), ctypes.byref(grid)))
+        return {"items": items.value, "passes": passes.value, "ops": ops.value, "device_bytes": nbytes.value,
+                "grid": grid.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(_lib.sim_batch_destroy(P(self.h)))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- cost model
+_sig("sim_mlp_param_count", [_i32, _i32])
+_sig("sim_mlp_create", [_i32, _i32, P, ctypes.POINTER(P)])
+_sig("sim_mlp_destroy", [P])
+_sig("sim_mlp_set_params", [P, P])
+_sig("sim_mlp_get_params", [P, P])
+_sig("sim_mlp_forward", [P, P, ctypes.c_int64, P, _i32])
+_sig("sim_mlp_loss_grad", [P, P, P, ctypes.c_int64, _i32, P, P])
+_sig("sim_mlp_train", [P, P, P, ctypes.c_int64, _i32, ctypes.c_float, _i32, P])
+_sig("sim_set_cost_model", [P, P])
+_sig("sim_plan_features", [_i32, _i32, P, _sz, _i32, P])
+_sig("sim_last_plan", [P, P, _sz, P])
+
+N_FEATURES = 16
+N_VARIANTS = 7
+VARIANTS = ["per_gate", "staged:12", "staged:13", "fused:3", "fused:4", "fused:5", "fused:6"]
+
+
+def variant_opts(v: int) -> sim_plan_opts:
+    name, _, num = VARIANTS[v].partition(":")
+    if name == "fused":
+        return plan_opts("fused", fuse_k=int(num))
+    return plan_opts(name, tile_qubits=int(num or 0))
+
+
+def sim_plan_features(n: int, dtype: int, sim_gates: np.ndarray, variant: int):
+    """Feature row of the cost model, or None if the variant is not feasible."""
+    g = np.ascontiguousarray(sim_gates, dtype=SIM_GATE_DTYPE)
+    out = np.zeros(N_FEATURES, dtype=np.float32)
+    rc = _lib.sim_plan_features(n, dtype, g.ctypes.data_as(P), len(g), variant, out.ctypes.data_as(P))
+    if rc == SIM_EUNSUPPORTED:
+        return None
+    check(rc)
+    return out
+
+
+class MLP:
+    """The plan cost model (parameters live on the GPU)."""
+
+    def __init__(self, d_in: int = N_FEATURES, hidden: int = 64, stream: int = 0):
+        self.d_in, self.hidden = d_in, hidden
+        self.n_params = _lib.sim_mlp_param_count(d_in, hidden)
+        h = P()
+        check(_lib.sim_mlp_create(d_in, hidden, P(stream or CUDA_STREAM_LEGACY), ctypes.byref(h)))
+        self.h = h.value
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.n_params
+        check(_lib.sim_mlp_set_params(P(self.h), t.ctypes.data_as(P)))
+
+    def get_params(self):
+        t = np.zeros(self.n_params, dtype=np.float32)
+        check(_lib.sim_mlp_get_params(P(self.h), t.ctypes.data_as(P)))
+        return t
+
+    def forward(self, X):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.zeros(len(X), dtype=np.float32)
+        check(_lib.sim_mlp_forward(P(self.h), X.ctypes.data_as(P), len(X), y.ctypes.data_as(P), 0))
+        return y
+
+    def loss_grad(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        loss = ctypes.c_float()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        check(_lib.sim_mlp_loss_grad(P(self.h), X.ctypes.data_as(P), T.ctypes.data_as(P), len(X), 0,
+                                     ctypes.byref(loss), g.ctypes.data_as(P)))
+        return loss.value, g
+
+    def train(self, X, T, steps: int, lr: float):
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        T = np.ascontiguousarray(T, dtype=np.float32)
+        loss = ctypes.c_float()
+        check(_lib.sim_mlp_train(P(self.h), X.ctypes.data_as(P), T.ctypes.data_as(P), len(X), steps,
+                                 ctypes.c_float(lr), 0, ctypes.byref(loss)))
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            check(_lib.sim_mlp_destroy(P(self.h)))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sim_set_cost_model(h: int, mlp):
+    check(_lib.sim_set_cost_model(P(h), P(mlp.h if mlp is not None else None)))
+
+
+def sim_last_plan(h: int):
+    n = ctypes.c_size_t()
+    check(_lib.sim_last_plan(P(h), None, 0, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.int32)
+    check(_lib.sim_last_plan(P(h), out.ctypes.data_as(P), n.value, ctypes.byref(n)))
+    return out

@@ -98,3 +98,25 @@ def test_fused_haar_cz_30q_vs_c128(gsim):
     assert 1.0 - abs(ip.item()) ** 2 / a.norm2() <= 1e-6
     a.close()
     b.close()
+
+
+def test_block_planner_handles_gates_wider_than_k_cpu():
+    """A SWAP with two controls lowers to an X with three controls (4 qubits):
+    wider than a k = 3 block, it must become its own per-gate step."""
+    from paper_1805_00988_gb300 import sim
+    g = C.concat([C.gate("swap", 0, target2=1, controls=(2, 3)), C.gate("h", 4),
+                  C.random_gates(10, 200, seed=3)])
+    blocks = sim.sim_plan_describe(10, 0, sim.to_sim_gates(g), sim.plan_opts("fused", fuse_k=3))[0]
+    assert blocks >= 2
+
+
+@pytest.mark.gpu
+def test_fused_wide_gates(gsim, orc):
+    n = 12
+    g = C.concat([C.gate("swap", 0, target2=5, controls=(2, 9)), C.random_gates(n, 100, seed=8)])
+    st = gsim.State(n, "c64")
+    psi = C.random_state(n, seed=2)
+    st.load(psi)
+    st.apply(g, plan="fused", fuse_k=3)
+    check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))
+    st.close()
