@@ -87,8 +87,8 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
         st.tile_qubits = o.tile_qubits;
         return apply_circuit_staged(s, gates, n_gates, st);
     }
-    // windows of about three layers of single-qubit gates
-    const size_t W = (size_t)std::max(64, 3 * s->n);
+    // windows of about eight layers of single-qubit gates
+    const size_t W = (size_t)std::max(64, 8 * s->n);
     std::vector<Window> win;
     for (size_t f = 0; f < n_gates; f += W) win.push_back(Window{f, std::min(W, n_gates - f)});
     std::vector<float> rows;

@@ -1,0 +1,69 @@
+"""The learned plan: a cost model trained on this GPU's own timings picks a
+plan variant per window.  Whatever it picks, the state must match the
+oracle; and its plans are judged against the fixed variants it replaces."""
+import numpy as np
+import pytest
+
+from paper_1805_00988_gb300 import circuits as C
+
+
+@pytest.fixture(scope="module")
+def trained():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1805_00988_gb300 import costmodel, sim
+    X, T, meta = costmodel.collect(n_list=(18, 20, 22), reps=3, max_windows=3)
+    m, loss = costmodel.train(X, T, steps=2000)
+    return sim, costmodel, m, X, T, meta
+
+
+def check(orc, got, ref):
+    got = got.astype(np.complex128)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+    assert orc.infidelity(ref, got) <= 1e-6
+
+
+@pytest.mark.gpu
+def test_model_fits_its_timings(trained):
+    sim, costmodel, m, X, T, meta = trained
+    pred = m.forward(X)
+    # log-time RMSE well under the spread of the targets
+    assert np.sqrt(np.mean((pred - T) ** 2)) < 0.5 * np.std(T)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("fam", ["qft", "haar_cz", "random"])
+def test_learned_plan_matches_oracle(trained, orc, fam):
+    sim = trained[0]
+    n = 18
+    g = {"qft": C.qft(n), "haar_cz": C.haar_cz(n, 12, seed=4), "random": C.random_gates(n, 400, seed=5)}[fam]
+    st = sim.State(n, "c64")
+    sim.sim_set_cost_model(st.h, trained[2])
+    psi = C.random_state(n, seed=3)
+    st.load(psi)
+    st.apply(g, plan="learned")
+    assert len(sim.sim_last_plan(st.h)) >= 1
+    check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))
+    st.close()
+
+
+@pytest.mark.gpu
+def test_learned_plan_gain_over_fixed_variants(trained):
+    """On held-out circuits the learned plan is close to the best fixed
+    variant and well ahead of the worst (what the model buys over guessing)."""
+    sim, costmodel, m = trained[0], trained[1], trained[2]
+    n = 22
+    st = sim.State(n, "c64")
+    sim.sim_set_cost_model(st.h, m)
+    rows = []
+    for g in (C.haar_cz(n, 16, seed=99), C.qft(n), C.random_gates(n, 300, seed=98)):
+        sg = sim.to_sim_gates(g)
+        t_learned = costmodel.time_window(st, sg, sim.plan_opts("learned"), 3)
+        fixed = {sim.VARIANTS[v]: costmodel.time_window(st, sg, sim.variant_opts(v), 3)
+                 for v in range(sim.N_VARIANTS)}
+        rows.append((t_learned, min(fixed.values()), max(fixed.values())))
+    st.close()
+    for t_l, best, worst in rows:
+        assert t_l <= 1.5 * best + 0.05, rows
+    assert sum(r[0] for r in rows) < sum(r[2] for r in rows)
