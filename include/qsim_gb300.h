@@ -251,6 +251,26 @@ int sim_num_kernel_classes(void);
  *   that are not bound by HBM. */
 int sim_measure_fma_peak(int which, double *tflops);
 
+/* sim_norm_noalloc: sum_j |a_j|^2 in FP64 of a caller's state -- 2^n
+ *   amplitudes of dtype at dev_state (device memory, 16-byte aligned) --
+ *   enqueued on `stream` (NULL = the legacy default stream); the result goes to
+ *   *out (host memory) and the call synchronises that stream.  The paper has
+ *   no counterpart of this entry point: it exists for callers that cannot
+ *   allocate device memory when they need a norm (for example while another
+ *   allocator, such as a framework's caching allocator or a memory pool sized
+ *   to the whole GPU, holds all free device memory, or where entering the
+ *   device allocator, which can synchronise the device, is not acceptable).
+ *   It allocates nothing: no cudaMalloc, no cudaFree, no allocating library
+ *   routine.  Its only scratch is a fixed 1217-double (9,736-byte) array
+ *   compiled into the library, which every GPU that loads the library holds
+ *   until the process exits.  All calls share that array: calls that overlap
+ *   on the GPU race and must be serialised by the caller; each call overwrites
+ *   every slot it reads, so nothing needs clearing between calls.  The first
+ *   call on a device looks up the array's device address (once per device,
+ *   with that device current); make that first call before any stream
+ *   capture.  n must be in [1, 34] (SIM_EINVAL beyond, with a message). */
+int sim_norm_noalloc(const void *dev_state, int n, int dtype, void *stream, double *out);
+
 /* Thread-local description of the last failure (empty string if none). */
 const char *sim_last_error(void);
 /* Library version string. */
