@@ -176,6 +176,17 @@ def run_reference(args, rank, world):
 
 
 # ----------------------------------------------------------------------------- GPU leg
+def load_cost_model(sim):
+    """The plan cost model trained on this machine's GB300 (parameters shipped
+    with the package); None when absent (the learned plan then falls back to
+    the greedy tile planner)."""
+    from paper_1805_00988_gb300 import costmodel
+    if not os.path.exists(costmodel.DEFAULT_PATH):
+        return None, {"cost_model": "absent: greedy tile planner used"}
+    m, info = costmodel.load()
+    return m, {"cost_model": info}
+
+
 def infidelity_torch(a, b, chunk=1 << 26):
     """1 - |<a|b>|^2 / (<a|a><b|b>) in FP64 over two CUDA tensors (chunked)."""
     import torch
@@ -213,6 +224,9 @@ def run_ours(args, rank, world, local_rank):
     opts = sim.plan_opts(plan, fuse_k=args.fuse_k, tile_qubits=args.tile)
     st = sim.State(n, "c64", device=dev)
     stream = st.stream
+    model, model_info = load_cost_model(sim)
+    if model is not None:
+        sim.sim_set_cost_model(st.h, model)
     shot_buf = torch.empty(shots, dtype=torch.int64, device=dev)
 
     def step():
@@ -303,16 +317,25 @@ def run_ours(args, rank, world, local_rank):
             "hbm_gbs": world * step_bytes / (ms_per_step / 1e3) / 1e9,
             "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
             "kernels": kernels, "norm": nrm, "expect_z_sum": ez}
+    line["config"].update(model_info if plan == "learned" else {})
+    if plan == "learned":
+        line["config"]["learned_windows"] = [sim.VARIANTS[v] for v in sim.sim_last_plan(st.h)]
 
     # plan variants on the same workload, each with its infidelity
     if args.variants and rank == 0:
         line["variants"] = run_variants(args, sim, C, gates, sg, dev, st, peaks)
 
+    if args.extras and rank == 0:
+        st.close()
+        st = None
+        line["extras"] = run_extras(args, sim, C, dev, model)
+
     if rank == 0 and world == 1 and args.cpu_baseline:
         rate, sample, cores, done, el = oracle_sample(gates, n, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "gates/s", "cores": cores, "kind": "oracle",
                                 "sample": sample, "seconds": el}
-    st.close()
+    if st is not None:
+        st.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -363,20 +386,106 @@ def run_variants(args, sim, C, gates, sg, dev, st_c64, peaks):
     return out
 
 
+def _timed(fn, stream, reps):
+    import torch
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        best = t if best is None else min(best, t)
+    return best
+
+
+def run_extras(args, sim, C, dev, model):
+    """The other workloads of the hot path, one line each (device time, best
+    of a few runs after a warm run)."""
+    import torch
+    out = {}
+    # the paper's benchmark circuit: QFT at 28 qubits from a random basis state, per-gate kernels
+    n = 28
+    j = C.random_basis_index(n, seed=SEED)
+    g = sim.to_sim_gates(C.qft(n))
+    for dt in ("c64", "c128"):
+        st = sim.State(n, dt, device=dev)
+        res = {}
+        for plan in ("per_gate", "staged"):
+            o = sim.plan_opts(plan)
+
+            def run():
+                sim.sim_set_basis_state(st.h, j)
+                sim.sim_apply_circuit(st.h, g, o)
+            run()
+            ms = _timed(run, st.stream, 2)
+            res[plan] = {"ms": ms, "gates_per_s": len(g) / (ms / 1e3)}
+        out["qft28_" + dt] = res
+        st.close()
+    # batched variational circuits: 4096 circuits of 8..20 qubits, 4..12 layers, one graph launch
+    ns, offs, bg = C.variational(4096, 8, 20, 4, 12, seed=SEED)
+    t0 = time.perf_counter()
+    b = sim.Batch(ns, offs, bg)
+    plan_s = time.perf_counter() - t0
+    b.run()
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        b.run()
+        ts.append(time.perf_counter() - t0)
+    info = b.info()
+    b.close()
+    tb = min(ts)
+    out["batched_4096"] = {"ms": tb * 1e3, "circuits_per_s": 4096 / tb, "gates_per_s": len(bg) / tb,
+                           "gates": int(len(bg)), "host_plan_s": plan_s, "work_items": info["items"],
+                           "persistent_ctas": info["grid"], "note": "wall time of sim_batch_run (graph launch + "
+                           "readback of 4096 <sum Z> values)"}
+    # 33 qubits, depth 24 (64 GiB complex64): learned plan vs the greedy tile planner, then 10^6 shots
+    if args.c5:
+        n5 = 33
+        g5 = sim.to_sim_gates(C.haar_cz(n5, 24, seed=SEED))
+        st = sim.State(n5, "c64", device=dev)
+        res = {}
+        for name, o in (("greedy_staged13", sim.plan_opts("staged", tile_qubits=13)),
+                        ("learned", sim.plan_opts("learned"))):
+            if name == "learned":
+                sim.sim_set_cost_model(st.h, model)
+
+            def run():
+                sim.sim_set_basis_state(st.h, 0)
+                sim.sim_apply_circuit(st.h, g5, o)
+            run()
+            ms = _timed(run, st.stream, 1)
+            res[name] = {"ms": ms, "gates_per_s": len(g5) / (ms / 1e3)}
+        res["learned"]["windows"] = [sim.VARIANTS[v] for v in sim.sim_last_plan(st.h)]
+        shots = torch.empty(1_000_000, dtype=torch.int64, device=dev)
+        ms = _timed(lambda: sim.sim_sample(st.h, 1_000_000, 7, shots.data_ptr(), out_on_device=True), st.stream, 2)
+        res["sample_1e6_shots_ms"] = ms
+        res["norm"] = st.norm2()
+        out["haar_cz_33q_depth24"] = res
+        st.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--plan", default="staged")
+    ap.add_argument("--plan", default="learned")
     ap.add_argument("--fuse-k", type=int, default=5)
     ap.add_argument("--tile", type=int, default=0, help="tile qubits of the staged plan (0 = library default)")
     ap.add_argument("--qubits", type=int, default=N_QUBITS)
     ap.add_argument("--depth", type=int, default=DEPTH)
     ap.add_argument("--shots", type=int, default=SHOTS)
     ap.add_argument("--no-variants", dest="variants", action="store_false")
-    ap.add_argument("--variant-plans", default="per_gate,staged")
+    ap.add_argument("--variant-plans", default="per_gate,staged:13,fused:4,learned")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--no-c5", dest="c5", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()

