@@ -239,6 +239,7 @@ int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, c
  * sim_launch_count: kernels this handle has launched since creation. */
 int sim_profile_enable(sim_t s, int on);
 int sim_profile_read(sim_t s, int max_classes, uint64_t *launches, double *total_ms, double *alg_bytes,
+                     double *alg_flops,
                      int reset);
 int sim_launch_count(sim_t s, uint64_t *out);
 const char *sim_kernel_class_name(int k);

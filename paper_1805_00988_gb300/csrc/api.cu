@@ -48,10 +48,10 @@ static cudaEvent_t pool_event(qsim_state *s)
     return e;
 }
 
-void launch_begin(qsim_state *s, int cls, double alg_bytes)
+void launch_begin(qsim_state *s, int cls, double alg_bytes, double alg_flops)
 {
     if (!s->profiling) return;
-    qsim_state::Mark m{cls, alg_bytes, pool_event(s), pool_event(s)};
+    qsim_state::Mark m{cls, alg_bytes, alg_flops, pool_event(s), pool_event(s)};
     if (m.a) cudaEventRecord(m.a, s->stream);
     s->marks.push_back(m);
 }
@@ -389,7 +389,8 @@ int sim_profile_enable(sim_t s, int on)
     return SIM_OK;
 }
 
-int sim_profile_read(sim_t s, int max_classes, uint64_t *launches, double *total_ms, double *alg_bytes, int reset)
+int sim_profile_read(sim_t s, int max_classes, uint64_t *launches, double *total_ms, double *alg_bytes,
+                     double *alg_flops, int reset)
 {
     if (int rc = check_handle(s)) return rc;
     QSIM_CUDA(cudaStreamSynchronize(s->stream));
@@ -399,6 +400,7 @@ int sim_profile_read(sim_t s, int max_classes, uint64_t *launches, double *total
             s->prof_launches[m.cls]++;
             s->prof_ms[m.cls] += ms;
             s->prof_bytes[m.cls] += m.bytes;
+            s->prof_flops[m.cls] += m.flops;
         }
     }
     s->marks.clear();
@@ -407,9 +409,10 @@ int sim_profile_read(sim_t s, int max_classes, uint64_t *launches, double *total
         if (launches) launches[k] = s->prof_launches[k];
         if (total_ms) total_ms[k] = s->prof_ms[k];
         if (alg_bytes) alg_bytes[k] = s->prof_bytes[k];
+        if (alg_flops) alg_flops[k] = s->prof_flops[k];
     }
     if (reset) {
-        for (int k = 0; k < KC_COUNT; ++k) { s->prof_launches[k] = 0; s->prof_ms[k] = 0; s->prof_bytes[k] = 0; }
+        for (int k = 0; k < KC_COUNT; ++k) { s->prof_launches[k] = 0; s->prof_ms[k] = 0; s->prof_bytes[k] = 0; s->prof_flops[k] = 0; }
     }
     return SIM_OK;
 }

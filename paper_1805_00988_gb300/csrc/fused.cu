@@ -451,7 +451,8 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
             a.nq = KQ;
             for (int i = 0; i < KQ; ++i) a.pos[i] = pos[b][i];
             a.rows = rows;
-            launch_begin(s, KC_FUSED, 2.0 * (double)s->bytes);
+            // tensor-core flops: three real GEMMs [rows x K] x [K x K] (3xTF32)
+            launch_begin(s, KC_FUSED, 2.0 * (double)s->bytes, 3.0 * 2.0 * (double)rows * K * K);
             k_fused_apply<KQ><<<(unsigned)((rows + kRows - 1) / kRows), kRows, sma, s->stream>>>(
                 (float *)s->amps, (const float *)(scratch + o_b) + b * 2 * (size_t)K * K, a, s->dev_status);
             rc = launch_end(s, "fused apply");

@@ -367,7 +367,11 @@ static int launch_pair_impl(qsim_state *s, const PairGate &g, uint64_t cm)
     // amplitudes the gate must change: 2 per base (1 for a phase on |1>), read + written
     const double amp = (s->dtype == SIM_C128) ? 16.0 : 8.0;
     const double touched = (double)bases * ((g.op == OP_DIAG_HI) ? 1.0 : 2.0);
-    launch_begin(s, op_class(g.op), 2.0 * touched * amp);
+    double flops = 0.0;
+    if (g.op == OP_DENSE) flops = 16.0 * touched;
+    else if (g.op == OP_DIAG || g.op == OP_ANTIDIAG) flops = 6.0 * touched;
+    else if (g.op == OP_DIAG_HI) flops = (g.m[6] == -1.0 && g.m[7] == 0.0) ? 0.0 : 6.0 * touched;
+    launch_begin(s, op_class(g.op), 2.0 * touched * amp, flops);
     if (s->dtype == SIM_C128) {
         a.n_items = bases;
         dispatch_split<double, 1, 2>(s, g.op, a, make_coef<double>(g.m));

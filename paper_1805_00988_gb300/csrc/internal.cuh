@@ -71,13 +71,14 @@ struct qsim_state {
     // instrumentation
     uint64_t launches = 0;
     bool profiling = false;
-    struct Mark { int cls; double bytes; cudaEvent_t a, b; };
+    struct Mark { int cls; double bytes, flops; cudaEvent_t a, b; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> event_pool;
     size_t event_next = 0;
     uint64_t prof_launches[qsim::KC_COUNT] = {0};
     double prof_ms[qsim::KC_COUNT] = {0};
     double prof_bytes[qsim::KC_COUNT] = {0};
+    double prof_flops[qsim::KC_COUNT] = {0};
 };
 
 namespace qsim {
@@ -88,7 +89,11 @@ constexpr int kRedThreads = 256;
 // Launch bracketing: call begin() before and end() after each kernel launch.
 // alg_bytes = the bytes the launch must move at minimum (what the operation
 // reads and writes of the state), used for roofline accounting.
-void launch_begin(qsim_state *s, int cls, double alg_bytes = 0.0);
+void launch_begin(qsim_state *s, int cls, double alg_bytes = 0.0, double alg_flops = 0.0);
+struct SGate;
+// algorithmic floating-point operations of one lowered gate on an n-qubit state
+// (8 per complex multiply-add; sign flips and moves count 0)
+double sgate_flops(const SGate &g, int n);
 int launch_end(qsim_state *s, const char *what);
 
 // ---------------------------------------------------------------- per-gate kernels

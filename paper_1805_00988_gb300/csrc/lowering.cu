@@ -1,4 +1,5 @@
 // lowering.cu -- circuit gates to the planners' gate form.
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -35,6 +36,19 @@ void lower_gates(const sim_gate *gates, size_t n_gates, std::vector<SGate> *out)
         SGate g{p.op, p.target, cm, {}, (int)k};
         memcpy(g.m, p.m, sizeof g.m);
         out->push_back(g);
+    }
+}
+
+double sgate_flops(const SGate &g, int n)
+{
+    const double amps = std::ldexp(1.0, n - __builtin_popcountll(g.ctrl));
+    switch (g.op) {
+    case OP_DENSE: return 16.0 * amps;                 // two complex MACs per amplitude
+    case OP_ANTIDIAG: return 6.0 * amps;               // one complex multiply per amplitude
+    case OP_DIAG: return 6.0 * amps;
+    case OP_DIAG_HI:                                   // only the |1> half; a sign flip is a move
+        return (g.m[6] == -1.0 && g.m[7] == 0.0) ? 0.0 : 3.0 * amps;
+    default: return 0.0;                               // exchanges
     }
 }
 

@@ -107,7 +107,7 @@ k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
 }
 
 template <typename R, int M>
-int launch_staged(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &geo)
+int launch_staged(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &geo, double flops)
 {
     const size_t smem = ((size_t)1 << M) * 2 * sizeof(R);
     static bool attr_set = false;   // per template instance
@@ -116,7 +116,7 @@ int launch_staged(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &
         attr_set = true;
     }
     const uint64_t tiles = 1ull << (s->n - M);
-    launch_begin(s, KC_STAGED, 2.0 * (double)s->bytes);
+    launch_begin(s, KC_STAGED, 2.0 * (double)s->bytes, flops);
     k_staged<R, M><<<(unsigned)tiles, kThr, smem, s->stream>>>((R *)s->amps, dops, nops, geo);
     return launch_end(s, "staged pass");
 }
@@ -128,7 +128,13 @@ int run_staged(qsim_state *s, const std::vector<SGate> &g, int M)
     std::vector<Pass> passes = form_passes(g, s->n, M);
     PlanBuilder<R> pb{s->n, M, M - kThrBits, VEC, {}, {}, 0};
     std::vector<int> counts;
-    for (const Pass &ps : passes) counts.push_back(pb.schedule(ps, g));
+    std::vector<double> pflops;
+    for (const Pass &ps : passes) {
+        counts.push_back(pb.schedule(ps, g));
+        double f = 0.0;
+        for (int m : ps.members) f += sgate_flops(g[m], s->n);
+        pflops.push_back(f);
+    }
     const size_t bytes = pb.ops.size() * sizeof(StOp<R>);
     if (int rc = ensure_host_pinned(&s->host_ops, &s->host_ops_bytes, bytes)) return rc;
     if (int rc = ensure_device(s, &s->dev_ops, &s->dev_ops_bytes, bytes)) return rc;
@@ -148,10 +154,10 @@ int run_staged(qsim_state *s, const std::vector<SGate> &g, int M)
             if (!((q >> b) & 1)) geo.outer_pos[geo.n_outer++] = b;
         int rc;
         switch (M) {
-        case 11: rc = launch_staged<R, 11>(s, dops + off, counts[p], geo); break;
-        case 12: rc = launch_staged<R, 12>(s, dops + off, counts[p], geo); break;
+        case 11: rc = launch_staged<R, 11>(s, dops + off, counts[p], geo, pflops[p]); break;
+        case 12: rc = launch_staged<R, 12>(s, dops + off, counts[p], geo, pflops[p]); break;
         case 13:
-            if constexpr (sizeof(R) == 4) rc = launch_staged<R, 13>(s, dops + off, counts[p], geo);
+            if constexpr (sizeof(R) == 4) rc = launch_staged<R, 13>(s, dops + off, counts[p], geo, pflops[p]);
             else rc = fail(SIM_EINVAL, "staged: complex128 tiles are at most 12 qubits");
             break;
         default: rc = fail(SIM_EINVAL, "staged: unsupported tile size");

@@ -81,7 +81,7 @@ _sig("sim_measure", [P, _i32, _u64, _u64, P, P])
 _sig("sim_sample", [P, _u64, _u64, P, _i32])
 _sig("sim_expect_z_sum", [P, P])
 _sig("sim_profile_enable", [P, _i32])
-_sig("sim_profile_read", [P, _i32, P, P, P, _i32])
+_sig("sim_profile_read", [P, _i32, P, P, P, P, _i32])
 _sig("sim_launch_count", [P, P])
 _sig("sim_kernel_class_name", [_i32], ctypes.c_char_p)
 _sig("sim_num_kernel_classes", [], _i32)
@@ -237,8 +237,10 @@ def sim_profile_read(h: int, reset: bool = True):
     launches = (ctypes.c_uint64 * k)()
     ms = (ctypes.c_double * k)()
     nbytes = (ctypes.c_double * k)()
-    check(_lib.sim_profile_read(P(h), k, launches, ms, nbytes, int(reset)))
-    return {_lib.sim_kernel_class_name(i).decode(): (int(launches[i]), float(ms[i]), float(nbytes[i]))
+    flops = (ctypes.c_double * k)()
+    check(_lib.sim_profile_read(P(h), k, launches, ms, nbytes, flops, int(reset)))
+    return {_lib.sim_kernel_class_name(i).decode(): (int(launches[i]), float(ms[i]), float(nbytes[i]),
+                                                     float(flops[i]))
             for i in range(k) if launches[i]}
 
 
