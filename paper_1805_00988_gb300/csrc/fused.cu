@@ -262,13 +262,22 @@ __global__ void __launch_bounds__(kRows, 1) k_fused_apply(float *__restrict__ st
         base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1ull));
     }
     const bool live = R < a.rows;
-    for (int c = 0; c < D; ++c) {
-        float2 v = make_float2(0.f, 0.f);
-        if (live) v = *reinterpret_cast<const float2 *>(st + 2 * (base | dep[c]));
-        const float hr = tf32_trunc(v.x), hi = tf32_trunc(v.y);
-        const uint32_t off = kmajor_off(tid, 2 * c, K);        // (re, im) share one 16-byte row chunk
-        *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_hi) + off) = make_float2(hr, hi);
-        *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_lo) + off) = make_float2(v.x - hr, v.y - hi);
+    // gather the row in batches of independent loads (one batch in flight per thread)
+    constexpr int BATCH = D < 16 ? D : 16;
+#pragma unroll 1
+    for (int c0 = 0; c0 < D; c0 += BATCH) {
+        float2 v[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u)
+            v[u] = live ? *reinterpret_cast<const float2 *>(st + 2 * (base | dep[c0 + u])) : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const float hr = tf32_trunc(v[u].x), hi = tf32_trunc(v[u].y);
+            const uint32_t off = kmajor_off(tid, 2 * (c0 + u), K);    // (re, im) share one 16-byte row chunk
+            *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_hi) + off) = make_float2(hr, hi);
+            *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_lo) + off) =
+                make_float2(v[u].x - hr, v[u].y - hi);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -279,7 +288,9 @@ __global__ void __launch_bounds__(kRows, 1) k_fused_apply(float *__restrict__ st
         // B chunk: hi and lo, copied as 16-byte vectors
         const float4 *src = reinterpret_cast<const float4 *>(bmat + (size_t)ch * 2 * NC * K);
         float4 *dst = reinterpret_cast<float4 *>(b_s);
-        for (int e = tid; e < 2 * NC * K / 4; e += kRows) dst[e] = src[e];
+        constexpr int NV = 2 * NC * K / 4;                      // float4 per chunk, a multiple of 128
+#pragma unroll 4
+        for (int e = tid; e < NV; e += kRows) dst[e] = __ldg(src + e);
         fence_async_smem();
         __syncthreads();
         if (tid == 0) {

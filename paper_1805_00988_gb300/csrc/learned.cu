@@ -109,20 +109,25 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
         if (best[w] < 0 || pred[r] < bestp[w]) { best[w] = who[r].second; bestp[w] = pred[r]; }
     }
     s->last_plan.assign(best.begin(), best.end());
-    for (size_t w = 0; w < win.size(); ++w) {
+    // consecutive windows with the same variant run as one call, so the tile
+    // and block planners see the whole run of gates
+    for (size_t w = 0; w < win.size();) {
+        size_t e = w + 1;
+        while (e < win.size() && best[e] == best[w]) ++e;
+        const size_t first = win[w].first, count = win[e - 1].first + win[e - 1].count - first;
         sim_plan_opts vo;
         variant_opts(best[w] < 0 ? 0 : best[w], &vo);
         int rc;
         if (vo.plan == SIM_PLAN_PER_GATE) {
             rc = SIM_OK;
-            for (size_t k = 0; k < win[w].count && rc == SIM_OK; ++k)
-                rc = launch_pair_gate(s, make_pair_gate(gates[win[w].first + k]));
+            for (size_t k = 0; k < count && rc == SIM_OK; ++k) rc = launch_pair_gate(s, make_pair_gate(gates[first + k]));
         } else if (vo.plan == SIM_PLAN_STAGED) {
-            rc = apply_circuit_staged(s, gates + win[w].first, win[w].count, vo);
+            rc = apply_circuit_staged(s, gates + first, count, vo);
         } else {
-            rc = apply_circuit_fused(s, gates + win[w].first, win[w].count, vo);
+            rc = apply_circuit_fused(s, gates + first, count, vo);
         }
         if (rc) return rc;
+        w = e;
     }
     return SIM_OK;
 }

@@ -73,7 +73,28 @@ template <typename R>
 __device__ __forceinline__ double sq(R re, R im)
 {
     const double r = (double)re, i = (double)im;
-    return r * r + i * i;
+    return fma(r, r, i * i);
+}
+
+// FP32 -> FP64 with integer operations (the FP64 pipe of this GPU is narrow,
+// so the conversion would cost as much as the arithmetic): a normal float is
+// widened exactly by rebiasing the exponent (127 -> 1023) and shifting the
+// mantissa; zero and subnormals become 0 (their squares are below 1e-76 and
+// do not change an FP64 sum of probabilities); states hold no inf / NaN.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const uint64_t d = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)(e + 896u) << 52) |
+                       ((uint64_t)(u & 0x007FFFFFu) << 29);
+    return e ? __longlong_as_double((long long)d) : 0.0;
+}
+
+template <>
+__device__ __forceinline__ double sq<float>(float re, float im)
+{
+    const double r = widen(re), i = widen(im);
+    return fma(r, r, i * i);
 }
 
 

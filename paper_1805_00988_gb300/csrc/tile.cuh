@@ -98,41 +98,22 @@ template <> struct V2<double> { using T = double2; };
 // instruction (fma.rn.f32x2); complex128 keeps plain doubles.
 template <typename R, int RA> struct Regs;
 template <int RA> struct Regs<float, RA> {
-    // pack p = (amplitude 2p, amplitude 2p + 1) as one 64-bit register pair
-    uint64_t r[RA / 2], i[RA / 2];
-    __device__ __forceinline__ static float lo(uint64_t x)
-    {
-        float a, b;
-        asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-        return a;
-    }
-    __device__ __forceinline__ static float hi(uint64_t x)
-    {
-        float a, b;
-        asm("mov.b64 {%0,%1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
-        return b;
-    }
-    __device__ __forceinline__ static uint64_t mk(float a, float b)
-    {
-        uint64_t x;
-        asm("mov.b64 %0, {%1,%2};" : "=l"(x) : "f"(a), "f"(b));
-        return x;
-    }
-    __device__ __forceinline__ float getr(int k) const { return (k & 1) ? hi(r[k >> 1]) : lo(r[k >> 1]); }
-    __device__ __forceinline__ float geti(int k) const { return (k & 1) ? hi(i[k >> 1]) : lo(i[k >> 1]); }
+    // pack p = (amplitude 2p, amplitude 2p + 1) in one float2 register pair
+    float2 r[RA / 2], i[RA / 2];
+    __device__ __forceinline__ float getr(int k) const { return (k & 1) ? r[k >> 1].y : r[k >> 1].x; }
+    __device__ __forceinline__ float geti(int k) const { return (k & 1) ? i[k >> 1].y : i[k >> 1].x; }
     __device__ __forceinline__ void setr(int k, float v)
     {
-        r[k >> 1] = (k & 1) ? mk(lo(r[k >> 1]), v) : mk(v, hi(r[k >> 1]));
+        if (k & 1) r[k >> 1].y = v; else r[k >> 1].x = v;
     }
     __device__ __forceinline__ void seti(int k, float v)
     {
-        i[k >> 1] = (k & 1) ? mk(lo(i[k >> 1]), v) : mk(v, hi(i[k >> 1]));
+        if (k & 1) i[k >> 1].y = v; else i[k >> 1].x = v;
     }
-    // both amplitudes of pack p at once
     __device__ __forceinline__ void set2(int p, float r0, float i0, float r1, float i1)
     {
-        r[p] = mk(r0, r1);
-        i[p] = mk(i0, i1);
+        r[p] = make_float2(r0, r1);
+        i[p] = make_float2(i0, i1);
     }
 };
 template <int RA> struct Regs<double, RA> {
@@ -146,62 +127,37 @@ template <int RA> struct Regs<double, RA> {
 template <typename R>
 struct CoefS { R ar, ai, br, bi, cr, ci, dr, di; };
 
-// packed FP32x2 helpers (PTX fma / mul on 64-bit register pairs, sm_100+)
-__device__ __forceinline__ uint64_t pk(float2 v)
-{
-    uint64_t r;
-    asm("mov.b64 %0, {%1,%2};" : "=l"(r) : "f"(v.x), "f"(v.y));
-    return r;
-}
-__device__ __forceinline__ float2 upk(uint64_t v)
-{
-    float2 r;
-    asm("mov.b64 {%0,%1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-}
-__device__ __forceinline__ uint64_t pfma(uint64_t a, uint64_t b, uint64_t c)
-{
-    uint64_t d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ uint64_t pmul(uint64_t a, uint64_t b)
-{
-    uint64_t d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-
-struct PCoef { uint64_t ar, ai, nai, br, bi, nbi, cr, ci, nci, dr, di, ndi; };
+// packed FP32x2 arithmetic (sm_100+ builtins on float2 register pairs)
+struct PCoef { float2 ar, ai, nai, br, bi, nbi, cr, ci, nci, dr, di, ndi; };
 
 __device__ __forceinline__ PCoef make_pcoef(const CoefS<float> &c)
 {
     PCoef p;
-    p.ar = pk(make_float2(c.ar, c.ar)); p.ai = pk(make_float2(c.ai, c.ai)); p.nai = pk(make_float2(-c.ai, -c.ai));
-    p.br = pk(make_float2(c.br, c.br)); p.bi = pk(make_float2(c.bi, c.bi)); p.nbi = pk(make_float2(-c.bi, -c.bi));
-    p.cr = pk(make_float2(c.cr, c.cr)); p.ci = pk(make_float2(c.ci, c.ci)); p.nci = pk(make_float2(-c.ci, -c.ci));
-    p.dr = pk(make_float2(c.dr, c.dr)); p.di = pk(make_float2(c.di, c.di)); p.ndi = pk(make_float2(-c.di, -c.di));
+    p.ar = make_float2(c.ar, c.ar); p.ai = make_float2(c.ai, c.ai); p.nai = make_float2(-c.ai, -c.ai);
+    p.br = make_float2(c.br, c.br); p.bi = make_float2(c.bi, c.bi); p.nbi = make_float2(-c.bi, -c.bi);
+    p.cr = make_float2(c.cr, c.cr); p.ci = make_float2(c.ci, c.ci); p.nci = make_float2(-c.ci, -c.ci);
+    p.dr = make_float2(c.dr, c.dr); p.di = make_float2(c.di, c.di); p.ndi = make_float2(-c.di, -c.di);
     return p;
 }
 
 // two amplitude pairs at once: lanes x / y are independent pairs
 template <int KIND>
-__device__ __forceinline__ void pupd(uint64_t &lr, uint64_t &li, uint64_t &hr, uint64_t &hi, const PCoef &c)
+__device__ __forceinline__ void pupd(float2 &lr, float2 &li, float2 &hr, float2 &hi, const PCoef &c)
 {
     if (KIND == SK_DENSE) {
-        const uint64_t nlr = pfma(c.ar, lr, pfma(c.nai, li, pfma(c.br, hr, pmul(c.nbi, hi))));
-        const uint64_t nli = pfma(c.ar, li, pfma(c.ai, lr, pfma(c.br, hi, pmul(c.bi, hr))));
-        const uint64_t nhr = pfma(c.cr, lr, pfma(c.nci, li, pfma(c.dr, hr, pmul(c.ndi, hi))));
-        const uint64_t nhi = pfma(c.cr, li, pfma(c.ci, lr, pfma(c.dr, hi, pmul(c.di, hr))));
+        const float2 nlr = __ffma2_rn(c.ar, lr, __ffma2_rn(c.nai, li, __ffma2_rn(c.br, hr, __fmul2_rn(c.nbi, hi))));
+        const float2 nli = __ffma2_rn(c.ar, li, __ffma2_rn(c.ai, lr, __ffma2_rn(c.br, hi, __fmul2_rn(c.bi, hr))));
+        const float2 nhr = __ffma2_rn(c.cr, lr, __ffma2_rn(c.nci, li, __ffma2_rn(c.dr, hr, __fmul2_rn(c.ndi, hi))));
+        const float2 nhi = __ffma2_rn(c.cr, li, __ffma2_rn(c.ci, lr, __ffma2_rn(c.dr, hi, __fmul2_rn(c.di, hr))));
         lr = nlr; li = nli; hr = nhr; hi = nhi;
     } else if (KIND == SK_ANTI) {
-        const uint64_t nlr = pfma(c.br, hr, pmul(c.nbi, hi));
-        const uint64_t nli = pfma(c.br, hi, pmul(c.bi, hr));
-        const uint64_t nhr = pfma(c.cr, lr, pmul(c.nci, li));
-        const uint64_t nhi = pfma(c.cr, li, pmul(c.ci, lr));
+        const float2 nlr = __ffma2_rn(c.br, hr, __fmul2_rn(c.nbi, hi));
+        const float2 nli = __ffma2_rn(c.br, hi, __fmul2_rn(c.bi, hr));
+        const float2 nhr = __ffma2_rn(c.cr, lr, __fmul2_rn(c.nci, li));
+        const float2 nhi = __ffma2_rn(c.cr, li, __fmul2_rn(c.ci, lr));
         lr = nlr; li = nli; hr = nhr; hi = nhi;
     } else {
-        uint64_t t = lr; lr = hr; hr = t;
+        float2 t = lr; lr = hr; hr = t;
         t = li; li = hi; hi = t;
     }
 }
