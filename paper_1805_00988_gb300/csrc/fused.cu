@@ -338,6 +338,170 @@ __global__ void __launch_bounds__(kRows, 1) k_fused_apply(float *__restrict__ st
     if (warp == 0) tmem_dealloc(taddr, NCOLS);
 }
 
+// ------------------------------------------------------------------ pipelined apply (k <= 5)
+// A persistent, warp-specialised version for blocks whose W fits one N chunk:
+// W (hi / lo) is loaded once per CTA; warps 0-3 gather the next 128 rows while
+// warp 8 issues the MMAs of the current tile into one of two TMEM accumulators
+// and warps 4-7 drain the other accumulator back to HBM.  Hand-offs are
+// mbarriers: A written (128 producer arrivals), accumulator full (MMA commit),
+// accumulator drained (128 consumer arrivals).  Every wait is bounded.
+constexpr int kPipeThreads = 288;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+template <int KQ>
+__global__ void __launch_bounds__(kPipeThreads, 2) k_fused_pipe(float *__restrict__ st, const float *__restrict__ bmat,
+                                                               ApplyArgs a, uint64_t ntiles, int *__restrict__ status)
+{
+    constexpr int D = 1 << KQ;
+    constexpr int K = 2 * D;
+    constexpr int N = K;
+    static_assert(N <= kNChunk, "the pipelined apply takes W in one N chunk");
+    constexpr uint32_t NC = (N < 32) ? 32 : N;          // TMEM columns per accumulator
+    constexpr uint32_t NCOLS = 2 * NC;                    // two accumulators
+    constexpr uint32_t SBO = (K / 4) * 128;
+    constexpr uint32_t IDESC = make_idesc_tf32(kRows, N);
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float *a_hi = reinterpret_cast<float *>(smem);      // kRows x K
+    float *a_lo = a_hi + kRows * K;
+    float *b_hi = a_lo + kRows * K;                      // N x K
+    float *b_lo = b_hi + N * K;
+    __shared__ uint64_t bar_a, bar_d[2], bar_e[2];
+    __shared__ uint32_t tslot;
+    __shared__ uint64_t dep[D];
+    __shared__ int failed;
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) failed = *reinterpret_cast<volatile int *>(status);
+    __syncthreads();
+    if (failed) return;
+    if (warp == 0) tmem_alloc(&tslot, NCOLS);
+    if (tid == 0) {
+        mbar_init(&bar_a, kRows);
+        mbar_init(&bar_d[0], 1);
+        mbar_init(&bar_d[1], 1);
+        mbar_init(&bar_e[0], kRows);
+        mbar_init(&bar_e[1], kRows);
+    }
+    for (int c = tid; c < D; c += kPipeThreads) {
+        uint64_t o = 0;
+        for (int i = 0; i < KQ; ++i)
+            if ((c >> i) & 1) o |= 1ull << a.pos[i];
+        dep[c] = o;
+    }
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(bmat);
+        float4 *dst = reinterpret_cast<float4 *>(b_hi);
+        for (int e = tid; e < 2 * N * K / 4; e += kPipeThreads) dst[e] = __ldg(src + e);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = tslot;
+    volatile int *vfailed = &failed;
+    const uint64_t step = gridDim.x;
+    const int iters = ((uint64_t)blockIdx.x < ntiles) ? (int)((ntiles - 1 - blockIdx.x) / step + 1) : 0;
+
+    auto row_base = [&](uint64_t t, int r) {
+        uint64_t base = t * kRows + (uint64_t)r;
+#pragma unroll
+        for (int i = 0; i < KQ; ++i) {
+            const int p = a.pos[i];
+            base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1ull));
+        }
+        return base;
+    };
+
+    if (warp < 4) {
+        // producers: thread tid gathers row tid of every tile of this CTA
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const uint64_t base = row_base(blockIdx.x + (uint64_t)i * step, tid);
+            float2 v[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) v[c] = *reinterpret_cast<const float2 *>(st + 2 * (base | dep[c]));
+            // the MMA of the previous tile must be done reading A
+            if (i >= 1 && !mbar_wait_bounded(&bar_d[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                const float hr = tf32_trunc(v[c].x), hi = tf32_trunc(v[c].y);
+                const uint32_t off = kmajor_off(tid, 2 * c, K);
+                *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_hi) + off) = make_float2(hr, hi);
+                *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_lo) + off) =
+                    make_float2(v[c].x - hr, v[c].y - hi);
+            }
+            fence_async_smem();
+            mbar_arrive(&bar_a);
+        }
+    } else if (warp < 8) {
+        // consumers: warp w reads TMEM lanes 32 (w - 4) .. + 31 = rows of the tile
+        const int r = tid - 128;
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int sb = i & 1;
+            if (!mbar_wait_bounded(&bar_d[sb], (uint32_t)((i >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint64_t base = row_base(blockIdx.x + (uint64_t)i * step, r);
+            const uint32_t lane_base = taddr + (uint32_t)(sb * NC) + ((uint32_t)((warp - 4) * 32) << 16);
+#pragma unroll 1
+            for (int col = 0; col < N; col += 16) {
+                float v[16];
+                tmem_ld16(lane_base + (uint32_t)col, v);
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int c = col / 2 + e;
+                    *reinterpret_cast<float2 *>(st + 2 * (base | dep[c])) = make_float2(v[2 * e], v[2 * e + 1]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bar_e[sb]);
+        }
+    } else if ((tid & 31) == 0) {
+        // issuer (warp 8, one thread)
+        const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo);
+        const uint32_t sb_hi = smem_u32(b_hi), sb_lo = smem_u32(b_lo);
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int sb = i & 1;
+            if (!mbar_wait_bounded(&bar_a, (uint32_t)(i & 1))) { *vfailed = 1; break; }
+            if (i >= 2 && !mbar_wait_bounded(&bar_e[sb], (uint32_t)(((i - 2) >> 1) & 1))) { *vfailed = 1; break; }
+            tc_fence_after();
+            const uint32_t d = taddr + (uint32_t)(sb * NC);
+#pragma unroll 1
+            for (int ks = 0; ks < K / 8; ++ks) {
+                const uint32_t ko = (uint32_t)ks * 256;
+                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC, ks > 0);
+                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_lo + ko, 128, SBO), IDESC, 1);
+                mma_tf32(d, make_desc(sa_lo + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC, 1);
+            }
+            mma_commit(&bar_d[sb]);
+        }
+    }
+    if (*vfailed) {
+        if (tid == 0) atomicExch(status, SIM_ETIMEOUT);
+        // give tensor-core work still in flight a bounded chance to finish
+        if (tid == 256 && iters > 0) mbar_wait_bounded(&bar_d[(iters - 1) & 1], (uint32_t)(((iters - 1) >> 1) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, NCOLS);
+}
+
+template <int KQ>
+size_t pipe_smem_bytes()
+{
+    constexpr int K = 2 << KQ;
+    return (size_t)(2 * kRows * K + 2 * K * K) * sizeof(float);
+}
+
 template <int KQ>
 size_t apply_smem_bytes()
 {
@@ -453,6 +617,25 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
         const size_t sma = apply_smem_bytes<KQ>();
         cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
         const uint64_t rows = 1ull << (n - KQ);
+        // k = 5: the persistent pipelined kernel, one CTA per SM slot it fits
+        // (for k = 3, 4 the one-tile-per-CTA kernel keeps more rows in flight
+        // and measured faster; k = 6 does not fit W and two A buffers)
+        int pipe_grid = 0;
+        size_t smp = 0;
+        if constexpr (KQ == 5) {
+            smp = pipe_smem_bytes<KQ>();
+            cudaFuncSetAttribute(k_fused_pipe<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_pipe<KQ>, kPipeThreads, smp) !=
+                    cudaSuccess || per_sm < 1) {
+                rc = fail(SIM_ECUDA, "fused apply: pipelined kernel does not fit on an SM");
+                break;
+            }
+            const int cols = 2 * ((2 << KQ) < 32 ? 32 : (2 << KQ));     // TMEM columns per CTA
+            per_sm = std::min(per_sm, 512 / cols);
+            const uint64_t tiles = (rows + kRows - 1) / kRows;
+            pipe_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms * per_sm);
+        }
         for (size_t b = 0; b < nb && rc == SIM_OK; ++b) {
             if (blocks[b].wide) {
                 rc = launch_sgate(s, g[blocks[b].members[0]]);
@@ -464,8 +647,14 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
             a.rows = rows;
             // tensor-core flops: three real GEMMs [rows x K] x [K x K] (3xTF32)
             launch_begin(s, KC_FUSED, 2.0 * (double)s->bytes, 3.0 * 2.0 * (double)rows * K * K);
-            k_fused_apply<KQ><<<(unsigned)((rows + kRows - 1) / kRows), kRows, sma, s->stream>>>(
-                (float *)s->amps, (const float *)(scratch + o_b) + b * 2 * (size_t)K * K, a, s->dev_status);
+            const float *bm = (const float *)(scratch + o_b) + b * 2 * (size_t)K * K;
+            if constexpr (KQ == 5) {
+                k_fused_pipe<KQ><<<(unsigned)pipe_grid, kPipeThreads, smp, s->stream>>>(
+                    (float *)s->amps, bm, a, (rows + kRows - 1) / kRows, s->dev_status);
+            } else {
+                k_fused_apply<KQ><<<(unsigned)((rows + kRows - 1) / kRows), kRows, sma, s->stream>>>(
+                    (float *)s->amps, bm, a, s->dev_status);
+            }
             rc = launch_end(s, "fused apply");
         }
     } while (0);
