@@ -281,19 +281,28 @@ def run_ours(args, rank, world, local_rank):
     gbs = (dbytes / dl) / sec / 1e9
     tflops = (dflops / dl) / sec / 1e12
     hbm_frac = gbs / peaks["hbm_gbs"]
-    alu_frac = tflops / FP32_PEAK_TFLOPS
-    if alu_frac > hbm_frac:
-        # the binding resource is FP32 arithmetic (complex 2x2 updates in registers)
-        roofline = {"kernel": dname, "bound": "alu", "achieved": tflops, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": alu_frac, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz",
+    if dname == "fused":
+        # tensor-core TF32 work: the measured sustained bf16 peak scaled by the
+        # nominal TF32 / bf16 dense ratio (1.1 / 2.25 PFLOP/s)
+        cpeak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
+        cbound, csrc = "tensor", "MEASURED_PEAKS.json bf16_tflops_sustained x (1.1 / 2.25) nominal TF32/bf16"
+    else:
+        cpeak = FP32_PEAK_TFLOPS
+        cbound, csrc = "alu", "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz"
+    cfrac = tflops / cpeak
+    if cfrac > hbm_frac:
+        # the binding resource is arithmetic (register 2x2 updates or tensor-core GEMMs)
+        roofline = {"kernel": dname, "bound": cbound, "achieved": tflops, "peak": cpeak,
+                    "unit": "TFLOP/s", "frac": cfrac, "traffic": None, "peak_source": csrc,
                     "alg_flops_per_launch": dflops / dl, "hbm": {"achieved_GBps": gbs, "peak_GBps": peaks["hbm_gbs"],
                                                                 "frac": hbm_frac}}
     else:
         roofline = {"kernel": dname, "bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
                     "unit": "GB/s", "frac": hbm_frac, "traffic": None,
                     "peak_source": ("measured (MEASURED_PEAKS.json hbm_gbs, copy)" if peak_kind == "measured"
-                                    else "fallback 6.8 TB/s")}
+                                    else "fallback 6.8 TB/s"),
+                    "compute": {"bound": cbound, "achieved_TFLOPs": tflops, "peak_TFLOPs": cpeak, "frac": cfrac,
+                                "peak_source": csrc}}
     roofline.update({"alg_bytes_per_launch": dbytes / dl, "avg_launch_ms": dms / dl, "launches": dl,
                      "timed_with": "CUDA events around every launch on the handle's stream, timed region"})
     kernels = {k: {"launches": v[0], "ms": v[1], "alg_GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None,
@@ -467,6 +476,7 @@ def run_extras(args, sim, C, dev, model):
         st = sim.State(n5, "c64", device=dev)
         res = {}
         for name, o in (("greedy_staged13", sim.plan_opts("staged", tile_qubits=13)),
+                        ("greedy_fused5", sim.plan_opts("fused", fuse_k=5)),
                         ("learned", sim.plan_opts("learned"))):
             if name == "learned":
                 sim.sim_set_cost_model(st.h, model)

@@ -517,36 +517,72 @@ struct Block {
     bool wide = false;        // one gate on more than k qubits: applied by a per-gate launch
 };
 
-// Greedy fixed-k blocks: scan the remaining gates; a gate joins the block if
-// it commutes with every gate skipped before it and the union of qubits stays
-// within k.
-std::vector<Block> form_blocks(const std::vector<SGate> &g, int k)
+// Gates absorbable into a block on the fixed qubit set S: scan the remaining
+// gates (at most W of them); a gate counts if it commutes with every gate
+// skipped before it and all its qubits are in S.
+int absorb_count(const std::vector<SGate> &g, const std::vector<char> &done, size_t first, uint64_t S, size_t W)
 {
+    uint64_t bx = 0, bd = 0;
+    int cnt = 0;
+    size_t seen = 0;
+    for (size_t i = first; i < g.size() && seen < W; ++i) {
+        if (done[i]) continue;
+        ++seen;
+        const uint64_t x = g[i].xq(), d = g[i].dq();
+        if (((x & (bx | bd)) == 0) && ((d & bx) == 0) && (((x | d) & ~S) == 0)) {
+            ++cnt;
+        } else {
+            bx |= x;
+            bd |= d;
+        }
+    }
+    return cnt;
+}
+
+// Fixed-k blocks with a lookahead choice of qubits: a block starts from the
+// qubits of the first remaining gate and grows, one qubit at a time up to k,
+// by the qubit that lets the most of the next gates (a window of 256) join;
+// then every remaining gate that commutes with the gates skipped before it and
+// lies on the block's qubits joins.
+std::vector<Block> form_blocks(const std::vector<SGate> &g, int k, int n)
+{
+    constexpr size_t kWindow = 256;
     std::vector<Block> blocks;
     std::vector<char> done(g.size(), 0);
     size_t first = 0;
     while (first < g.size()) {
         Block b{0, {}};
-        uint64_t bx = 0, bd = 0;
-        for (size_t i = first; i < g.size(); ++i) {
-            if (done[i]) continue;
-            const uint64_t x = g[i].xq(), d = g[i].dq();
-            const bool free_of_skipped = ((x & (bx | bd)) == 0) && ((d & bx) == 0);
-            if (free_of_skipped && __builtin_popcountll(b.qmask | x | d) <= k) {
-                b.qmask |= x | d;
-                b.members.push_back((int)i);
-                done[i] = 1;
-            } else {
-                bx |= x;
-                bd |= d;
-            }
-        }
-        if (b.members.empty()) {
+        uint64_t S = g[first].xq() | g[first].dq();
+        if (__builtin_popcountll(S) > k) {
             // the first remaining gate alone spans more than k qubits
-            b.qmask = g[first].xq() | g[first].dq();
+            b.qmask = S;
             b.members.push_back((int)first);
             b.wide = true;
             done[first] = 1;
+        } else {
+            while (__builtin_popcountll(S) < k) {
+                int best_q = -1, best = absorb_count(g, done, first, S, kWindow);
+                for (int q = 0; q < n; ++q) {
+                    if ((S >> q) & 1) continue;
+                    const int c = absorb_count(g, done, first, S | (1ull << q), kWindow);
+                    if (c > best) { best = c; best_q = q; }
+                }
+                if (best_q < 0) break;
+                S |= 1ull << best_q;
+            }
+            uint64_t bx = 0, bd = 0;
+            for (size_t i = first; i < g.size(); ++i) {
+                if (done[i]) continue;
+                const uint64_t x = g[i].xq(), d = g[i].dq();
+                if (((x & (bx | bd)) == 0) && ((d & bx) == 0) && (((x | d) & ~S) == 0)) {
+                    b.qmask |= x | d;
+                    b.members.push_back((int)i);
+                    done[i] = 1;
+                } else {
+                    bx |= x;
+                    bd |= d;
+                }
+            }
         }
         blocks.push_back(b);
         while (first < g.size() && done[first]) ++first;
@@ -672,9 +708,8 @@ int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t 
 {
     std::vector<SGate> g;
     lower_gates(gates, n_gates, &g);
-    std::vector<Block> b = form_blocks(g, k);
+    std::vector<Block> b = form_blocks(g, k, n);
     if (blocks_out) *blocks_out = (int64_t)b.size();
-    (void)n;
     return SIM_OK;
 }
 
@@ -687,7 +722,7 @@ int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, co
     std::vector<SGate> g;
     lower_gates(gates, n_gates, &g);
     if (g.empty()) return SIM_OK;
-    std::vector<Block> blocks = form_blocks(g, k);
+    std::vector<Block> blocks = form_blocks(g, k, s->n);
     switch (k) {
     case 3: return run_fused<3>(s, g, blocks);
     case 4: return run_fused<4>(s, g, blocks);
