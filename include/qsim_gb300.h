@@ -174,7 +174,9 @@ int sim_batch_destroy(sim_batch_t b);
 /* ---- plan cost model ---------------------------------------------------------
  * A small MLP (d_in -> hidden -> hidden -> 1, ReLU) trained on the GPU by the
  * library's own forward / backward / Adam kernels to predict the log of a
- * circuit segment's run time under each plan variant (there is no paper
+ * circuit segment's run time under each plan variant, up to an additive
+ * constant per register size (only the variants of one segment are
+ * compared with each other; there is no paper
  * counterpart: the paper applies every gate with its own kernel launch).
  * Parameters: one FP32 vector W1 (d_in x hidden, row-major), b1, W2, b2,
  * W3 (hidden x 1), b3 -- sim_mlp_param_count() floats.

@@ -3,7 +3,9 @@
 ``collect`` cuts circuits of several families into the windows the learned
 plan uses, runs every window under every feasible plan variant on the GPU
 (CUDA events, median of repeats) and records the library's feature row for
-it; the target is log(milliseconds).  ``train`` fits the MLP with the
+it; the target is log(milliseconds per 2^30 amplitudes) -- the time scaled
+to a 30-qubit state, so that a register a few qubits larger than any timed
+one is predicted from the per-amplitude cost the model has seen.  ``train`` fits the MLP with the
 library's own kernels (sim_mlp_train); ``save`` / ``load`` keep the
 parameters as JSON.  Everything here drives the C ABI; no simulation
 arithmetic happens in Python.
@@ -51,26 +53,43 @@ def time_window(st, sg, opts, reps: int) -> float:
     return float(np.median(ts))
 
 
+def target(ms: float, n: int) -> float:
+    """The regression target: log of the time scaled to 2^30 amplitudes."""
+    return math.log(max(ms, 1e-4)) - (n - 30) * math.log(2.0)
+
+
 def collect(n_list=(24, 26, 28), reps: int = 3, seed: int = 7, max_windows: int = 6, log=None):
-    """Returns X (rows x features, float32), T (log ms, float32), meta."""
+    """Returns X (rows x features, float32), T (``target``, float32), meta.
+
+    Rows: every window of the first ``max_windows`` of each family's circuit
+    under every feasible variant, and the span of all those windows as one
+    segment under every variant but per-gate (the learned plan compares the
+    per-window choice with one variant over the whole circuit)."""
     X, T, meta = [], [], []
+
+    def row(st, n, fam, w0, seg, v):
+        f = sim.sim_plan_features(n, sim.SIM_C64, seg, v)
+        if f is None:
+            return
+        ms = time_window(st, seg, sim.variant_opts(v), reps)
+        X.append(f)
+        T.append(target(ms, n))
+        meta.append((n, fam, w0, v, ms))
+        if log:
+            log("n=%d %-11s w0=%4d len=%5d %-9s %.3f ms" % (n, fam, w0, len(seg), sim.VARIANTS[v], ms))
+
     for n in n_list:
         st = sim.State(n, "c64")
         for fam, g in families(n, seed + n):
             sg = sim.to_sim_gates(g)
             W = window_size(n)
-            for w0 in range(0, min(len(sg), W * max_windows), W):
-                win = sg[w0:w0 + W]
+            span = min(len(sg), W * max_windows)
+            for w0 in range(0, span, W):
                 for v in range(sim.N_VARIANTS):
-                    f = sim.sim_plan_features(n, sim.SIM_C64, win, v)
-                    if f is None:
-                        continue
-                    ms = time_window(st, win, sim.variant_opts(v), reps)
-                    X.append(f)
-                    T.append(math.log(max(ms, 1e-4)))
-                    meta.append((n, fam, w0, v, ms))
-                    if log:
-                        log("n=%d %-11s w0=%4d %-9s %.3f ms" % (n, fam, w0, sim.VARIANTS[v], ms))
+                    row(st, n, fam, w0, sg[w0:w0 + W], v)
+            if span > W:
+                for v in range(1, sim.N_VARIANTS):
+                    row(st, n, fam, -1, sg[:span], v)
         st.close()
     return np.array(X, dtype=np.float32), np.array(T, dtype=np.float32), meta
 
@@ -109,7 +128,7 @@ def main(argv=None):
     import argparse
     import time
     ap = argparse.ArgumentParser(description="collect timings on this GPU and train the plan cost model")
-    ap.add_argument("--n", default="24,26,28")
+    ap.add_argument("--n", default="26,28,30,32")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--windows", type=int, default=6)
     ap.add_argument("--steps", type=int, default=3000)

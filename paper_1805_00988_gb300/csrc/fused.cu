@@ -141,6 +141,31 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 consecutive columns of the warp's 32 lanes into r[]; the caller issues
+// tmem_wait_ld() before reading r
+__device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *r)
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 __host__ __device__ __forceinline__ float tf32_trunc(float x)
 {
 #ifdef __CUDA_ARCH__
@@ -338,65 +363,134 @@ __global__ void __launch_bounds__(kRows, 1) k_fused_apply(float *__restrict__ st
     if (warp == 0) tmem_dealloc(taddr, NCOLS);
 }
 
-// ------------------------------------------------------------------ pipelined apply (k <= 5)
-// A persistent, warp-specialised version for blocks whose W fits one N chunk:
-// W (hi / lo) is loaded once per CTA; warps 0-3 gather the next 128 rows while
-// warp 8 issues the MMAs of the current tile into one of two TMEM accumulators
-// and warps 4-7 drain the other accumulator back to HBM.  Hand-offs are
-// mbarriers: A written (128 producer arrivals), accumulator full (MMA commit),
-// accumulator drained (128 consumer arrivals).  Every wait is bounded.
-constexpr int kPipeThreads = 288;
+// ------------------------------------------------------------------ streamed apply (k <= 5)
+// A persistent, warp-specialised version for blocks whose W fits one N chunk.
+// A tile is 128 rows x 2^k amplitudes: the 2^(k+7) amplitudes that share
+// every index bit outside T = (block qubits) u (the 7 lowest other qubits).
+// Bits 0 .. L-1 of the index all lie in T (L >= 7), so a tile is
+// 2^(k+7-L) <= 32 contiguous runs of 2^L amplitudes (>= 1 KB each).
+//   warp 9: streams tiles into a ring of S shared-memory stages, lane j
+//       issuing the cp.async.bulk of run j; the stage's mbarrier counts the
+//       bytes landed;
+//   warps 0-3: thread r takes row r of a landed stage, frees the stage, and
+//       writes the row's TF32 hi / lo parts (K-major core-matrix layout) into
+//       one of two A buffers once the MMAs that last read that buffer are done;
+//   warp 8 (one thread): per K-step one MMA A_hi x [W_hi | W_lo] (N = 2K) and
+//       one A_lo x W_hi (N = K) into one of two TMEM accumulators, so that
+//       columns [0, K) hold A_hi W_hi + A_lo W_hi and [K, 2K) hold A_hi W_lo;
+//       commit to that accumulator's mbarrier;
+//   warps 4-7: drain the other accumulator (both halves, summed) to HBM.
+// W (hi / lo) is loaded once per CTA.  Every wait is bounded by %globaltimer;
+// on a timeout the CTA records SIM_ETIMEOUT, lets copies and MMAs in flight
+// land (bounded again), frees its tensor memory and returns.
+constexpr int kStreamThreads = 320;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 {
     asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+// one contiguous global -> shared copy on the bulk-copy engine; completion is
+// counted (in bytes) on the mbarrier.  Addresses 16-byte aligned, size a
+// multiple of 16.
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst_smem)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// S: stages in the ring; MINB: CTAs per SM the registers are budgeted for
+template <int KQ> struct StreamCfg;
+template <> struct StreamCfg<3> { static constexpr int S = 3, MINB = 2; };
+template <> struct StreamCfg<4> { static constexpr int S = 2, MINB = 2; };
+template <> struct StreamCfg<5> { static constexpr int S = 2, MINB = 1; };
 
 template <int KQ>
-__global__ void __launch_bounds__(kPipeThreads, 2) k_fused_pipe(float *__restrict__ st, const float *__restrict__ bmat,
-                                                               ApplyArgs a, uint64_t ntiles, int *__restrict__ status)
+__global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
+    k_fused_stream(float *__restrict__ st, const float *__restrict__ bmat, ApplyArgs a, uint64_t ntiles,
+                   int *__restrict__ status)
 {
+    constexpr int S = StreamCfg<KQ>::S;
     constexpr int D = 1 << KQ;
     constexpr int K = 2 * D;
     constexpr int N = K;
-    static_assert(N <= kNChunk, "the pipelined apply takes W in one N chunk");
-    constexpr uint32_t NC = (N < 32) ? 32 : N;          // TMEM columns per accumulator
-    constexpr uint32_t NCOLS = 2 * NC;                    // two accumulators
+    static_assert(N <= kNChunk, "the streamed apply takes W in one N chunk");
+    constexpr int TB = KQ + 7;                       // tile bits
+    constexpr int TAMP = 1 << TB;                    // amplitudes per tile = kRows * D
+    constexpr uint32_t TBYTES = (uint32_t)TAMP * 8u;
+    constexpr uint32_t NC = 2 * N;                   // TMEM columns per accumulator: [hi part | lo part]
+    constexpr uint32_t NCOLS = 2 * NC;
+    static_assert(NCOLS >= 32 && (NCOLS & (NCOLS - 1)) == 0, "TMEM allocations are powers of two >= 32");
     constexpr uint32_t SBO = (K / 4) * 128;
-    constexpr uint32_t IDESC = make_idesc_tf32(kRows, N);
+    constexpr uint32_t IDESC2 = make_idesc_tf32(kRows, 2 * N);
+    constexpr uint32_t IDESC1 = make_idesc_tf32(kRows, N);
+    constexpr int ABUF = kRows * K;                  // floats of one A operand
 
     extern __shared__ __align__(1024) unsigned char smem[];
-    float *a_hi = reinterpret_cast<float *>(smem);      // kRows x K
-    float *a_lo = a_hi + kRows * K;
-    float *b_hi = a_lo + kRows * K;                      // N x K
-    float *b_lo = b_hi + N * K;
-    __shared__ uint64_t bar_a, bar_d[2], bar_e[2];
+    float2 *stage = reinterpret_cast<float2 *>(smem);                           // S x TAMP amplitudes
+    float *abuf = reinterpret_cast<float *>(smem + (size_t)S * TBYTES);         // [buffer][hi | lo] kRows x K
+    float *b_hi = abuf + 4 * ABUF;                                               // N x K, then b_lo (N x K)
+    __shared__ uint64_t bar_full[S], bar_empty[S], bar_a[2], bar_d[2], bar_e[2];
     __shared__ uint32_t tslot;
-    __shared__ uint64_t dep[D];
+    __shared__ int tpos[TB];          // global bit of tile-local bit j (ascending)
+    __shared__ uint64_t pmask;        // block bits
+    __shared__ int lrun;              // L: tile-local bits 0 .. L-1 are global bits 0 .. L-1
+    __shared__ uint32_t uc[D];        // tile-local offset of column c
+    __shared__ uint64_t gc[D];        // global offset of column c
     __shared__ int failed;
 
-    const int tid = threadIdx.x, warp = tid >> 5;
-    if (tid == 0) failed = *reinterpret_cast<volatile int *>(status);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        failed = *reinterpret_cast<volatile int *>(status);
+        uint64_t pm = 0;
+        for (int i = 0; i < KQ; ++i) pm |= 1ull << a.pos[i];
+        uint64_t tm = pm;
+        for (int b = 0, cnt = 0; cnt < 7; ++b)
+            if (!((pm >> b) & 1)) { tm |= 1ull << b; ++cnt; }
+        for (int b = 0, j = 0; j < TB; ++b)
+            if ((tm >> b) & 1) tpos[j++] = b;
+        int L = 0;
+        while (L < TB && tpos[L] == L) ++L;
+        lrun = L;
+        pmask = pm;
+    }
     __syncthreads();
     if (failed) return;
     if (warp == 0) tmem_alloc(&tslot, NCOLS);
     if (tid == 0) {
-        mbar_init(&bar_a, kRows);
-        mbar_init(&bar_d[0], 1);
-        mbar_init(&bar_d[1], 1);
-        mbar_init(&bar_e[0], kRows);
-        mbar_init(&bar_e[1], kRows);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&bar_full[s], 1);
+            mbar_init(&bar_empty[s], kRows);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_a[b], kRows);
+            mbar_init(&bar_d[b], 1);
+            mbar_init(&bar_e[b], kRows);
+        }
     }
-    for (int c = tid; c < D; c += kPipeThreads) {
-        uint64_t o = 0;
+    for (int c = tid; c < D; c += kStreamThreads) {
+        uint32_t u = 0;
+        uint64_t g = 0;
         for (int i = 0; i < KQ; ++i)
-            if ((c >> i) & 1) o |= 1ull << a.pos[i];
-        dep[c] = o;
+            if ((c >> i) & 1) {
+                g |= 1ull << a.pos[i];
+                for (int j = 0; j < TB; ++j)
+                    if (tpos[j] == a.pos[i]) u |= 1u << j;
+            }
+        uc[c] = u;
+        gc[c] = g;
     }
     {
         const float4 *src = reinterpret_cast<const float4 *>(bmat);
         float4 *dst = reinterpret_cast<float4 *>(b_hi);
-        for (int e = tid; e < 2 * N * K / 4; e += kPipeThreads) dst[e] = __ldg(src + e);
+        for (int e = tid; e < 2 * N * K / 4; e += kStreamThreads) dst[e] = __ldg(src + e);
     }
     fence_async_smem();
     tc_fence_before();
@@ -407,80 +501,159 @@ __global__ void __launch_bounds__(kPipeThreads, 2) k_fused_pipe(float *__restric
     const uint64_t step = gridDim.x;
     const int iters = ((uint64_t)blockIdx.x < ntiles) ? (int)((ntiles - 1 - blockIdx.x) / step + 1) : 0;
 
-    auto row_base = [&](uint64_t t, int r) {
-        uint64_t base = t * kRows + (uint64_t)r;
+    // global index of tile t's first amplitude: zero bits inserted at T
+    auto tile_base = [&](uint64_t t) {
+        uint64_t b = t;
 #pragma unroll
-        for (int i = 0; i < KQ; ++i) {
-            const int p = a.pos[i];
-            base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1ull));
+        for (int j = 0; j < TB; ++j) {
+            const int p = tpos[j];
+            b = ((b >> p) << (p + 1)) | (b & ((1ull << p) - 1ull));
         }
-        return base;
+        return b;
+    };
+    // row r: its tile-local offset and global offset (row bits = T minus the block bits)
+    auto row_offsets = [&](int r, uint32_t &u, uint64_t &g) {
+        u = 0;
+        g = 0;
+        const uint64_t pm = pmask;
+        for (int j = 0, i = 0; j < TB; ++j) {
+            const int p = tpos[j];
+            if ((pm >> p) & 1) continue;
+            if ((r >> i) & 1) {
+                u |= 1u << j;
+                g |= 1ull << p;
+            }
+            ++i;
+        }
     };
 
-    if (warp < 4) {
-        // producers: thread tid gathers row tid of every tile of this CTA
+    if (warp == 9) {
+        // loader warp: lane j copies run j of every tile
+        const int L = lrun;
+        const int nrun = 1 << (TB - L);
+        const uint32_t rbytes = 8u << L;
+        uint64_t go = 0;
+        for (int b = 0; b < TB - L; ++b)
+            if ((lane >> b) & 1) go |= 1ull << tpos[L + b];
+        int issued = 0;
         for (int i = 0; i < iters && !*vfailed; ++i) {
-            const uint64_t base = row_base(blockIdx.x + (uint64_t)i * step, tid);
-            float2 v[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) v[c] = *reinterpret_cast<const float2 *>(st + 2 * (base | dep[c]));
-            // the MMA of the previous tile must be done reading A
-            if (i >= 1 && !mbar_wait_bounded(&bar_d[(i - 1) & 1], (uint32_t)(((i - 1) >> 1) & 1))) {
+            const int s = i % S;
+            if (i >= S && !mbar_wait_bounded(&bar_empty[s], (uint32_t)((i / S - 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step);
+            if (lane == 0) mbar_arrive_expect_tx(&bar_full[s], TBYTES);
+            __syncwarp();
+            if (lane < nrun)
+                bulk_load(stage + (size_t)s * TAMP + ((size_t)lane << L), st + 2 * (base | go), rbytes, &bar_full[s]);
+            issued = i + 1;
+        }
+        // copies still in flight land before the CTA may exit
+        if (lane == 0)
+            for (int i = (issued > S ? issued - S : 0); i < issued; ++i)
+                mbar_wait_bounded(&bar_full[i % S], (uint32_t)((i / S) & 1));
+    } else if (warp < 4) {
+        uint32_t ur;
+        uint64_t gr;
+        row_offsets(tid, ur, gr);
+        // Bank spreading: with zc block bits among tile-local bits 0..3, the
+        // 16 threads of a half-warp differ in their row's zr = 4 - zc low
+        // tile bits only, so thread r reads column c ^ x with
+        // x = (r >> zr) mod 2^zc: the low 4 tile-local bits (one 8-byte word
+        // per bank pair) are then distinct across the half-warp.  uc is
+        // linear over XOR, so column c ^ x sits at (ur | uc[c]) ^ uc[x].
+        int zc = 0;
+        for (int j = 0; j < 4; ++j) zc += (int)((pmask >> tpos[j]) & 1);
+        const int x = (tid >> (4 - zc)) & ((1 << zc) - 1);
+        const uint32_t ux = uc[x];
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int s = i % S;
+            if (!mbar_wait_bounded(&bar_full[s], (uint32_t)((i / S) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            const float2 *sg = stage + (size_t)s * TAMP;
+            float2 v[D];            // v[j] = column j ^ x of row tid
 #pragma unroll
-            for (int c = 0; c < D; ++c) {
-                const float hr = tf32_trunc(v[c].x), hi = tf32_trunc(v[c].y);
-                const uint32_t off = kmajor_off(tid, 2 * c, K);
-                *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_hi) + off) = make_float2(hr, hi);
-                *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_lo) + off) =
-                    make_float2(v[c].x - hr, v[c].y - hi);
+            for (int j = 0; j < D; ++j) v[j] = sg[(ur | uc[j]) ^ ux];
+            mbar_arrive(&bar_empty[s]);
+            // A buffer i & 1: the MMAs of tile i - 2 must be done reading it
+            if (i >= 2 && !mbar_wait_bounded(&bar_d[i & 1], (uint32_t)(((i - 2) >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            unsigned char *ahi = reinterpret_cast<unsigned char *>(abuf + (size_t)(i & 1) * 2 * ABUF);
+            unsigned char *alo = ahi + ABUF * sizeof(float);
+#pragma unroll
+            for (int j = 0; j < D; j += 2) {
+                // columns 2p, 2p + 1 (p = (j ^ x) / 2) = one 16-byte row chunk
+                // of a core matrix; x odd swaps which register holds which
+                const uint32_t off = kmajor_off(tid, 2 * ((j ^ x) & ~1), K);
+                const float2 e0 = (x & 1) ? v[j + 1] : v[j], e1 = (x & 1) ? v[j] : v[j + 1];
+                const float h0 = tf32_trunc(e0.x), h1 = tf32_trunc(e0.y);
+                const float h2 = tf32_trunc(e1.x), h3 = tf32_trunc(e1.y);
+                *reinterpret_cast<float4 *>(ahi + off) = make_float4(h0, h1, h2, h3);
+                *reinterpret_cast<float4 *>(alo + off) = make_float4(e0.x - h0, e0.y - h1, e1.x - h2, e1.y - h3);
             }
             fence_async_smem();
-            mbar_arrive(&bar_a);
+            mbar_arrive(&bar_a[i & 1]);
         }
     } else if (warp < 8) {
         // consumers: warp w reads TMEM lanes 32 (w - 4) .. + 31 = rows of the tile
         const int r = tid - 128;
+        uint32_t ur;
+        uint64_t gr;
+        row_offsets(r, ur, gr);
         for (int i = 0; i < iters && !*vfailed; ++i) {
             const int sb = i & 1;
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
             if (!mbar_wait_bounded(&bar_d[sb], (uint32_t)((i >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
             tc_fence_after();
-            const uint64_t base = row_base(blockIdx.x + (uint64_t)i * step, r);
             const uint32_t lane_base = taddr + (uint32_t)(sb * NC) + ((uint32_t)((warp - 4) * 32) << 16);
-#pragma unroll 1
-            for (int col = 0; col < N; col += 16) {
-                float v[16];
-                tmem_ld16(lane_base + (uint32_t)col, v);
+            constexpr int W = N < 32 ? N : 32;            // columns per round (16 complex at most)
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
+            for (int col = 0; col < N; col += W) {
+                uint32_t hi[W], lo[W];
+                if constexpr (W == 32) {
+                    tmem_ld32_nowait(lane_base + (uint32_t)col, hi);
+                    tmem_ld32_nowait(lane_base + (uint32_t)(N + col), lo);
+                } else {
+                    static_assert(W == 16, "N is 16, 32 or 64");
+                    tmem_ld16_nowait(lane_base + (uint32_t)col, hi);
+                    tmem_ld16_nowait(lane_base + (uint32_t)(N + col), lo);
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int e = 0; e < W / 2; ++e) {
                     const int c = col / 2 + e;
-                    *reinterpret_cast<float2 *>(st + 2 * (base | dep[c])) = make_float2(v[2 * e], v[2 * e + 1]);
+                    *reinterpret_cast<float2 *>(st + 2 * (base | gc[c])) =
+                        make_float2(__uint_as_float(hi[2 * e]) + __uint_as_float(lo[2 * e]),
+                                    __uint_as_float(hi[2 * e + 1]) + __uint_as_float(lo[2 * e + 1]));
                 }
             }
             tc_fence_before();
             mbar_arrive(&bar_e[sb]);
         }
-    } else if ((tid & 31) == 0) {
+    } else if (lane == 0) {
         // issuer (warp 8, one thread)
-        const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo);
-        const uint32_t sb_hi = smem_u32(b_hi), sb_lo = smem_u32(b_lo);
+        const uint32_t sb_hi = smem_u32(b_hi);
         for (int i = 0; i < iters && !*vfailed; ++i) {
             const int sb = i & 1;
-            if (!mbar_wait_bounded(&bar_a, (uint32_t)(i & 1))) { *vfailed = 1; break; }
+            if (!mbar_wait_bounded(&bar_a[sb], (uint32_t)((i >> 1) & 1))) { *vfailed = 1; break; }
             if (i >= 2 && !mbar_wait_bounded(&bar_e[sb], (uint32_t)(((i - 2) >> 1) & 1))) { *vfailed = 1; break; }
             tc_fence_after();
+            const uint32_t sa_hi = smem_u32(abuf + (size_t)sb * 2 * ABUF), sa_lo = sa_hi + ABUF * sizeof(float);
             const uint32_t d = taddr + (uint32_t)(sb * NC);
 #pragma unroll 1
             for (int ks = 0; ks < K / 8; ++ks) {
                 const uint32_t ko = (uint32_t)ks * 256;
-                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC, ks > 0);
-                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_lo + ko, 128, SBO), IDESC, 1);
-                mma_tf32(d, make_desc(sa_lo + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC, 1);
+                // B rows 0 .. 2N-1 = W_hi then W_lo (contiguous, same 8-row group stride)
+                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC2, ks > 0);
+                mma_tf32(d, make_desc(sa_lo + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC1, 1);
             }
             mma_commit(&bar_d[sb]);
         }
@@ -496,10 +669,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2) k_fused_pipe(float *__restric
 }
 
 template <int KQ>
-size_t pipe_smem_bytes()
+size_t stream_smem_bytes()
 {
     constexpr int K = 2 << KQ;
-    return (size_t)(2 * kRows * K + 2 * K * K) * sizeof(float);
+    return (size_t)StreamCfg<KQ>::S * ((size_t)kRows << KQ) * 8 + (size_t)(4 * kRows * K + 2 * K * K) * sizeof(float);
 }
 
 template <int KQ>
@@ -590,6 +763,28 @@ std::vector<Block> form_blocks(const std::vector<SGate> &g, int k, int n)
     return blocks;
 }
 
+// CTAs of one kernel that fit on an SM at once: registers (allocated per warp
+// in units of 256), shared memory (static + dynamic + the per-CTA reservation)
+// and threads.
+int resident_ctas(int dev, const void *fn, int threads, size_t dyn_smem)
+{
+    cudaFuncAttributes fa{};
+    int regs_sm = 0, smem_sm = 0, smem_rsv = 0, thr_sm = 0;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess)
+        return 0;
+    const int warps = (threads + 31) / 32;
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_warp > 0 ? (regs_sm / regs_warp) / warps : 0;
+    const size_t smem_cta = fa.sharedSizeBytes + dyn_smem + (size_t)smem_rsv;
+    const int by_smem = (int)((size_t)smem_sm / smem_cta);
+    const int by_thr = thr_sm / (warps * 32);
+    return std::min(by_regs, std::min(by_smem, by_thr));
+}
+
 template <int KQ>
 int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Block> &blocks)
 {
@@ -652,22 +847,27 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
         if ((rc = launch_end(s, "fused build"))) break;
         const size_t sma = apply_smem_bytes<KQ>();
         cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
+        cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
         const uint64_t rows = 1ull << (n - KQ);
-        // k = 5: the persistent pipelined kernel, one CTA per SM slot it fits
-        // (for k = 3, 4 the one-tile-per-CTA kernel keeps more rows in flight
-        // and measured faster; k = 6 does not fit W and two A buffers)
+        // k <= 5: the persistent streamed kernel, as many CTAs as fit at once
+        // (k = 6 does not fit W, a stage ring and A in shared memory)
         int pipe_grid = 0;
         size_t smp = 0;
-        if constexpr (KQ == 5) {
-            smp = pipe_smem_bytes<KQ>();
-            cudaFuncSetAttribute(k_fused_pipe<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
-            int per_sm = 0;
-            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_pipe<KQ>, kPipeThreads, smp) !=
-                    cudaSuccess || per_sm < 1) {
-                rc = fail(SIM_ECUDA, "fused apply: pipelined kernel does not fit on an SM");
+        if constexpr (KQ <= 5) {
+            smp = stream_smem_bytes<KQ>();
+            cudaFuncSetAttribute(k_fused_stream<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
+            cudaFuncSetAttribute(k_fused_stream<KQ>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+            // CTAs per SM from the kernel's own register and shared-memory
+            // footprint; the CTAs never wait on one another, so this only
+            // sets the grid
+            int per_sm = resident_ctas(s->device, (const void *)k_fused_stream<KQ>, kStreamThreads, smp);
+            if (per_sm < 1) {
+                rc = fail(SIM_ECUDA, "fused apply: streamed kernel does not fit on an SM");
                 break;
             }
-            const int cols = 2 * ((2 << KQ) < 32 ? 32 : (2 << KQ));     // TMEM columns per CTA
+            const int cols = 4 * (2 << KQ);                              // TMEM columns per CTA
             per_sm = std::min(per_sm, 512 / cols);
             const uint64_t tiles = (rows + kRows - 1) / kRows;
             pipe_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms * per_sm);
@@ -684,8 +884,8 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
             // tensor-core flops: three real GEMMs [rows x K] x [K x K] (3xTF32)
             launch_begin(s, KC_FUSED, 2.0 * (double)s->bytes, 3.0 * 2.0 * (double)rows * K * K);
             const float *bm = (const float *)(scratch + o_b) + b * 2 * (size_t)K * K;
-            if constexpr (KQ == 5) {
-                k_fused_pipe<KQ><<<(unsigned)pipe_grid, kPipeThreads, smp, s->stream>>>(
+            if constexpr (KQ <= 5) {
+                k_fused_stream<KQ><<<(unsigned)pipe_grid, kStreamThreads, smp, s->stream>>>(
                     (float *)s->amps, bm, a, (rows + kRows - 1) / kRows, s->dev_status);
             } else {
                 k_fused_apply<KQ><<<(unsigned)((rows + kRows - 1) / kRows), kRows, sma, s->stream>>>(

@@ -1,12 +1,19 @@
 // learned.cu -- SIM_PLAN_LEARNED: the circuit is cut into windows of
-// consecutive gates; for every window and every feasible plan variant the
-// host computes a feature row, the cost model (mlp.cu) predicts the log run
-// time of all rows in one batched forward pass on the GPU, and each window is
-// applied with its cheapest variant.  Without a model the greedy fixed-k tile
-// planner (the staged plan) is used: it is both the fallback and the judge the
-// learned plans are measured against.
+// consecutive gates; for every window, and for the whole circuit, and every
+// feasible plan variant the host computes a feature row (rows in parallel on
+// the host cores), the cost model (mlp.cu) predicts the log run time of all
+// rows in one batched forward pass on the GPU, and the cheaper of two plans
+// runs: each window with its own cheapest variant, or the whole circuit with
+// one variant (one variant over many windows lets the block and pass planners
+// work across window boundaries, which per-window predictions cannot see).
+// Without a model the greedy fixed-k tile planner (the staged plan) is used:
+// it is both the fallback and the judge the learned plans are measured
+// against.
+#include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "internal.cuh"
@@ -20,6 +27,26 @@ namespace {
 struct Window {
     size_t first, count;
 };
+
+// f(0) .. f(count - 1) on up to 16 host threads
+template <typename F>
+void parallel_for(size_t count, F f)
+{
+    size_t nt = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
+    nt = std::min(nt, count);
+    if (nt <= 1) {
+        for (size_t i = 0; i < count; ++i) f(i);
+        return;
+    }
+    std::atomic<size_t> next{0};
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (size_t t = 0; t < nt; ++t)
+        th.emplace_back([&] {
+            for (size_t i; (i = next.fetch_add(1)) < count;) f(i);
+        });
+    for (auto &x : th) x.join();
+}
 
 int variant_opts(int v, sim_plan_opts *o)
 {
@@ -87,26 +114,60 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
         st.tile_qubits = o.tile_qubits;
         return apply_circuit_staged(s, gates, n_gates, st);
     }
+    if (n_gates == 0) {
+        s->last_plan.clear();
+        return SIM_OK;
+    }
     // windows of about eight layers of single-qubit gates
     const size_t W = (size_t)std::max(64, 8 * s->n);
     std::vector<Window> win;
     for (size_t f = 0; f < n_gates; f += W) win.push_back(Window{f, std::min(W, n_gates - f)});
+    // candidate segments: every window, and the whole circuit (segment nw)
+    const size_t nw = win.size();
+    std::vector<Window> seg(win);
+    if (nw > 1) seg.push_back(Window{0, n_gates});
+    std::vector<std::pair<size_t, int>> cand;
+    for (size_t w = 0; w < seg.size(); ++w)
+        for (int v = 0; v < SIM_VARIANTS; ++v)
+            if (feasible(s->n, s->dtype, v)) cand.push_back({w, v});
+    std::vector<float> feat(cand.size() * SIM_FEATURES);
+    std::vector<char> ok(cand.size(), 0);
+    parallel_for(cand.size(), [&](size_t r) {
+        const Window &w = seg[cand[r].first];
+        ok[r] = plan_features(s->n, s->dtype, gates + w.first, w.count, cand[r].second,
+                              feat.data() + r * SIM_FEATURES) == SIM_OK;
+    });
     std::vector<float> rows;
     std::vector<std::pair<size_t, int>> who;
-    for (size_t w = 0; w < win.size(); ++w)
-        for (int v = 0; v < SIM_VARIANTS; ++v) {
-            float f[SIM_FEATURES];
-            if (plan_features(s->n, s->dtype, gates + win[w].first, win[w].count, v, f) != SIM_OK) continue;
-            rows.insert(rows.end(), f, f + SIM_FEATURES);
-            who.push_back({w, v});
+    for (size_t r = 0; r < cand.size(); ++r)
+        if (ok[r]) {
+            rows.insert(rows.end(), feat.begin() + r * SIM_FEATURES, feat.begin() + (r + 1) * SIM_FEATURES);
+            who.push_back(cand[r]);
         }
     std::vector<float> pred(who.size());
     if (int rc = sim_mlp_forward((qsim_mlp *)s->cost_model, rows.data(), (int64_t)who.size(), pred.data(), 0)) return rc;
-    std::vector<int> best(win.size(), -1);
-    std::vector<float> bestp(win.size(), 0.f);
+    std::vector<int> best(nw, -1);
+    std::vector<float> bestp(nw, 0.f);
+    int whole_v = -1;
+    float whole_p = 0.f;
     for (size_t r = 0; r < who.size(); ++r) {
         const size_t w = who[r].first;
-        if (best[w] < 0 || pred[r] < bestp[w]) { best[w] = who[r].second; bestp[w] = pred[r]; }
+        if (w < nw) {
+            if (best[w] < 0 || pred[r] < bestp[w]) { best[w] = who[r].second; bestp[w] = pred[r]; }
+        } else if (whole_v < 0 || pred[r] < whole_p) {
+            whole_v = who[r].second;
+            whole_p = pred[r];
+        }
+    }
+    // predicted times: the model's target is a log time, so windows add in exp
+    if (whole_v >= 0) {
+        double mix = 0;
+        bool all = true;
+        for (size_t w = 0; w < nw; ++w) {
+            if (best[w] < 0) all = false;
+            else mix += std::exp((double)bestp[w]);
+        }
+        if (!all || std::exp((double)whole_p) <= mix) std::fill(best.begin(), best.end(), whole_v);
     }
     s->last_plan.assign(best.begin(), best.end());
     // consecutive windows with the same variant run as one call, so the tile

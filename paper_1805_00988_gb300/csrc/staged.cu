@@ -44,20 +44,26 @@ k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
     uint64_t base = 0;
     for (int i = 0; i < geo.n_outer; ++i) base |= ((tile >> i) & 1ull) << geo.outer_pos[i];
 
-    // global offsets in the I/O layout
-    uint64_t toff = base;
+    // global offsets in the I/O layout: the thread's offset and one per
+    // register bit.  They are formed again for the store (from inputs the
+    // compiler cannot prove equal) instead of being held live across the
+    // gate sequence, which would spill at two CTAs per SM.
+    uint64_t toff, roff[RB];
+    auto io_offsets = [&](int t, uint64_t b0) {
+        toff = b0;
 #pragma unroll
-    for (int i = 0; i < kThrBits; ++i) {
-        const int b = thr_local(M, RB, VEC, 0, i);
-        const uint64_t g = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
-        if ((tid >> i) & 1) toff |= g;
-    }
-    uint64_t roff[RB];
+        for (int i = 0; i < kThrBits; ++i) {
+            const int b = thr_local(M, RB, VEC, 0, i);
+            const uint64_t g = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
+            if ((t >> i) & 1) toff |= g;
+        }
 #pragma unroll
-    for (int j = 0; j < RB; ++j) {
-        const int b = reg_local(M, RB, VEC, 0, j);
-        roff[j] = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
-    }
+        for (int j = 0; j < RB; ++j) {
+            const int b = reg_local(M, RB, VEC, 0, j);
+            roff[j] = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
+        }
+    };
+    io_offsets(tid, base);
 
     Regs<R, RA> v;
     if constexpr (VEC == 2) {
@@ -84,6 +90,12 @@ k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
     }
 
     apply_ops<R, M>(v, ops, nops, base, tid, sm);
+    {
+        int t2 = tid;
+        uint64_t b2 = base;
+        asm volatile("" : "+r"(t2), "+l"(b2));
+        io_offsets(t2, b2);
+    }
     // the planner always ends a pass in layout 0
     if constexpr (VEC == 2) {
 #pragma unroll

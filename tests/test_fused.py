@@ -54,11 +54,26 @@ def test_fused_single_block(gsim, orc, k):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("n,k", [(10, 3), (12, 4), (13, 5), (14, 6), (16, 3), (18, 5), (20, 6)])
+@pytest.mark.parametrize("n,k", [(10, 3), (11, 4), (12, 5), (12, 4), (13, 5), (14, 6), (16, 3), (18, 5), (20, 6)])
 def test_fused_random_circuits(gsim, orc, n, k):
     g = C.concat([C.random_gates(n, 300, seed=n * 10 + k), C.qft(n)])
     st = gsim.State(n, "c64")
     psi = C.random_state(n, seed=n)
+    st.load(psi)
+    st.apply(g, plan="fused", fuse_k=k)
+    check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))
+    st.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_fused_many_tiles_per_cta(gsim, orc, k):
+    """24 qubits: every CTA of the persistent kernel streams many tiles, so
+    the stage ring and both accumulators wrap around many times."""
+    n = 24
+    g = C.concat([C.random_gates(n, 120, seed=40 + k), C.haar_cz(n, 2, seed=k)])
+    st = gsim.State(n, "c64")
+    psi = C.random_state(n, seed=7 + k)
     st.load(psi)
     st.apply(g, plan="fused", fuse_k=k)
     check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))

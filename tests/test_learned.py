@@ -13,7 +13,9 @@ def trained():
     if not torch.cuda.is_available():
         pytest.skip("no GPU")
     from paper_1805_00988_gb300 import costmodel, sim
-    X, T, meta = costmodel.collect(n_list=(18, 20, 22), reps=3, max_windows=3)
+    # 22 and 24 qubits: large enough that kernel time, not launch overhead,
+    # sets the timings; the gain test below runs two qubits further out
+    X, T, meta = costmodel.collect(n_list=(22, 24), reps=3, max_windows=3)
     m, loss = costmodel.train(X, T, steps=2000)
     return sim, costmodel, m, X, T, meta
 
