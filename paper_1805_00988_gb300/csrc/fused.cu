@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(kRows, 1) k_fused_apply(float *__restrict__ st
 //       bytes landed;
 //   warps 0-3: thread r takes row r of a landed stage, frees the stage, and
 //       writes the row's TF32 hi / lo parts (K-major core-matrix layout) into
-//       one of two A buffers once the MMAs that last read that buffer are done;
+//       one of AB A buffers once the MMAs that last read that buffer are done;
 //   warp 8 (one thread): per K-step one MMA A_hi x [W_hi | W_lo] (N = 2K) and
 //       one A_lo x W_hi (N = K) into one of two TMEM accumulators, so that
 //       columns [0, K) hold A_hi W_hi + A_lo W_hi and [K, 2K) hold A_hi W_lo;
@@ -406,11 +406,12 @@ __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint3
                  : "memory");
 }
 
-// S: stages in the ring; MINB: CTAs per SM the registers are budgeted for
+// S: stages in the ring; AB: A buffers (1 or 2); MINB: CTAs per SM the
+// registers are budgeted for
 template <int KQ> struct StreamCfg;
-template <> struct StreamCfg<3> { static constexpr int S = 3, MINB = 2; };
-template <> struct StreamCfg<4> { static constexpr int S = 2, MINB = 2; };
-template <> struct StreamCfg<5> { static constexpr int S = 2, MINB = 1; };
+template <> struct StreamCfg<3> { static constexpr int S = 3, AB = 2, MINB = 2; };
+template <> struct StreamCfg<4> { static constexpr int S = 2, AB = 2, MINB = 2; };
+template <> struct StreamCfg<5> { static constexpr int S = 2, AB = 2, MINB = 1; };
 
 template <int KQ>
 __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
@@ -418,6 +419,8 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
                    int *__restrict__ status)
 {
     constexpr int S = StreamCfg<KQ>::S;
+    constexpr int AB = StreamCfg<KQ>::AB;
+    static_assert(AB == 1 || AB == 2, "one or two A buffers");
     constexpr int D = 1 << KQ;
     constexpr int K = 2 * D;
     constexpr int N = K;
@@ -436,7 +439,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
     extern __shared__ __align__(1024) unsigned char smem[];
     float2 *stage = reinterpret_cast<float2 *>(smem);                           // S x TAMP amplitudes
     float *abuf = reinterpret_cast<float *>(smem + (size_t)S * TBYTES);         // [buffer][hi | lo] kRows x K
-    float *b_hi = abuf + 4 * ABUF;                                               // N x K, then b_lo (N x K)
+    float *b_hi = abuf + 2 * AB * ABUF;                                          // N x K, then b_lo (N x K)
     __shared__ uint64_t bar_full[S], bar_empty[S], bar_a[2], bar_d[2], bar_e[2];
     __shared__ uint32_t tslot;
     __shared__ int tpos[TB];          // global bit of tile-local bit j (ascending)
@@ -578,12 +581,12 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
 #pragma unroll
             for (int j = 0; j < D; ++j) v[j] = sg[(ur | uc[j]) ^ ux];
             mbar_arrive(&bar_empty[s]);
-            // A buffer i & 1: the MMAs of tile i - 2 must be done reading it
-            if (i >= 2 && !mbar_wait_bounded(&bar_d[i & 1], (uint32_t)(((i - 2) >> 1) & 1))) {
+            // A buffer i % AB: the MMAs of tile i - AB must be done reading it
+            if (i >= AB && !mbar_wait_bounded(&bar_d[(i - AB) & 1], (uint32_t)(((i - AB) >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
-            unsigned char *ahi = reinterpret_cast<unsigned char *>(abuf + (size_t)(i & 1) * 2 * ABUF);
+            unsigned char *ahi = reinterpret_cast<unsigned char *>(abuf + (size_t)(i % AB) * 2 * ABUF);
             unsigned char *alo = ahi + ABUF * sizeof(float);
 #pragma unroll
             for (int j = 0; j < D; j += 2) {
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
                 *reinterpret_cast<float4 *>(alo + off) = make_float4(e0.x - h0, e0.y - h1, e1.x - h2, e1.y - h3);
             }
             fence_async_smem();
-            mbar_arrive(&bar_a[i & 1]);
+            mbar_arrive(&bar_a[i % AB]);
         }
     } else if (warp < 8) {
         // consumers: warp w reads TMEM lanes 32 (w - 4) .. + 31 = rows of the tile
@@ -643,10 +646,10 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
         const uint32_t sb_hi = smem_u32(b_hi);
         for (int i = 0; i < iters && !*vfailed; ++i) {
             const int sb = i & 1;
-            if (!mbar_wait_bounded(&bar_a[sb], (uint32_t)((i >> 1) & 1))) { *vfailed = 1; break; }
+            if (!mbar_wait_bounded(&bar_a[i % AB], (uint32_t)((i / AB) & 1))) { *vfailed = 1; break; }
             if (i >= 2 && !mbar_wait_bounded(&bar_e[sb], (uint32_t)(((i - 2) >> 1) & 1))) { *vfailed = 1; break; }
             tc_fence_after();
-            const uint32_t sa_hi = smem_u32(abuf + (size_t)sb * 2 * ABUF), sa_lo = sa_hi + ABUF * sizeof(float);
+            const uint32_t sa_hi = smem_u32(abuf + (size_t)(i % AB) * 2 * ABUF), sa_lo = sa_hi + ABUF * sizeof(float);
             const uint32_t d = taddr + (uint32_t)(sb * NC);
 #pragma unroll 1
             for (int ks = 0; ks < K / 8; ++ks) {
@@ -672,7 +675,8 @@ template <int KQ>
 size_t stream_smem_bytes()
 {
     constexpr int K = 2 << KQ;
-    return (size_t)StreamCfg<KQ>::S * ((size_t)kRows << KQ) * 8 + (size_t)(4 * kRows * K + 2 * K * K) * sizeof(float);
+    return (size_t)StreamCfg<KQ>::S * ((size_t)kRows << KQ) * 8 +
+           (size_t)(2 * StreamCfg<KQ>::AB * kRows * K + 2 * K * K) * sizeof(float);
 }
 
 template <int KQ>

@@ -8,10 +8,11 @@
 //
 // Sampling (§2.4: many outcomes from one state without re-running the gates)
 // is an inverse CDF over the FP64 prefix of |a_j|^2 that is never
-// materialised for the whole state: per-block sums, one scan over the block
-// sums, shots bucketed by block (counting sort), then one CTA per touched
-// block scans that block in shared memory and resolves its shots.  About two
-// reads of the state in total.
+// materialised for the whole state: sums per sub-block of 256 amplitudes and
+// per block of 32 sub-blocks (one read of the state), one scan over the block
+// sums, shots bucketed by block (counting sort), then per shot one warp picks
+// the sub-block from the block's sub-sums and scans only those 256
+// amplitudes (2 KB of complex64 per shot instead of the whole block).
 #include <cmath>
 
 #include "internal.cuh"
@@ -98,6 +99,23 @@ __device__ __forceinline__ double sq<float>(float re, float im)
 }
 
 
+// a += |re + i im|^2 as two FP64 FMAs (both squares exact in FP64 for a
+// complex64 amplitude)
+template <typename R>
+__device__ __forceinline__ void acc_sq(double &a, R re, R im)
+{
+    const double r = (double)re, i = (double)im;
+    a = fma(r, r, a);
+    a = fma(i, i, a);
+}
+template <>
+__device__ __forceinline__ void acc_sq<float>(double &a, float re, float im)
+{
+    const double r = widen(re), i = widen(im);
+    a = fma(r, r, a);
+    a = fma(i, i, a);
+}
+
 // VEC amplitudes per 16-byte vector: 2 for complex64, 1 for complex128.
 // raw() issues the load only; sq2() turns it into |a|^2 in FP64.  Callers
 // issue a batch of raw loads before any arithmetic so that each thread keeps
@@ -113,6 +131,10 @@ template <> struct AV<float> {
         p[1] = sq<float>(x.z, x.w);
     }
     __device__ __forceinline__ static void load(const float *st, uint64_t v, double p[2]) { sq2(raw(st, v), p); }
+    __device__ __forceinline__ static void parts(const Raw &x, float re[2], float im[2])
+    {
+        re[0] = x.x; im[0] = x.y; re[1] = x.z; im[1] = x.w;
+    }
 };
 template <> struct AV<double> {
     static constexpr int VEC = 1;
@@ -124,33 +146,45 @@ template <> struct AV<double> {
         p[1] = 0.0;
     }
     __device__ __forceinline__ static void load(const double *st, uint64_t v, double p[2]) { sq2(raw(st, v), p); }
+    __device__ __forceinline__ static void parts(const Raw &x, double re[1], double im[1])
+    {
+        re[0] = x.x; im[0] = x.y;
+    }
 };
 
 constexpr int kBatch = 8;     // 16-byte loads in flight per thread
 
 // Masked FP64 sums over a contiguous range per block.
-//   RED_NORM: out0 = sum |a|^2
+//   RED_NORM: out0 = sum |a|^2                    (two FP64 FMAs per amplitude)
 //   RED_BIT : out0 = sum over bit q = 0, out1 = sum over bit q = 1
-//   RED_EXPZ: out0 = sum |a_x|^2 (n - 2 popcount x)
-template <typename R>
+//   RED_EXPZ: out0 = sum |a_x|^2 (n - 2 popcount x)  (weights from a table)
+template <typename R, int MODE>
 __global__ void __launch_bounds__(kRedThreads) k_masked_sum(const R *__restrict__ st, uint64_t nvec, uint64_t per,
-                                                            int mode, int q, int n, double *__restrict__ partial)
+                                                            int q, int n, double *__restrict__ partial)
 {
     constexpr int VEC = AV<R>::VEC;
     __shared__ double sh[2 * kRedThreads / 32];
+    __shared__ double wtab[64];                 // RED_EXPZ: wtab[k] = n - 2k
+    if (MODE == RED_EXPZ) {
+        for (int k = threadIdx.x; k <= n; k += kRedThreads) wtab[k] = (double)(n - 2 * k);
+        __syncthreads();
+    }
     const uint64_t lo = (uint64_t)blockIdx.x * per;
     const uint64_t hi = min(nvec, lo + per);
     double a = 0.0, b = 0.0;
-    auto add = [&](uint64_t v, const double p[2]) {
+    auto add = [&](uint64_t v, const typename AV<R>::Raw &x) {
+        R re[VEC], im[VEC];
+        AV<R>::parts(x, re, im);
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const uint64_t i = v * VEC + e;
-            if (mode == RED_NORM) {
-                a += p[e];
-            } else if (mode == RED_BIT) {
-                if ((i >> q) & 1ull) b += p[e]; else a += p[e];
+            if (MODE == RED_NORM) {
+                acc_sq<R>(a, re[e], im[e]);
+            } else if (MODE == RED_BIT) {
+                if ((i >> q) & 1ull) acc_sq<R>(b, re[e], im[e]);
+                else acc_sq<R>(a, re[e], im[e]);
             } else {
-                a += p[e] * (double)(n - 2 * __popcll(i));
+                a = fma(sq<R>(re[e], im[e]), wtab[__popcll(i)], a);
             }
         }
     };
@@ -160,17 +194,9 @@ __global__ void __launch_bounds__(kRedThreads) k_masked_sum(const R *__restrict_
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) x[u] = AV<R>::raw(st, v + (uint64_t)u * kRedThreads);
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            double p[2];
-            AV<R>::sq2(x[u], p);
-            add(v + (uint64_t)u * kRedThreads, p);
-        }
+        for (int u = 0; u < kBatch; ++u) add(v + (uint64_t)u * kRedThreads, x[u]);
     }
-    for (; v < hi; v += kRedThreads) {
-        double p[2];
-        AV<R>::load(st, v, p);
-        add(v, p);
-    }
+    for (; v < hi; v += kRedThreads) add(v, AV<R>::raw(st, v));
     block_sum2<kRedThreads>(a, b, sh);
     if (threadIdx.x == 0) {
         partial[2 * blockIdx.x] = a;
@@ -223,36 +249,117 @@ __global__ void k_collapse(R *__restrict__ st, uint64_t N, int q, int outcome, R
 constexpr int kSampleLog = 13;             // 8192 amplitudes per sampling block
 constexpr int kScanThreads = 1024;
 
-// FP64 sum of |a|^2 per block of bs amplitudes (one CTA per block).
+// Sub-blocks: min(256, bs) amplitudes, nsub = bs / sub <= 32 per block; lane
+// l of a warp takes amplitudes l*apl .. l*apl + apl - 1 of a sub-block
+// (apl = max(1, sub / 32)), so a lane-serial prefix followed by a warp scan
+// is the sub-block's prefix in index order.
+constexpr int kSubLog = 8;
+
+struct SubGeo {
+    uint32_t sub, nsub, apl, lanes;
+    __host__ __device__ explicit SubGeo(uint64_t bs)
+    {
+        sub = (uint32_t)(bs < (1ull << kSubLog) ? bs : (1ull << kSubLog));
+        nsub = (uint32_t)(bs / sub);
+        apl = sub >= 32 ? sub / 32 : 1;
+        lanes = sub / apl;
+    }
+};
+
+template <typename R> struct Amp;
+template <> struct Amp<float> { using T = float2; };
+template <> struct Amp<double> { using T = double2; };
+
+// FP64 |a|^2 of the apl amplitudes of lane `lane` in sub-block `j` (zeros for
+// idle lanes and unused slots), loads first
 template <typename R>
-__global__ void __launch_bounds__(256) k_block_sums(const R *__restrict__ st, uint64_t bs, double *__restrict__ bsum)
+__device__ __forceinline__ void lane_squares(const R *st, uint64_t base, const SubGeo &g, uint32_t j, int lane,
+                                             double p[8])
 {
-    constexpr int VEC = AV<R>::VEC;
-    __shared__ double sh[2 * 256 / 32];
-    const uint64_t nv = bs / VEC;
-    const uint64_t lo = (uint64_t)blockIdx.x * nv;
-    double a = 0.0, b = 0.0;
-    uint64_t v = threadIdx.x;
-    for (; v + (kBatch - 1) * 256 < nv; v += kBatch * 256) {
-        typename AV<R>::Raw x[kBatch];
+    using T = typename Amp<R>::T;
+    const T *a = reinterpret_cast<const T *>(st) + base + (uint64_t)j * g.sub + (uint64_t)lane * g.apl;
+    T x[8];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) x[u] = AV<R>::raw(st, lo + v + u * 256);
+    for (int e = 0; e < 8; ++e)
+        if ((uint32_t)lane < g.lanes && (uint32_t)e < g.apl) x[e] = a[e];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            double p[2];
-            AV<R>::sq2(x[u], p);
-            a += p[0];
-            if (VEC == 2) a += p[1];
+    for (int e = 0; e < 8; ++e) {
+        p[e] = 0.0;
+        if ((uint32_t)lane < g.lanes && (uint32_t)e < g.apl) acc_sq<R>(p[e], x[e].x, x[e].y);
+    }
+}
+
+// warp inclusive scan of lanes 0..31, fixed order (shfl_up doubling)
+__device__ __forceinline__ double warp_incl_scan(double x, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
+// One CTA (8 warps) per block of bs amplitudes.  Groups of 8 lanes own one
+// sub-block each (4 per warp, 32 per CTA): lane g of a group accumulates a
+// contiguous eighth of the sub-block with two FP64 FMAs per amplitude, and a
+// 3-step xor tree inside the group gives the sub-sum.  Warp 0 then scans the
+// block's sub-sums (warp_incl_scan) and the block sum is the scan's last
+// element -- k_resolve repeats that scan bit for bit.
+template <typename R>
+__global__ void __launch_bounds__(256) k_sub_sums(const R *__restrict__ st, uint64_t bs, double *__restrict__ sub,
+                                                  double *__restrict__ bsum)
+{
+    using T = typename Amp<R>::T;
+    const SubGeo g(bs);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t j = (uint32_t)(warp * 4 + (lane >> 3));       // this group's sub-block
+    const uint32_t gl = (uint32_t)(lane & 7);                    // lane within the group
+    const uint64_t base = (uint64_t)blockIdx.x * bs;
+    __shared__ double ss[32];
+    double t = 0.0;
+    if (j < g.nsub) {
+        const uint32_t per = g.sub >= 8 ? g.sub / 8 : 1;         // amplitudes per lane
+        if (gl * per < g.sub) {
+            const T *a = reinterpret_cast<const T *>(st) + base + (uint64_t)j * g.sub + (uint64_t)gl * per;
+            if (sizeof(R) == 4 && per == 32) {
+                // complex64, full sub-block: 16 aligned 16-byte loads per lane, 8 in flight
+                const float4 *a4 = reinterpret_cast<const float4 *>(a);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    float4 x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) x[u] = a4[h * 8 + u];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        acc_sq<float>(t, x[u].x, x[u].y);
+                        acc_sq<float>(t, x[u].z, x[u].w);
+                    }
+                }
+            } else {
+                for (uint32_t e0 = 0; e0 < per; e0 += 8) {
+                    T x[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (e0 + u < per) x[u] = a[e0 + u];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (e0 + u < per) acc_sq<R>(t, x[u].x, x[u].y);
+                }
+            }
         }
     }
-    for (; v < nv; v += 256) {
-        double p[2];
-        AV<R>::load(st, lo + v, p);
-        a += p[0];
-        if (VEC == 2) a += p[1];
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (gl == 0 && j < g.nsub) {
+        ss[j] = t;
+        sub[(uint64_t)blockIdx.x * g.nsub + j] = t;
     }
-    block_sum2<256>(a, b, sh);
-    if (threadIdx.x == 0) bsum[blockIdx.x] = a;
+    __syncthreads();
+    if (warp == 0) {
+        const double c = warp_incl_scan(((uint32_t)lane < g.nsub) ? ss[lane] : 0.0, lane);
+        if ((uint32_t)lane == g.nsub - 1) bsum[blockIdx.x] = c;
+    }
 }
 
 // Exclusive scan of nb values in one CTA: contiguous segments per thread,
@@ -325,83 +432,68 @@ __global__ void k_scatter(uint64_t shots, const uint32_t *__restrict__ shot_blk,
     }
 }
 
-// One CTA per block that received shots: |a|^2 of the block loaded into
-// shared memory (coalesced), inclusive FP64 scan there, then each shot takes
-// the smallest j with bexcl + C_j > u_s * total (none -> the block's last
-// non-zero amplitude).
+// One CTA per block that received shots.  Warp 0 rebuilds the block's
+// inclusive scan of sub-sums P (the same operations as k_sub_sums); warp w
+// then takes shots w, w + 8, ... of the block: t = u_s * total; the sub-block
+// is the first j with bexcl + P[j] > t; the warp scans its amplitudes (lane-
+// serial prefix, then a warp scan of lane totals) and the outcome is the
+// first index whose prefix exceeds t.  Where rounding leaves no crossing (t
+// within an ulp of a boundary), the last sub-block / amplitude with non-zero
+// probability is taken.
 template <typename R>
 __global__ void __launch_bounds__(256) k_resolve(const R *__restrict__ st, uint64_t bs, uint64_t seed,
                                                  const double *__restrict__ bexcl, const double *__restrict__ total,
-                                                 const uint32_t *__restrict__ counts,
+                                                 const double *__restrict__ sub, const uint32_t *__restrict__ counts,
                                                  const uint32_t *__restrict__ offs, const uint32_t *__restrict__ order,
                                                  uint64_t *__restrict__ out)
 {
-    constexpr int VEC = AV<R>::VEC;
-    extern __shared__ double cdf[];            // bs doubles
-    __shared__ double tsum[256];
-    __shared__ int last_nz;
     const uint32_t cnt = counts[blockIdx.x];
     if (cnt == 0) return;
-    if (threadIdx.x == 0) last_nz = -1;
+    const SubGeo g(bs);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __shared__ double P[32];
+    if (warp == 0)
+        P[lane] = warp_incl_scan(((uint32_t)lane < g.nsub) ? sub[(uint64_t)blockIdx.x * g.nsub + lane] : 0.0, lane);
     __syncthreads();
+    const double be = bexcl[blockIdx.x], tot = *total;
     const uint64_t base = (uint64_t)blockIdx.x * bs;
-    int my_last = -1;
-    auto put = [&](uint64_t v, const double p[2]) {
-#pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-            cdf[v * VEC + e] = p[e];
-            if (p[e] > 0.0) my_last = (int)(v * VEC + e);
-        }
-    };
-    uint64_t v = threadIdx.x;
-    for (; v + (kBatch - 1) * 256 < bs / VEC; v += kBatch * 256) {
-        typename AV<R>::Raw x[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) x[u] = AV<R>::raw(st, base / VEC + v + u * 256);
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            double p[2];
-            AV<R>::sq2(x[u], p);
-            put(v + u * 256, p);
-        }
-    }
-    for (; v < bs / VEC; v += 256) {
-        double p[2];
-        AV<R>::load(st, base / VEC + v, p);
-        put(v, p);
-    }
-    if (my_last >= 0) atomicMax(&last_nz, my_last);
-    __syncthreads();
-    const uint64_t per = (bs + 255) / 256;
-    const uint64_t lo = threadIdx.x * per, hi = min(bs, lo + per);
-    double acc = 0.0;
-    for (uint64_t i = lo; i < hi; ++i) {
-        acc += cdf[i];
-        cdf[i] = acc;
-    }
-    tsum[threadIdx.x] = acc;
-    __syncthreads();
-    for (int off = 1; off < 256; off <<= 1) {
-        double v = (threadIdx.x >= (unsigned)off) ? tsum[threadIdx.x - off] : 0.0;
-        __syncthreads();
-        tsum[threadIdx.x] += v;
-        __syncthreads();
-    }
-    const double pre = bexcl[blockIdx.x] + ((threadIdx.x > 0) ? tsum[threadIdx.x - 1] : 0.0);
-    for (uint64_t i = lo; i < hi; ++i) cdf[i] += pre;
-    __syncthreads();
-    const double tot = *total;
     const uint32_t o0 = offs[blockIdx.x];
-    for (uint32_t k = threadIdx.x; k < cnt; k += 256) {
+    const bool lane_nz = (uint32_t)lane < g.nsub && (lane == 0 ? P[0] > 0.0 : P[lane] > P[lane - 1]);
+    const unsigned sub_nz = __ballot_sync(0xffffffffu, lane_nz);
+    for (uint32_t k = warp; k < cnt; k += 8) {
         const uint32_t s = order[o0 + k];
         const double t = unif(seed, s) * tot;
-        uint64_t a = 0, b = bs;
-        while (a < b) {
-            const uint64_t mid = (a + b) >> 1;
-            if (cdf[mid] > t) b = mid; else a = mid + 1;
+        const unsigned hit = __ballot_sync(0xffffffffu, (uint32_t)lane < g.nsub && be + P[lane] > t);
+        const uint32_t j = hit ? (uint32_t)(__ffs(hit) - 1) : (sub_nz ? (uint32_t)(31 - __clz(sub_nz)) : 0u);
+        const double pre = be + (j > 0 ? P[j - 1] : 0.0);
+        double p[8];
+        lane_squares<R>(st, base, g, j, lane, p);
+        double c[8], run = 0.0;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            run += p[e];
+            c[e] = run;
         }
-        const uint64_t j = (a < bs) ? a : (uint64_t)max(last_nz, 0);
-        out[s] = base + j;
+        const double incl = warp_incl_scan(run, lane);
+        const double start = pre + (incl - run);
+        int first = -1, last_nz = -1;
+#pragma unroll
+        for (int e = 7; e >= 0; --e) {
+            if ((uint32_t)e < g.apl && start + c[e] > t) first = e;
+            if (last_nz < 0 && p[e] > 0.0) last_nz = e;
+        }
+        const unsigned fl = __ballot_sync(0xffffffffu, first >= 0);
+        uint64_t idx;
+        if (fl) {
+            const int L = __ffs(fl) - 1;
+            idx = (uint64_t)L * g.apl + (uint64_t)__shfl_sync(0xffffffffu, first, L);
+        } else {
+            const unsigned nl = __ballot_sync(0xffffffffu, last_nz >= 0);
+            const int L = nl ? 31 - __clz(nl) : 0;
+            const int e = __shfl_sync(0xffffffffu, last_nz, L);
+            idx = (uint64_t)L * g.apl + (uint64_t)(e > 0 ? e : 0);
+        }
+        if (lane == 0) out[s] = base + (uint64_t)j * g.sub + idx;
     }
 }
 
@@ -449,12 +541,17 @@ int reduce_sums(qsim_state *s, int mode, int qubit, double out[2])
     const uint64_t nvec = (s->dtype == SIM_C128) ? N : N / 2;
     const uint64_t per = (nvec + kRedBlocks - 1) / kRedBlocks;
     launch_begin(s, KC_REDUCE, (double)s->bytes);
-    if (s->dtype == SIM_C128)
-        k_masked_sum<double><<<kRedBlocks, kRedThreads, 0, s->stream>>>((const double *)s->amps, nvec, per, mode,
-                                                                       qubit, s->n, s->red_partial);
-    else
-        k_masked_sum<float><<<kRedBlocks, kRedThreads, 0, s->stream>>>((const float *)s->amps, nvec, per, mode,
-                                                                      qubit, s->n, s->red_partial);
+    if (s->dtype == SIM_C128) {
+        const double *st = (const double *)s->amps;
+        if (mode == RED_NORM) k_masked_sum<double, RED_NORM><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
+        else if (mode == RED_BIT) k_masked_sum<double, RED_BIT><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
+        else k_masked_sum<double, RED_EXPZ><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
+    } else {
+        const float *st = (const float *)s->amps;
+        if (mode == RED_NORM) k_masked_sum<float, RED_NORM><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
+        else if (mode == RED_BIT) k_masked_sum<float, RED_BIT><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
+        else k_masked_sum<float, RED_EXPZ><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
+    }
     int rc = launch_end(s, "masked sum");
     if (rc) return rc;
     launch_begin(s, KC_REDUCE);
@@ -502,16 +599,19 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
     const uint64_t N = 1ull << s->n;
     const uint64_t bs = (s->n >= kSampleLog) ? (1ull << kSampleLog) : N;
     const uint64_t nb = N / bs;
-    // scratch: bsum, bexcl (nb doubles), counts, offs, cursor (nb u32), total, last (8 B each),
-    //          shot_blk, order (shots u32), out (shots u64 when the caller wants host output)
+    const SubGeo sg(bs);
+    // scratch: sub-sums (nb * nsub doubles), bsum, bexcl (nb doubles), counts, offs, cursor (nb u32),
+    //          total, last (8 B each), shot_blk, order (shots u32), out (shots u64 for host output)
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
+    const size_t o_sub = take(nb * sg.nsub * 8);
     const size_t o_bsum = take(nb * 8), o_bexcl = take(nb * 8), o_tot = take(8), o_last = take(8);
     const size_t o_cnt = take(nb * 4), o_offs = take(nb * 4), o_cur = take(nb * 4), o_u32tot = take(8);
     const size_t o_sblk = take(shots * 4), o_order = take(shots * 4);
     const size_t o_out = out_on_device ? 0 : take(shots * 8);
     char *scratch = nullptr;
     QSIM_CUDA(cudaMallocAsync((void **)&scratch, off, s->stream));
+    double *sub = (double *)(scratch + o_sub);
     double *bsum = (double *)(scratch + o_bsum), *bexcl = (double *)(scratch + o_bexcl);
     double *tot = (double *)(scratch + o_tot);
     uint64_t *last = (uint64_t *)(scratch + o_last);
@@ -523,9 +623,9 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
     const bool c128 = s->dtype == SIM_C128;
     do {
         launch_begin(s, KC_SAMPLE, (double)s->bytes);
-        if (c128) k_block_sums<double><<<(unsigned)nb, 256, 0, s->stream>>>((const double *)s->amps, bs, bsum);
-        else k_block_sums<float><<<(unsigned)nb, 256, 0, s->stream>>>((const float *)s->amps, bs, bsum);
-        if ((rc = launch_end(s, "block sums"))) break;
+        if (c128) k_sub_sums<double><<<(unsigned)nb, 256, 0, s->stream>>>((const double *)s->amps, bs, sub, bsum);
+        else k_sub_sums<float><<<(unsigned)nb, 256, 0, s->stream>>>((const float *)s->amps, bs, sub, bsum);
+        if ((rc = launch_end(s, "sub-block sums"))) break;
         launch_begin(s, KC_SAMPLE);
         k_scan_exclusive<double><<<1, kScanThreads, 0, s->stream>>>(bsum, bexcl, nb, tot);
         if ((rc = launch_end(s, "block scan"))) break;
@@ -558,17 +658,14 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
         launch_begin(s, KC_SAMPLE);
         k_scatter<<<grid_for(shots, 256, s->num_sms), 256, 0, s->stream>>>(shots, sblk, cur, order);
         if ((rc = launch_end(s, "scatter shots"))) break;
-        const size_t smem = bs * sizeof(double);
-        launch_begin(s, KC_SAMPLE, (double)s->bytes);
-        if (c128) {
-            cudaFuncSetAttribute(k_resolve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_resolve<double><<<(unsigned)nb, 256, smem, s->stream>>>((const double *)s->amps, bs, seed, bexcl, tot,
-                                                                      cnt, offs, order, dout);
-        } else {
-            cudaFuncSetAttribute(k_resolve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            k_resolve<float><<<(unsigned)nb, 256, smem, s->stream>>>((const float *)s->amps, bs, seed, bexcl, tot,
-                                                                     cnt, offs, order, dout);
-        }
+        // per shot: one sub-block of amplitudes
+        launch_begin(s, KC_SAMPLE, (double)shots * sg.sub * (c128 ? 16.0 : 8.0));
+        if (c128)
+            k_resolve<double><<<(unsigned)nb, 256, 0, s->stream>>>((const double *)s->amps, bs, seed, bexcl, tot, sub,
+                                                                   cnt, offs, order, dout);
+        else
+            k_resolve<float><<<(unsigned)nb, 256, 0, s->stream>>>((const float *)s->amps, bs, seed, bexcl, tot, sub,
+                                                                  cnt, offs, order, dout);
         if ((rc = launch_end(s, "resolve shots"))) break;
         if (!out_on_device) {
             if (cudaMemcpyAsync(out, dout, shots * 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) {

@@ -186,7 +186,7 @@ def test_measure_matches_oracle(sim, orc, dt):
 
 
 @pytest.mark.parametrize("dt", ["c64", "c128"])
-@pytest.mark.parametrize("n", [1, 3, 12, 13, 15, 18])
+@pytest.mark.parametrize("n", [1, 3, 7, 12, 13, 15, 18, 20])
 def test_sample_matches_oracle(sim, orc, dt, n):
     """Same state (copied from the GPU), same u_s: identical indices except
     shots whose target lies within 1e-12 of a prefix boundary."""
@@ -206,6 +206,29 @@ def test_sample_matches_oracle(sim, orc, dt, n):
             t = orc.uniform(321, int(s)) * tot
             near = np.min(np.abs(c - t))
             assert near <= 1e-12 * tot, (s, got[s], ref[s])
+    assert len(diff) <= 2
+    st.close()
+
+
+@pytest.mark.parametrize("q", [0, 9, 15])
+def test_sample_after_collapse_matches_oracle(sim, orc, q):
+    """After a measurement half of the amplitudes are exactly zero: whole
+    sub-blocks (q >= 8) or every other amplitude (q = 0) carry no
+    probability, and no shot may land there."""
+    n = 16
+    st = sim.State(n, "c64")
+    st.apply(C.random_gates(n, 60, seed=q + 7))
+    m, _ = st.measure(q, seed=5, draw=0)
+    psi = st.state().astype(np.complex128)
+    got = st.sample(50000, seed=77)
+    assert np.all(((got >> q) & 1) == m)
+    ref = orc.sample(psi, 50000, seed=77)
+    diff = np.nonzero(got != ref)[0]
+    if len(diff):
+        c = np.cumsum(np.abs(psi) ** 2)
+        for s in diff:
+            t = orc.uniform(77, int(s)) * c[-1]
+            assert np.min(np.abs(c - t)) <= 1e-12 * c[-1], (s, got[s], ref[s])
     assert len(diff) <= 2
     st.close()
 
