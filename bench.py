@@ -45,6 +45,29 @@ N_QUBITS, DEPTH, SEED, SHOTS = 30, 20, 1234, 1_000_000
 # 152 SMs x 128 FP32 FMA lanes x 2 flop x 2.070 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 
+# DRAM traffic of a kernel class from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch) as bytes per amplitude, with the SHA-256
+# of the kernel's source file at capture time: reported only while that file
+# is unchanged.  Captures run a 27-qubit state (1 GiB, 8x the L2; full
+# captures stay at a few GB on the device) and the traffic of a launch grows
+# with the state, so it is scaled by 2^n.
+TRAFFIC = {
+    "fused": {"bytes_per_amp": None, "source": "paper_1805_00988_gb300/csrc/fused.cu", "sha256": None,
+              "profile": "profiles/k_fused_stream5_27q.md"},
+}
+
+
+def traffic_for(kind: str, n: int):
+    import hashlib
+    t = TRAFFIC.get(kind)
+    if not t or t["bytes_per_amp"] is None:
+        return None, None
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
+    with open(path, "rb") as f:
+        if hashlib.sha256(f.read()).hexdigest() != t["sha256"]:
+            return None, "kernel source changed since the capture in " + t["profile"]
+    return t["bytes_per_amp"] * 2.0 ** n, ("ncu capture in %s (27-qubit launch, scaled by 2^(n-27))" % t["profile"])
+
 
 def workload_name(n, depth):
     return "haar_cz: %d qubits, depth %d (Haar U(2) on every qubit + CZ on a random matching per layer)" % (n, depth)
@@ -303,6 +326,10 @@ def run_ours(args, rank, world, local_rank):
                                     else "fallback 6.8 TB/s"),
                     "compute": {"bound": cbound, "achieved_TFLOPs": tflops, "peak_TFLOPs": cpeak, "frac": cfrac,
                                 "peak_source": csrc}}
+    traffic, tsrc = traffic_for(dname, n)
+    roofline["traffic"] = traffic
+    if tsrc:
+        roofline["traffic_source"] = tsrc
     roofline.update({"alg_bytes_per_launch": dbytes / dl, "avg_launch_ms": dms / dl, "launches": dl,
                      "timed_with": "CUDA events around every launch on the handle's stream, timed region"})
     kernels = {k: {"launches": v[0], "ms": v[1], "alg_GBps": (v[2] / (v[1] / 1e3) / 1e9) if v[1] > 0 else None,
@@ -339,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
                        "gates": int(len(gates)), "state": "complex64", "plan": plan, "tile_qubits": args.tile,
                        "shots": shots,
                        "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs larger than L2 (8 GiB state vs 129 MB L2); no flush"},
+                       "l2": "inputs larger than L2 (%.3g GiB state vs 129 MB L2); no flush" % (2.0 ** n * 8 / 2 ** 30)},
             "hbm_gbs": world * step_bytes / (ms_per_step / 1e3) / 1e9,
             "clocks": clocks, "gpu_launches": int(launches), "e2e": e2e, "roofline": roofline,
             "kernels": kernels, "norm": nrm, "expect_z_sum": ez}

@@ -81,12 +81,12 @@ typedef enum {
     SIM_PLAN_PER_GATE = 0,   /* one kernel launch per gate (one state pass each) */
     SIM_PLAN_STAGED = 1,     /* runs of gates applied per tile in one pass (registers + shared memory) */
     SIM_PLAN_FUSED = 2,      /* gates fused into k-qubit unitaries built in FP64, applied on tensor cores */
-    SIM_PLAN_LEARNED = 3     /* per-block choice made by the trained cost model */
+    SIM_PLAN_LEARNED = 3     /* per-window (or whole-circuit) variant chosen by the trained cost model */
 } sim_plan_kind;
 
 typedef struct sim_plan_opts {
     int32_t plan;            /* sim_plan_kind */
-    int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block, 2..6 */
+    int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block, 3..6 (0 = 5) */
     int32_t tile_qubits;     /* SIM_PLAN_STAGED: tile size log2 (0 = default) */
     int32_t flags;           /* reserved, 0 */
 } sim_plan_opts;

@@ -78,7 +78,7 @@ __global__ void k_batch_reset(BCtl *ctl, int *done, int64_t ndone, int *finished
     for (int64_t j = i; j < ncirc; j += stride) finished[j] = 0;
 }
 
-__global__ void __launch_bounds__(kThr, 1) k_batch(float2 *__restrict__ scratch, const BCirc *__restrict__ circs,
+__global__ void __launch_bounds__(kThr, 2) k_batch(float2 *__restrict__ scratch, const BCirc *__restrict__ circs,
                                                  const BPass *__restrict__ passes, const StOp<float> *__restrict__ ops,
                                                  const BItem *__restrict__ items, int64_t nitems, BCtl *ctl,
                                                  int *done, int *finished, double *__restrict__ partial,
@@ -160,7 +160,8 @@ __global__ void __launch_bounds__(kThr, 1) k_batch(float2 *__restrict__ scratch,
             }
         }
 
-        apply_ops<float, M>(v, ops + ps.op0, ps.nops, base, tid, sm);
+        apply_ops<float, M>(v, ops + ps.op0, ps.nops, base, tid, sm,
+                            reinterpret_cast<StOp<float> *>(smem_raw + ((size_t)1 << kBM) * 2 * sizeof(float)));
 
         if (it.pass + 1 < c.npass) {
 #pragma unroll
@@ -418,11 +419,14 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
             rc = cuda_fail(cudaGetLastError(), "sim_batch_create: upload");
             break;
         }
-        const size_t smem = ((size_t)1 << kBM) * 2 * sizeof(float);
+        const size_t smem = ((size_t)1 << kBM) * 2 * sizeof(float) + op_stage_bytes<float>();
         if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "batch smem attribute");
             break;
         }
+        // two CTAs per SM (128 registers a thread, 70 KB of shared memory each)
+        cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -430,7 +434,9 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
             rc = fail(SIM_ECUDA, "sim_batch_create: persistent kernel does not fit on an SM");
             break;
         }
-        // every CTA must be resident at once (the waits rely on it)
+        // one persistent CTA per resident slot.  A wait only ever waits on
+        // items earlier in the queue (pass-major order), which CTAs already
+        // running hold, so progress does not depend on residency.
         b->grid = sms * per_sm;
         // capture reset + persistent launch in a graph
         cudaStream_t cs;

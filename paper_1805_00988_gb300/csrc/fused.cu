@@ -13,7 +13,8 @@
 //
 // Precision: kind::tf32 keeps 10 mantissa bits, too few for an infidelity of
 // 1e-6 over ~100 blocks.  Both operands are split x = x_hi + x_lo with x_hi
-// the TF32 truncation of x, and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is
+// = x rounded to TF32 and x_lo = (x - x_hi) rounded to TF32 (both to nearest,
+// so the split carries no bias), and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is
 // accumulated in FP32 in tensor memory (3xTF32; Ootomo & Yokota 2022).  U_blk
 // itself is formed in FP64 (k_fuse_build) before the split.
 //
@@ -166,18 +167,17 @@ __device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, uint32_t *r)
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__host__ __device__ __forceinline__ float tf32_trunc(float x)
+// x rounded to TF32 (10 explicit mantissa bits), nearest with ties away from
+// zero.  Both parts of a 3xTF32 split are rounded, not truncated: truncation
+// (and the tensor core's own truncation of FP32 operands) shrinks every
+// element by half a TF32 ulp on average, and that bias builds up as a drift
+// of the norm over many blocks.
+// (two integer operations: add half a TF32 ulp to the magnitude bits, then
+// clear the 13 bits below the TF32 mantissa; a carry into the exponent is the
+// correct rounding up to the next binade; states hold no inf / NaN)
+__device__ __forceinline__ float tf32_rn(float x)
 {
-#ifdef __CUDA_ARCH__
-    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
-#else
-    uint32_t u;
-    memcpy(&u, &x, 4);
-    u &= 0xFFFFE000u;
-    float r;
-    memcpy(&r, &u, 4);
-    return r;
-#endif
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 // byte offset of element (row, kk) in a K-major no-swizzle operand of K columns
@@ -224,8 +224,8 @@ __global__ void __launch_bounds__(256) k_fuse_build(const FGate *__restrict__ ga
         const int i = n >> 1, b = n & 1, j = kk >> 1, a = kk & 1;
         const double2 u = U[i * D + j];
         const double w = (a == b) ? u.x : (a == 1 ? -u.y : u.y);
-        const float hi = tf32_trunc((float)w);
-        const float lo = (float)(w - (double)hi);
+        const float hi = tf32_rn((float)w);
+        const float lo = tf32_rn((float)(w - (double)hi));
         const int ch = n / NC, nl = n % NC;
         float *chunk = out + (size_t)ch * 2 * NC * K;
         const uint32_t off = kmajor_off(nl, kk, K) >> 2;
@@ -297,11 +297,11 @@ __global__ void __launch_bounds__(kRows, 1) k_fused_apply(float *__restrict__ st
             v[u] = live ? *reinterpret_cast<const float2 *>(st + 2 * (base | dep[c0 + u])) : make_float2(0.f, 0.f);
 #pragma unroll
         for (int u = 0; u < BATCH; ++u) {
-            const float hr = tf32_trunc(v[u].x), hi = tf32_trunc(v[u].y);
+            const float hr = tf32_rn(v[u].x), hi = tf32_rn(v[u].y);
             const uint32_t off = kmajor_off(tid, 2 * (c0 + u), K);    // (re, im) share one 16-byte row chunk
             *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_hi) + off) = make_float2(hr, hi);
             *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_lo) + off) =
-                make_float2(v[u].x - hr, v[u].y - hi);
+                make_float2(tf32_rn(v[u].x - hr), tf32_rn(v[u].y - hi));
         }
     }
     tc_fence_before();
@@ -594,10 +594,11 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
                 // of a core matrix; x odd swaps which register holds which
                 const uint32_t off = kmajor_off(tid, 2 * ((j ^ x) & ~1), K);
                 const float2 e0 = (x & 1) ? v[j + 1] : v[j], e1 = (x & 1) ? v[j] : v[j + 1];
-                const float h0 = tf32_trunc(e0.x), h1 = tf32_trunc(e0.y);
-                const float h2 = tf32_trunc(e1.x), h3 = tf32_trunc(e1.y);
+                const float h0 = tf32_rn(e0.x), h1 = tf32_rn(e0.y);
+                const float h2 = tf32_rn(e1.x), h3 = tf32_rn(e1.y);
                 *reinterpret_cast<float4 *>(ahi + off) = make_float4(h0, h1, h2, h3);
-                *reinterpret_cast<float4 *>(alo + off) = make_float4(e0.x - h0, e0.y - h1, e1.x - h2, e1.y - h3);
+                *reinterpret_cast<float4 *>(alo + off) = make_float4(tf32_rn(e0.x - h0), tf32_rn(e0.y - h1),
+                                                                     tf32_rn(e1.x - h2), tf32_rn(e1.y - h3));
             }
             fence_async_smem();
             mbar_arrive(&bar_a[i % AB]);
@@ -608,6 +609,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
         uint32_t ur;
         uint64_t gr;
         row_offsets(r, ur, gr);
+        const bool q0_in_block = (pmask & 1ull) != 0;
         for (int i = 0; i < iters && !*vfailed; ++i) {
             const int sb = i & 1;
             const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
@@ -630,12 +632,20 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
                     tmem_ld16_nowait(lane_base + (uint32_t)(N + col), lo);
                 }
                 tmem_wait_ld();
+                float v[W];
 #pragma unroll
-                for (int e = 0; e < W / 2; ++e) {
-                    const int c = col / 2 + e;
-                    *reinterpret_cast<float2 *>(st + 2 * (base | gc[c])) =
-                        make_float2(__uint_as_float(hi[2 * e]) + __uint_as_float(lo[2 * e]),
-                                    __uint_as_float(hi[2 * e + 1]) + __uint_as_float(lo[2 * e + 1]));
+                for (int e = 0; e < W; ++e) v[e] = __uint_as_float(hi[e]) + __uint_as_float(lo[e]);
+                if (q0_in_block) {
+                    // columns c, c + 1 are neighbouring amplitudes: one 16-byte store
+#pragma unroll
+                    for (int e = 0; e < W / 2; e += 2)
+                        *reinterpret_cast<float4 *>(st + 2 * (base | gc[col / 2 + e])) =
+                            make_float4(v[2 * e], v[2 * e + 1], v[2 * e + 2], v[2 * e + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < W / 2; ++e)
+                        *reinterpret_cast<float2 *>(st + 2 * (base | gc[col / 2 + e])) =
+                            make_float2(v[2 * e], v[2 * e + 1]);
                 }
             }
             tc_fence_before();

@@ -89,7 +89,8 @@ k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
         }
     }
 
-    apply_ops<R, M>(v, ops, nops, base, tid, sm);
+    apply_ops<R, M>(v, ops, nops, base, tid, sm,
+                    reinterpret_cast<StOp<R> *>(smem_raw + ((size_t)1 << M) * 2 * sizeof(R)));
     {
         int t2 = tid;
         uint64_t b2 = base;
@@ -121,7 +122,7 @@ k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
 template <typename R, int M>
 int launch_staged(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &geo, double flops)
 {
-    const size_t smem = ((size_t)1 << M) * 2 * sizeof(R);
+    const size_t smem = ((size_t)1 << M) * 2 * sizeof(R) + op_stage_bytes<R>();
     static bool attr_set = false;   // per template instance
     if (!attr_set) {
         QSIM_CUDA(cudaFuncSetAttribute(k_staged<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

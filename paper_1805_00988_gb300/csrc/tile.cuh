@@ -327,19 +327,40 @@ __device__ __forceinline__ void relayout(int from, int to, Regs<R, RA> &v, R *sm
     }
 }
 
+// ops staged in shared memory per chunk: every field read of the op loop is
+// then a broadcast shared load instead of a dependent global load
+constexpr int kOpChunk = 64;
+static_assert(sizeof(StOp<float>) % 16 == 0 && sizeof(StOp<double>) % 16 == 0, "ops are copied as 16-byte vectors");
+template <typename R>
+__host__ __device__ constexpr size_t op_stage_bytes() { return (size_t)kOpChunk * sizeof(StOp<R>); }
+
 // Apply an encoded op list to the registers of one tile (the whole body of a
 // pass between the global load and store).  base = global index bits of the
-// tile outside Q; sm = the tile's shared memory (2^M amplitudes).
+// tile outside Q; sm = the tile's shared memory (2^M amplitudes); sops =
+// shared memory for kOpChunk ops.  Every thread of the CTA runs the same op
+// sequence (the chunk copies are CTA-wide).
 template <typename R, int M>
-__device__ __forceinline__ void apply_ops(Regs<R, (1 << (M - kThrBits))> &v, const StOp<R> *__restrict__ ops, int nops,
-                                          uint64_t base, int tid, R *sm)
+__device__ __forceinline__ void apply_ops(Regs<R, (1 << (M - kThrBits))> &v, const StOp<R> *__restrict__ gops,
+                                          int nops, uint64_t base, int tid, R *sm, StOp<R> *sops)
 {
     constexpr int VEC = (sizeof(R) == 4) ? 2 : 1;
     constexpr int RB = M - kThrBits;
     constexpr int RA = 1 << RB;
     int layout = 0;
     uint64_t negm = 0;
-    for (int p = 0; p < nops; ++p) {
+    const StOp<R> *ops = sops;
+    for (int p0 = 0; p0 < nops; p0 += kOpChunk) {
+    const int cnt = min(kOpChunk, nops - p0);
+    {
+        // this chunk of ops into shared memory (after every thread is done with the last one)
+        __syncthreads();
+        const uint4 *src = reinterpret_cast<const uint4 *>(gops + p0);
+        uint4 *dst = reinterpret_cast<uint4 *>(sops);
+        constexpr int W = (int)(sizeof(StOp<R>) / 16);
+        for (int e = tid; e < cnt * W; e += kThr) dst[e] = __ldg(src + e);
+        __syncthreads();
+    }
+    for (int p = 0; p < cnt; ++p) {
         const int kind = ops[p].kind;
         const int arg = ops[p].arg;
         if (kind == SK_LAYOUT) {
@@ -395,6 +416,7 @@ __device__ __forceinline__ void apply_ops(Regs<R, (1 << (M - kThrBits))> &v, con
                     }
             }
         }
+    }
     }
     flush_neg(v, negm);
 }
