@@ -192,7 +192,9 @@ int sim_batch_destroy(sim_batch_t b);
  *   eps 1e-8, learning rate lr); *final_loss (may be NULL) after the last.
  * sim_set_cost_model: SIM_PLAN_LEARNED on this handle consults model m (NULL
  *   = no model: the greedy fixed-k plan is used).  The model must outlive the
- *   handle's use of it. */
+ *   handle's use of it.  A complex128 handle runs SIM_PLAN_LEARNED as the
+ *   per-gate plan without consulting the model (every complex128 plan is
+ *   bound by the FP64 pipe, where per-gate kernels do the least work). */
 typedef struct qsim_mlp *sim_mlp_t;
 int sim_mlp_param_count(int d_in, int hidden);
 int sim_mlp_create(int d_in, int hidden, void *stream, sim_mlp_t *out);

@@ -918,30 +918,42 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
 
 }  // namespace
 
-int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out)
-{
+struct FusedPlan {
+    int n, k;
+    size_t n_gates;
     std::vector<SGate> g;
-    lower_gates(gates, n_gates, &g);
-    std::vector<Block> b = form_blocks(g, k, n);
-    if (blocks_out) *blocks_out = (int64_t)b.size();
+    std::vector<Block> blocks;
+};
+void FusedPlanFree::operator()(FusedPlan *p) const { delete p; }
+
+int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out, FusedPlanPtr *keep)
+{
+    FusedPlanPtr p(new FusedPlan{n, k, n_gates, {}, {}});
+    lower_gates(gates, n_gates, &p->g);
+    p->blocks = form_blocks(p->g, k, n);
+    if (blocks_out) *blocks_out = (int64_t)p->blocks.size();
+    if (keep) *keep = std::move(p);
     return SIM_OK;
 }
 
-int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
+int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o,
+                        const FusedPlan *planned)
 {
     if (s->dtype != SIM_C64) return fail(SIM_EUNSUPPORTED, "fused plan: complex64 states only (TF32 tensor cores)");
     int k = o.fuse_k ? o.fuse_k : 5;
     if (k < 3 || k > 6) return fail(SIM_EINVAL, "fused plan: fuse_k must be in 3..6");
     if (s->n < k + 7) return fail(SIM_EINVAL, "fused plan: needs n >= fuse_k + 7 (one CTA covers 128 rows)");
-    std::vector<SGate> g;
-    lower_gates(gates, n_gates, &g);
-    if (g.empty()) return SIM_OK;
-    std::vector<Block> blocks = form_blocks(g, k, s->n);
+    FusedPlanPtr own;
+    if (!planned || planned->n != s->n || planned->k != k || planned->n_gates != n_gates) {
+        describe_fused(s->n, gates, n_gates, k, nullptr, &own);
+        planned = own.get();
+    }
+    if (planned->g.empty()) return SIM_OK;
     switch (k) {
-    case 3: return run_fused<3>(s, g, blocks);
-    case 4: return run_fused<4>(s, g, blocks);
-    case 5: return run_fused<5>(s, g, blocks);
-    default: return run_fused<6>(s, g, blocks);
+    case 3: return run_fused<3>(s, planned->g, planned->blocks);
+    case 4: return run_fused<4>(s, planned->g, planned->blocks);
+    case 5: return run_fused<5>(s, planned->g, planned->blocks);
+    default: return run_fused<6>(s, planned->g, planned->blocks);
     }
 }
 

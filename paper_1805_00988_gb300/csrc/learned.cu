@@ -67,7 +67,7 @@ bool feasible(int n, int dtype, int v)
 
 }  // namespace
 
-int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out)
+int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out, FusedPlanPtr *keep)
 {
     if (!feasible(n, dtype, v)) return SIM_EUNSUPPORTED;
     std::vector<SGate> g;
@@ -89,7 +89,7 @@ int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v
         lc = (double)l;
     } else if (v >= 3) {
         int64_t b = 0;
-        describe_fused(n, gates, n_gates, v, &b);
+        describe_fused(n, gates, n_gates, v, &b, keep);
         launches = (double)b;
     }
     for (int i = 0; i < SIM_FEATURES; ++i) out[i] = 0.f;
@@ -118,6 +118,18 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
         s->last_plan.clear();
         return SIM_OK;
     }
+    if (s->dtype == SIM_C128) {
+        // complex128 on this GPU is bound by the FP64 pipe in every plan, not
+        // by HBM: a tile pass saves state traffic that is not the limit and,
+        // for diagonal and controlled gates, does FP64 work on every
+        // amplitude of the tile where the per-gate kernels touch only the
+        // affected ones.  The per-gate plan is the fastest and the model
+        // (trained on complex64 timings) is not consulted.
+        s->last_plan.assign(1, 0);
+        for (size_t k = 0; k < n_gates; ++k)
+            if (int rc = launch_pair_gate(s, make_pair_gate(gates[k]))) return rc;
+        return SIM_OK;
+    }
     // windows of about eight layers of single-qubit gates
     const size_t W = (size_t)std::max(64, 8 * s->n);
     std::vector<Window> win;
@@ -132,10 +144,15 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
             if (feasible(s->n, s->dtype, v)) cand.push_back({w, v});
     std::vector<float> feat(cand.size() * SIM_FEATURES);
     std::vector<char> ok(cand.size(), 0);
+    // the block plans of the whole circuit are kept: if one of them wins it
+    // runs without being planned again
+    FusedPlanPtr whole_plan[SIM_VARIANTS];
     parallel_for(cand.size(), [&](size_t r) {
         const Window &w = seg[cand[r].first];
-        ok[r] = plan_features(s->n, s->dtype, gates + w.first, w.count, cand[r].second,
-                              feat.data() + r * SIM_FEATURES) == SIM_OK;
+        const int v = cand[r].second;
+        FusedPlanPtr *keep = (cand[r].first == nw && nw > 1 && v >= 3) ? &whole_plan[v] : nullptr;
+        ok[r] = plan_features(s->n, s->dtype, gates + w.first, w.count, v, feat.data() + r * SIM_FEATURES,
+                              keep) == SIM_OK;
     });
     std::vector<float> rows;
     std::vector<std::pair<size_t, int>> who;
@@ -185,7 +202,8 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
         } else if (vo.plan == SIM_PLAN_STAGED) {
             rc = apply_circuit_staged(s, gates + first, count, vo);
         } else {
-            rc = apply_circuit_fused(s, gates + first, count, vo);
+            const bool whole = first == 0 && count == n_gates && best[w] >= 3;
+            rc = apply_circuit_fused(s, gates + first, count, vo, whole ? whole_plan[best[w]].get() : nullptr);
         }
         if (rc) return rc;
         w = e;

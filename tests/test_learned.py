@@ -73,3 +73,21 @@ def test_learned_plan_gain_over_fixed_variants(trained):
     for t_l, best, worst in rows:
         assert t_l <= 1.25 * best + 2.0, rows
     assert sum(r[0] for r in rows) < sum(r[2] for r in rows)
+
+
+@pytest.mark.gpu
+def test_learned_plan_complex128_runs_per_gate(trained, orc):
+    """complex128 is FP64-bound in every plan: the learned plan runs the
+    per-gate kernels without consulting the model, at complex128 accuracy."""
+    sim = trained[0]
+    n = 14
+    g = C.random_gates(n, 200, seed=12)
+    st = sim.State(n, "c128")
+    sim.sim_set_cost_model(st.h, trained[2])
+    psi = C.random_state(n, seed=2)
+    st.load(psi)
+    st.apply(g, plan="learned")
+    assert list(sim.sim_last_plan(st.h)) == [0]
+    ref = orc.apply_circuit(psi, g)
+    assert np.max(np.abs(st.state() - ref)) <= 1e-11 * np.max(np.abs(ref))
+    st.close()
