@@ -704,78 +704,122 @@ struct Block {
     bool wide = false;        // one gate on more than k qubits: applied by a per-gate launch
 };
 
-// Gates absorbable into a block on the fixed qubit set S: scan the remaining
-// gates (at most W of them); a gate counts if it commutes with every gate
-// skipped before it and all its qubits are in S.
-int absorb_count(const std::vector<SGate> &g, const std::vector<char> &done, size_t first, uint64_t S, size_t W)
-{
-    uint64_t bx = 0, bd = 0;
-    int cnt = 0;
-    size_t seen = 0;
-    for (size_t i = first; i < g.size() && seen < W; ++i) {
-        if (done[i]) continue;
-        ++seen;
-        const uint64_t x = g[i].xq(), d = g[i].dq();
-        if (((x & (bx | bd)) == 0) && ((d & bx) == 0) && (((x | d) & ~S) == 0)) {
-            ++cnt;
-        } else {
-            bx |= x;
-            bd |= d;
-        }
-    }
-    return cnt;
-}
+// Fixed-k blocks with a lookahead choice of qubits.  A block starts from the
+// qubits of the first remaining gate and grows up to k qubits; each growth
+// step adds the set of at most `depth` further qubits that lets the most of
+// the next gates (a window of 256 not yet placed) join -- a gate joins if all
+// its qubits are in the set and it commutes with every gate skipped before it
+// (ties: the smaller set, then the earlier candidates).  Then every remaining
+// gate that commutes with the gates skipped before it and lies on the block's
+// qubits joins.  depth 1 adds one qubit at a time; depth 2 also weighs pairs
+// (two qubits that only pay off together, such as the two ends of a CZ).
+// Blocks come out one at a time, so that a caller can launch the first ones
+// while it plans the rest.
+class BlockPlanner {
+public:
+    BlockPlanner(const std::vector<SGate> &g, int k, int n, int depth)
+        : g_(g), k_(k), n_(n), depth_(depth), done_(g.size(), 0) {}
 
-// Fixed-k blocks with a lookahead choice of qubits: a block starts from the
-// qubits of the first remaining gate and grows, one qubit at a time up to k,
-// by the qubit that lets the most of the next gates (a window of 256) join;
-// then every remaining gate that commutes with the gates skipped before it and
-// lies on the block's qubits joins.
-std::vector<Block> form_blocks(const std::vector<SGate> &g, int k, int n)
-{
-    constexpr size_t kWindow = 256;
-    std::vector<Block> blocks;
-    std::vector<char> done(g.size(), 0);
-    size_t first = 0;
-    while (first < g.size()) {
-        Block b{0, {}};
-        uint64_t S = g[first].xq() | g[first].dq();
-        if (__builtin_popcountll(S) > k) {
+    bool next(Block *b)
+    {
+        while (first_ < g_.size() && done_[first_]) ++first_;
+        if (first_ >= g_.size()) return false;
+        *b = Block{0, {}};
+        uint64_t S = g_[first_].xq() | g_[first_].dq();
+        if (__builtin_popcountll(S) > k_) {
             // the first remaining gate alone spans more than k qubits
-            b.qmask = S;
-            b.members.push_back((int)first);
-            b.wide = true;
-            done[first] = 1;
-        } else {
-            while (__builtin_popcountll(S) < k) {
-                int best_q = -1, best = absorb_count(g, done, first, S, kWindow);
-                for (int q = 0; q < n; ++q) {
-                    if ((S >> q) & 1) continue;
-                    const int c = absorb_count(g, done, first, S | (1ull << q), kWindow);
-                    if (c > best) { best = c; best_q = q; }
-                }
-                if (best_q < 0) break;
-                S |= 1ull << best_q;
+            b->qmask = S;
+            b->members.push_back((int)first_);
+            b->wide = true;
+            done_[first_] = 1;
+            return true;
+        }
+        load_window();
+        while (__builtin_popcountll(S) < k_) {
+            const int free = k_ - __builtin_popcountll(S);
+            std::vector<int> cand;
+            for (int q = 0; q < n_; ++q)
+                if (!((S >> q) & 1) && ((touched_ >> q) & 1)) cand.push_back(q);
+            int best = absorb(S);
+            uint64_t best_add = 0;
+            for (size_t i = 0; i < cand.size(); ++i) {
+                const uint64_t a1 = 1ull << cand[i];
+                const int c1 = absorb(S | a1);
+                if (c1 > best) { best = c1; best_add = a1; }
             }
-            uint64_t bx = 0, bd = 0;
-            for (size_t i = first; i < g.size(); ++i) {
-                if (done[i]) continue;
-                const uint64_t x = g[i].xq(), d = g[i].dq();
-                if (((x & (bx | bd)) == 0) && ((d & bx) == 0) && (((x | d) & ~S) == 0)) {
-                    b.qmask |= x | d;
-                    b.members.push_back((int)i);
-                    done[i] = 1;
-                } else {
-                    bx |= x;
-                    bd |= d;
-                }
+            if (depth_ >= 2 && free >= 2) {
+                for (size_t i = 0; i < cand.size(); ++i)
+                    for (size_t j = i + 1; j < cand.size(); ++j) {
+                        const uint64_t a2 = (1ull << cand[i]) | (1ull << cand[j]);
+                        const int c2 = absorb(S | a2);
+                        if (c2 > best) { best = c2; best_add = a2; }
+                    }
+            }
+            if (!best_add) break;
+            S |= best_add;
+        }
+        uint64_t bx = 0, bd = 0;
+        for (size_t i = first_; i < g_.size(); ++i) {
+            if (done_[i]) continue;
+            const uint64_t x = g_[i].xq(), d = g_[i].dq();
+            if (((x & (bx | bd)) == 0) && ((d & bx) == 0) && (((x | d) & ~S) == 0)) {
+                b->qmask |= x | d;
+                b->members.push_back((int)i);
+                done_[i] = 1;
+            } else {
+                bx |= x;
+                bd |= d;
             }
         }
-        blocks.push_back(b);
-        while (first < g.size() && done[first]) ++first;
+        return true;
     }
-    return blocks;
-}
+
+private:
+    static constexpr size_t kWindow = 256;
+
+    // the next kWindow not-placed gates as (non-diagonal, diagonal) masks
+    void load_window()
+    {
+        wx_.clear();
+        wd_.clear();
+        touched_ = 0;
+        for (size_t i = first_; i < g_.size() && wx_.size() < kWindow; ++i) {
+            if (done_[i]) continue;
+            wx_.push_back(g_[i].xq());
+            wd_.push_back(g_[i].dq());
+            touched_ |= g_[i].xq() | g_[i].dq();
+        }
+    }
+
+    // gates of the window that could join a block on qubit set S
+    int absorb(uint64_t S) const
+    {
+        uint64_t bx = 0, bd = 0;
+        int cnt = 0;
+        for (size_t i = 0; i < wx_.size(); ++i) {
+            const uint64_t x = wx_[i], d = wd_[i];
+            if (((x & (bx | bd)) == 0) && ((d & bx) == 0) && (((x | d) & ~S) == 0)) {
+                ++cnt;
+            } else {
+                bx |= x;
+                bd |= d;
+            }
+        }
+        return cnt;
+    }
+
+    const std::vector<SGate> &g_;
+    int k_, n_, depth_;
+    std::vector<char> done_;
+    size_t first_ = 0;
+    std::vector<uint64_t> wx_, wd_;
+    uint64_t touched_ = 0;
+};
+
+// the planner depth the fused plan runs with, and the cheaper one the learned
+// plan uses to predict block counts for its features
+constexpr int kRunDepth = 2;
+constexpr int kFeatureDepth = 1;
 
 // CTAs of one kernel that fit on an SM at once: registers (allocated per warp
 // in units of 256), shared memory (static + dynamic + the per-CTA reservation)
@@ -799,66 +843,39 @@ int resident_ctas(int dev, const void *fn, int threads, size_t dyn_smem)
     return std::min(by_regs, std::min(by_smem, by_thr));
 }
 
+// Plan and run the fused blocks in groups: each group of blocks is planned,
+// its gates uploaded, its W matrices built (one k_fuse_build launch) and its
+// applies launched; the host then plans the next group while the GPU works
+// through this one, so only the first (small) group's planning is exposed.
+// Host and device copies of the gate lists keep one region per group (no
+// reuse within a call); the W matrices use two device slots, reused in
+// stream order.
 template <int KQ>
-int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Block> &blocks)
+int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
 {
     constexpr int K = 2 << KQ;
+    constexpr size_t kGroup = 8;                       // blocks per group after the first
+    constexpr size_t kFirst = 2;                       // blocks in the first group
     const int n = s->n;
-    // pad every block to KQ qubits (identity on the added ones)
-    std::vector<std::vector<int>> pos(blocks.size());
-    std::vector<FGate> fg;
-    std::vector<int> goff(1, 0);
-    for (size_t b = 0; b < blocks.size(); ++b) {
-        if (blocks[b].wide) {
-            goff.push_back((int)fg.size());
-            continue;
-        }
-        uint64_t q = blocks[b].qmask;
-        for (int extra = 0; extra < n && __builtin_popcountll(q) < KQ; ++extra) q |= 1ull << extra;
-        for (int i = 0; i < n; ++i)
-            if ((q >> i) & 1) pos[b].push_back(i);
-        auto loc = [&](int qubit) {
-            for (int i = 0; i < KQ; ++i)
-                if (pos[b][i] == qubit) return i;
-            return -1;
-        };
-        for (int m : blocks[b].members) {
-            FGate f;
-            f.target = loc(g[m].target);
-            f.ctrl = 0;
-            for (int c = 0; c < n; ++c)
-                if ((g[m].ctrl >> c) & 1) f.ctrl |= 1u << loc(c);
-            memcpy(f.m, g[m].m, sizeof f.m);
-            fg.push_back(f);
-        }
-        goff.push_back((int)fg.size());
-    }
-    const size_t nb = blocks.size();
-    const size_t bytes_g = fg.size() * sizeof(FGate), bytes_o = goff.size() * sizeof(int);
-    const size_t bytes_b = nb * 2 * (size_t)K * K * sizeof(float);
-    const size_t o_g = 0, o_o = (bytes_g + 255) & ~(size_t)255, o_b = (o_o + bytes_o + 255) & ~(size_t)255;
-    const size_t total = o_b + bytes_b;
-    if (int rc = ensure_host_pinned(&s->host_ops, &s->host_ops_bytes, o_b)) return rc;
+    const size_t ng = g.size();
+    // per call: gate lists (<= ng FGates, <= 2 ng + 1 offsets), W slots (2 x kGroup blocks)
+    const size_t bytes_g = ng * sizeof(FGate), bytes_o = (2 * ng + 2) * sizeof(int);
+    const size_t bytes_slot = kGroup * 2 * (size_t)K * K * sizeof(float);
+    const size_t o_g = 0, o_o = (bytes_g + 255) & ~(size_t)255, o_w = (o_o + bytes_o + 255) & ~(size_t)255;
+    const size_t total = o_w + 2 * bytes_slot;
+    if (int rc = ensure_host_pinned(&s->host_ops, &s->host_ops_bytes, o_w)) return rc;
     char *scratch = nullptr;
     QSIM_CUDA(cudaMallocAsync((void **)&scratch, total, s->stream));
-    memcpy((char *)s->host_ops + o_g, fg.data(), bytes_g);
-    memcpy((char *)s->host_ops + o_o, goff.data(), bytes_o);
+    FGate *hg = (FGate *)((char *)s->host_ops + o_g);
+    int *ho = (int *)((char *)s->host_ops + o_o);
     int rc = SIM_OK;
     do {
-        if (cudaMemcpyAsync(scratch, s->host_ops, o_b, cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
-            rc = cuda_fail(cudaGetLastError(), "fused upload");
-            break;
-        }
         if (cudaMemsetAsync(s->dev_status, 0, sizeof(int), s->stream) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "status reset");
             break;
         }
         const size_t smb = (size_t)(1 << KQ) * (1 << KQ) * sizeof(double2);
         cudaFuncSetAttribute(k_fuse_build<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
-        launch_begin(s, KC_FUSE_BUILD, (double)bytes_b);
-        k_fuse_build<KQ><<<(unsigned)nb, 256, smb, s->stream>>>((const FGate *)(scratch + o_g),
-                                                                 (const int *)(scratch + o_o), (float *)(scratch + o_b));
-        if ((rc = launch_end(s, "fused build"))) break;
         const size_t sma = apply_smem_bytes<KQ>();
         cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
         cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -886,26 +903,77 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
             const uint64_t tiles = (rows + kRows - 1) / kRows;
             pipe_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms * per_sm);
         }
-        for (size_t b = 0; b < nb && rc == SIM_OK; ++b) {
-            if (blocks[b].wide) {
-                rc = launch_sgate(s, g[blocks[b].members[0]]);
-                continue;
+        BlockPlanner planner(g, KQ, n, depth);
+        size_t fg_used = 0, go_used = 0;
+        int slot = 0;
+        for (size_t grp = 0; rc == SIM_OK; ++grp, slot ^= 1) {
+            // plan the next group
+            std::vector<Block> blocks;
+            Block b;
+            const size_t want = grp == 0 ? kFirst : kGroup;
+            while (blocks.size() < want && planner.next(&b)) blocks.push_back(b);
+            if (blocks.empty()) break;
+            // pad every block to KQ qubits (identity on the added ones); gates in block-local qubits
+            const size_t fg0 = fg_used, go0 = go_used;
+            std::vector<std::vector<int>> pos(blocks.size());
+            ho[go_used++] = 0;
+            for (size_t bi = 0; bi < blocks.size(); ++bi) {
+                if (!blocks[bi].wide) {
+                    uint64_t q = blocks[bi].qmask;
+                    for (int extra = 0; extra < n && __builtin_popcountll(q) < KQ; ++extra) q |= 1ull << extra;
+                    for (int i = 0; i < n; ++i)
+                        if ((q >> i) & 1) pos[bi].push_back(i);
+                    auto loc = [&](int qubit) {
+                        for (int i = 0; i < KQ; ++i)
+                            if (pos[bi][i] == qubit) return i;
+                        return -1;
+                    };
+                    for (int m : blocks[bi].members) {
+                        FGate f;
+                        f.target = loc(g[m].target);
+                        f.ctrl = 0;
+                        for (int c = 0; c < n; ++c)
+                            if ((g[m].ctrl >> c) & 1) f.ctrl |= 1u << loc(c);
+                        memcpy(f.m, g[m].m, sizeof f.m);
+                        hg[fg_used++] = f;
+                    }
+                }
+                ho[go_used++] = (int)(fg_used - fg0);
             }
-            ApplyArgs a{};
-            a.nq = KQ;
-            for (int i = 0; i < KQ; ++i) a.pos[i] = pos[b][i];
-            a.rows = rows;
-            // tensor-core flops: three real GEMMs [rows x K] x [K x K] (3xTF32)
-            launch_begin(s, KC_FUSED, 2.0 * (double)s->bytes, 3.0 * 2.0 * (double)rows * K * K);
-            const float *bm = (const float *)(scratch + o_b) + b * 2 * (size_t)K * K;
-            if constexpr (KQ <= 5) {
-                k_fused_stream<KQ><<<(unsigned)pipe_grid, kStreamThreads, smp, s->stream>>>(
-                    (float *)s->amps, bm, a, (rows + kRows - 1) / kRows, s->dev_status);
-            } else {
-                k_fused_apply<KQ><<<(unsigned)((rows + kRows - 1) / kRows), kRows, sma, s->stream>>>(
-                    (float *)s->amps, bm, a, s->dev_status);
+            const size_t nb = blocks.size();
+            FGate *dg = (FGate *)(scratch + o_g) + fg0;
+            int *dgo = (int *)(scratch + o_o) + go0;
+            float *dw = (float *)(scratch + o_w + (size_t)slot * bytes_slot);
+            if ((fg_used > fg0 && cudaMemcpyAsync(dg, hg + fg0, (fg_used - fg0) * sizeof(FGate), cudaMemcpyHostToDevice,
+                                                  s->stream) != cudaSuccess) ||
+                cudaMemcpyAsync(dgo, ho + go0, (nb + 1) * sizeof(int), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+                rc = cuda_fail(cudaGetLastError(), "fused upload");
+                break;
             }
-            rc = launch_end(s, "fused apply");
+            launch_begin(s, KC_FUSE_BUILD, (double)nb * 2 * K * K * sizeof(float));
+            k_fuse_build<KQ><<<(unsigned)nb, 256, smb, s->stream>>>(dg, dgo, dw);
+            if ((rc = launch_end(s, "fused build"))) break;
+            for (size_t bi = 0; bi < nb && rc == SIM_OK; ++bi) {
+                if (blocks[bi].wide) {
+                    rc = launch_sgate(s, g[blocks[bi].members[0]]);
+                    continue;
+                }
+                ApplyArgs a{};
+                a.nq = KQ;
+                for (int i = 0; i < KQ; ++i) a.pos[i] = pos[bi][i];
+                a.rows = rows;
+                // tensor-core flops: three real GEMMs [rows x K] x [K x K] (3xTF32)
+                launch_begin(s, KC_FUSED, 2.0 * (double)s->bytes, 3.0 * 2.0 * (double)rows * K * K);
+                const float *bm = dw + bi * 2 * (size_t)K * K;
+                if constexpr (KQ <= 5) {
+                    k_fused_stream<KQ><<<(unsigned)pipe_grid, kStreamThreads, smp, s->stream>>>(
+                        (float *)s->amps, bm, a, (rows + kRows - 1) / kRows, s->dev_status);
+                } else {
+                    k_fused_apply<KQ><<<(unsigned)((rows + kRows - 1) / kRows), kRows, sma, s->stream>>>(
+                        (float *)s->amps, bm, a, s->dev_status);
+                }
+                rc = launch_end(s, "fused apply");
+            }
         }
     } while (0);
     cudaFreeAsync(scratch, s->stream);
@@ -918,42 +986,34 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, const std::vector<Bloc
 
 }  // namespace
 
-struct FusedPlan {
-    int n, k;
-    size_t n_gates;
-    std::vector<SGate> g;
-    std::vector<Block> blocks;
-};
-void FusedPlanFree::operator()(FusedPlan *p) const { delete p; }
-
-int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out, FusedPlanPtr *keep)
+int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out, int depth)
 {
-    FusedPlanPtr p(new FusedPlan{n, k, n_gates, {}, {}});
-    lower_gates(gates, n_gates, &p->g);
-    p->blocks = form_blocks(p->g, k, n);
-    if (blocks_out) *blocks_out = (int64_t)p->blocks.size();
-    if (keep) *keep = std::move(p);
+    std::vector<SGate> g;
+    lower_gates(gates, n_gates, &g);
+    BlockPlanner planner(g, k, n, depth > 0 ? depth : kRunDepth);
+    Block b;
+    int64_t nb = 0;
+    while (planner.next(&b)) ++nb;
+    if (blocks_out) *blocks_out = nb;
     return SIM_OK;
 }
 
-int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o,
-                        const FusedPlan *planned)
+int fused_feature_depth() { return kFeatureDepth; }
+
+int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
 {
     if (s->dtype != SIM_C64) return fail(SIM_EUNSUPPORTED, "fused plan: complex64 states only (TF32 tensor cores)");
     int k = o.fuse_k ? o.fuse_k : 5;
     if (k < 3 || k > 6) return fail(SIM_EINVAL, "fused plan: fuse_k must be in 3..6");
     if (s->n < k + 7) return fail(SIM_EINVAL, "fused plan: needs n >= fuse_k + 7 (one CTA covers 128 rows)");
-    FusedPlanPtr own;
-    if (!planned || planned->n != s->n || planned->k != k || planned->n_gates != n_gates) {
-        describe_fused(s->n, gates, n_gates, k, nullptr, &own);
-        planned = own.get();
-    }
-    if (planned->g.empty()) return SIM_OK;
+    std::vector<SGate> g;
+    lower_gates(gates, n_gates, &g);
+    if (g.empty()) return SIM_OK;
     switch (k) {
-    case 3: return run_fused<3>(s, planned->g, planned->blocks);
-    case 4: return run_fused<4>(s, planned->g, planned->blocks);
-    case 5: return run_fused<5>(s, planned->g, planned->blocks);
-    default: return run_fused<6>(s, planned->g, planned->blocks);
+    case 3: return run_fused<3>(s, g, kRunDepth);
+    case 4: return run_fused<4>(s, g, kRunDepth);
+    case 5: return run_fused<5>(s, g, kRunDepth);
+    default: return run_fused<6>(s, g, kRunDepth);
     }
 }
 

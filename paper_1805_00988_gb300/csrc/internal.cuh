@@ -157,22 +157,13 @@ int launch_sgate(qsim_state *s, const SGate &g);
 
 // ---------------------------------------------------------------- staged / fused plans
 int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
-// A fused plan (lowered gates and their blocks) formed once by describe_fused
-// and handed to apply_circuit_fused, so that a caller that has planned a
-// circuit to predict its cost does not plan it again to run it.
-struct FusedPlan;
-struct FusedPlanFree {
-    void operator()(FusedPlan *p) const;
-};
-using FusedPlanPtr = std::unique_ptr<FusedPlan, FusedPlanFree>;
-
-int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o,
-                        const FusedPlan *planned = nullptr);
+int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
 int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
-int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out,
-                  FusedPlanPtr *keep = nullptr);
-int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out,
-                   FusedPlanPtr *keep = nullptr);
+int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out);
+// blocks of the fused plan; depth 0 = the depth the plan runs with
+int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out, int depth = 0);
+// the (cheaper) planner depth the learned plan's features are computed with
+int fused_feature_depth();
 int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,
                     int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len);
 

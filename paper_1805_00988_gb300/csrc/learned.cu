@@ -67,7 +67,7 @@ bool feasible(int n, int dtype, int v)
 
 }  // namespace
 
-int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out, FusedPlanPtr *keep)
+int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out)
 {
     if (!feasible(n, dtype, v)) return SIM_EUNSUPPORTED;
     std::vector<SGate> g;
@@ -89,7 +89,10 @@ int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v
         lc = (double)l;
     } else if (v >= 3) {
         int64_t b = 0;
-        describe_fused(n, gates, n_gates, v, &b, keep);
+        // block count from the one-qubit-at-a-time planner: cheap enough to
+        // run for every window and variant; the run plans deeper, and the
+        // model learns the mapping from these features to its timings
+        describe_fused(n, gates, n_gates, v, &b, fused_feature_depth());
         launches = (double)b;
     }
     for (int i = 0; i < SIM_FEATURES; ++i) out[i] = 0.f;
@@ -144,15 +147,10 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
             if (feasible(s->n, s->dtype, v)) cand.push_back({w, v});
     std::vector<float> feat(cand.size() * SIM_FEATURES);
     std::vector<char> ok(cand.size(), 0);
-    // the block plans of the whole circuit are kept: if one of them wins it
-    // runs without being planned again
-    FusedPlanPtr whole_plan[SIM_VARIANTS];
     parallel_for(cand.size(), [&](size_t r) {
         const Window &w = seg[cand[r].first];
-        const int v = cand[r].second;
-        FusedPlanPtr *keep = (cand[r].first == nw && nw > 1 && v >= 3) ? &whole_plan[v] : nullptr;
-        ok[r] = plan_features(s->n, s->dtype, gates + w.first, w.count, v, feat.data() + r * SIM_FEATURES,
-                              keep) == SIM_OK;
+        ok[r] = plan_features(s->n, s->dtype, gates + w.first, w.count, cand[r].second,
+                              feat.data() + r * SIM_FEATURES) == SIM_OK;
     });
     std::vector<float> rows;
     std::vector<std::pair<size_t, int>> who;
@@ -202,8 +200,7 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
         } else if (vo.plan == SIM_PLAN_STAGED) {
             rc = apply_circuit_staged(s, gates + first, count, vo);
         } else {
-            const bool whole = first == 0 && count == n_gates && best[w] >= 3;
-            rc = apply_circuit_fused(s, gates + first, count, vo, whole ? whole_plan[best[w]].get() : nullptr);
+            rc = apply_circuit_fused(s, gates + first, count, vo);
         }
         if (rc) return rc;
         w = e;

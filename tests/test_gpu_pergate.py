@@ -153,8 +153,10 @@ def test_haar_cz_30q_mirror(sim):
 
 
 @pytest.mark.parametrize("dt", ["c64", "c128"])
-def test_reductions_and_probabilities(sim, orc, dt):
-    n = 16
+@pytest.mark.parametrize("n", [2, 3, 4, 5, 16, 21])
+def test_reductions_and_probabilities(sim, orc, dt, n):
+    """n < 4 takes the per-amplitude <sum Z> kernel, n >= 4 the chunked one;
+    21 qubits spread the chunks over every block of the fixed grid."""
     g = C.random_gates(n, 60, seed=2)
     st = sim.State(n, dt)
     st.apply(g)
