@@ -712,13 +712,16 @@ struct Block {
 // (ties: the smaller set, then the earlier candidates).  Then every remaining
 // gate that commutes with the gates skipped before it and lies on the block's
 // qubits joins.  depth 1 adds one qubit at a time; depth 2 also weighs pairs
-// (two qubits that only pay off together, such as the two ends of a CZ).
+// (two qubits that only pay off together, such as the two ends of a CZ),
+// depth 3 triples (split over the host threads).
 // Blocks come out one at a time, so that a caller can launch the first ones
 // while it plans the rest.
 class BlockPlanner {
 public:
     BlockPlanner(const std::vector<SGate> &g, int k, int n, int depth)
         : g_(g), k_(k), n_(n), depth_(depth), done_(g.size(), 0) {}
+
+    void set_depth(int d) { depth_ = d; }
 
     bool next(Block *b)
     {
@@ -754,6 +757,23 @@ public:
                         const int c2 = absorb(S | a2);
                         if (c2 > best) { best = c2; best_add = a2; }
                     }
+            }
+            if (depth_ >= 3 && free >= 3) {
+                // triples, split by their first candidate over host threads;
+                // each slice keeps its first best, the earliest slice wins ties
+                const size_t nc = cand.size();
+                std::vector<int> sbest(nc, -1);
+                std::vector<uint64_t> sadd(nc, 0);
+                parallel_for(nc, [&](size_t i) {
+                    for (size_t j = i + 1; j < nc; ++j)
+                        for (size_t l = j + 1; l < nc; ++l) {
+                            const uint64_t a3 = (1ull << cand[i]) | (1ull << cand[j]) | (1ull << cand[l]);
+                            const int c3 = absorb(S | a3);
+                            if (c3 > sbest[i]) { sbest[i] = c3; sadd[i] = a3; }
+                        }
+                });
+                for (size_t i = 0; i < nc; ++i)
+                    if (sbest[i] > best) { best = sbest[i]; best_add = sadd[i]; }
             }
             if (!best_add) break;
             S |= best_add;
@@ -818,7 +838,7 @@ private:
 
 // the planner depth the fused plan runs with, and the cheaper one the learned
 // plan uses to predict block counts for its features
-constexpr int kRunDepth = 2;
+constexpr int kRunDepth = 3;
 constexpr int kFeatureDepth = 1;
 
 // CTAs of one kernel that fit on an SM at once: registers (allocated per warp
@@ -903,7 +923,8 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
             const uint64_t tiles = (rows + kRows - 1) / kRows;
             pipe_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms * per_sm);
         }
-        BlockPlanner planner(g, KQ, n, depth);
+        // the first group is planned at depth <= 2 (its planning time is exposed)
+        BlockPlanner planner(g, KQ, n, std::min(depth, 2));
         size_t fg_used = 0, go_used = 0;
         int slot = 0;
         for (size_t grp = 0; rc == SIM_OK; ++grp, slot ^= 1) {
@@ -913,6 +934,7 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
             const size_t want = grp == 0 ? kFirst : kGroup;
             while (blocks.size() < want && planner.next(&b)) blocks.push_back(b);
             if (blocks.empty()) break;
+            if (grp == 0) planner.set_depth(depth);
             // pad every block to KQ qubits (identity on the added ones); gates in block-local qubits
             const size_t fg0 = fg_used, go0 = go_used;
             std::vector<std::vector<int>> pos(blocks.size());

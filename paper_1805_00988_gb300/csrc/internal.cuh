@@ -5,6 +5,9 @@
 #include <stdint.h>
 
 #include <string>
+#include <atomic>
+#include <thread>
+#include <algorithm>
 #include <memory>
 #include <vector>
 
@@ -166,6 +169,26 @@ int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t 
 int fused_feature_depth();
 int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,
                     int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len);
+
+// f(0) .. f(count - 1) on up to 16 host threads (plain loop for one)
+template <typename F>
+void parallel_for(size_t count, F f)
+{
+    size_t nt = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
+    nt = std::min(nt, count);
+    if (nt <= 1) {
+        for (size_t i = 0; i < count; ++i) f(i);
+        return;
+    }
+    std::atomic<size_t> next{0};
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (size_t t = 0; t < nt; ++t)
+        th.emplace_back([&] {
+            for (size_t i; (i = next.fetch_add(1)) < count;) f(i);
+        });
+    for (auto &x : th) x.join();
+}
 
 // host-side SplitMix64 draw (Steele, Lea & Flood 2014)
 uint64_t splitmix64_host(uint64_t x);

@@ -28,26 +28,6 @@ struct Window {
     size_t first, count;
 };
 
-// f(0) .. f(count - 1) on up to 16 host threads
-template <typename F>
-void parallel_for(size_t count, F f)
-{
-    size_t nt = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
-    nt = std::min(nt, count);
-    if (nt <= 1) {
-        for (size_t i = 0; i < count; ++i) f(i);
-        return;
-    }
-    std::atomic<size_t> next{0};
-    std::vector<std::thread> th;
-    th.reserve(nt);
-    for (size_t t = 0; t < nt; ++t)
-        th.emplace_back([&] {
-            for (size_t i; (i = next.fetch_add(1)) < count;) f(i);
-        });
-    for (auto &x : th) x.join();
-}
-
 int variant_opts(int v, sim_plan_opts *o)
 {
     memset(o, 0, sizeof *o);
