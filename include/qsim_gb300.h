@@ -226,7 +226,10 @@ int sim_last_plan(sim_t s, int32_t *variants, size_t cap, size_t *len);
  *   changes, and the order in which the gates are applied (circuit indices;
  *   a SWAP appears three times, lowered to three CNOT-type moves; identity
  *   gates are dropped) -- up to order_cap entries, the full length in
- *   *order_len.  SIM_EINVAL if no tile fits (n below 11) or a gate is invalid. */
+ *   *order_len.  SIM_EINVAL if no tile fits (n below 11) or a gate is invalid.
+ *   With opts->plan = SIM_PLAN_FUSED, *passes gets the number of fused blocks
+ *   the fused plan forms for opts->fuse_k (0 = 5); *ops, *layout_changes and
+ *   *order_len are set to 0.  Other plans: SIM_EUNSUPPORTED. */
 int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts,
                       int64_t *passes, int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap,
                       size_t *order_len);
@@ -238,7 +241,9 @@ int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, c
  *   sim_kernel_class_name) the launches, summed device milliseconds and
  *   summed algorithmic bytes (the state bytes each launch must read and
  *   write: 2S / 2^c for a dense gate with c controls, S for a pass over the
- *   whole state, ...) since the last reset; any output array may be NULL;
+ *   whole state, ...) and summed algorithmic flops (8 per complex multiply-
+ *   add of the gate arithmetic; 3 real GEMMs per fused block) since the last
+ *   reset; any output array may be NULL;
  *   reset != 0 clears the counters.  Fills at most max_classes entries.
  * sim_launch_count: kernels this handle has launched since creation. */
 int sim_profile_enable(sim_t s, int on);

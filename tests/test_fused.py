@@ -132,9 +132,15 @@ def test_block_planner_handles_gates_wider_than_k_cpu():
 
 
 @pytest.mark.gpu
-def test_fused_wide_gates(gsim, orc):
+@pytest.mark.parametrize("where", ["first", "late"])
+def test_fused_wide_gates(gsim, orc, where):
+    """A gate wider than k runs as its own per-gate launch between blocks,
+    first or deep inside the circuit (then in a later group of the
+    plan-as-you-launch pipeline)."""
     n = 12
-    g = C.concat([C.gate("swap", 0, target2=5, controls=(2, 9)), C.random_gates(n, 100, seed=8)])
+    wide = C.gate("swap", 0, target2=5, controls=(2, 9))
+    g = (C.concat([wide, C.random_gates(n, 100, seed=8)]) if where == "first" else
+         C.concat([C.random_gates(n, 150, seed=8), wide, C.random_gates(n, 100, seed=9), wide]))
     st = gsim.State(n, "c64")
     psi = C.random_state(n, seed=2)
     st.load(psi)
