@@ -61,6 +61,24 @@ TRAFFIC = {
 }
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The largest x over all ranks (a timed region ends when the slowest
+    rank's does); with one rank, x itself."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput of independent replicas: every rank processed
+    units_per_rank units in `seconds` (the max over ranks)."""
+    return world * units_per_rank / seconds
+
+
 def traffic_for(kind: str, n: int):
     """DRAM bytes of one launch of the kernel class at n qubits, or None.
     The hash covers the source file up to the marker `until` (the device code
@@ -298,12 +316,9 @@ def run_ours(args, rank, world, local_rank):
     launches = sim.sim_launch_count(st.h) - l0
     prof = sim.sim_profile_read(st.h, reset=True)
     sim.sim_profile_enable(st.h, False)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_per_step = ms / args.steps
-    gates_per_s = world * len(gates) / (ms_per_step / 1e3)
+    gates_per_s = job_rate(len(gates), world, ms_per_step / 1e3)
     step_bytes = sum(v[2] for v in prof.values()) / args.steps
     peaks, peak_kind = load_peaks()
 
@@ -362,11 +377,8 @@ def run_ours(args, rank, world, local_rank):
         sim.sim_sample(st.h, shots, 99, out=host_shots)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * len(gates) / e2e_s, "unit": "gates/s", "h2d_bytes_per_step": int(sg.nbytes),
+    e2e_s = max_over_ranks(e2e_s, world, dev)
+    e2e = {"value": job_rate(len(gates), world, e2e_s), "unit": "gates/s", "h2d_bytes_per_step": int(sg.nbytes),
            "d2h_bytes_per_step": int(shots * 8 + 16)}
 
     line = {"metric": METRIC, "value": gates_per_s, "unit": "gates/s", "n_gpus": world, "steps": args.steps,

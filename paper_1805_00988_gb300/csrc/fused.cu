@@ -839,6 +839,7 @@ private:
 // the planner depth the fused plan runs with, and the cheaper one the learned
 // plan uses to predict block counts for its features
 constexpr int kRunDepth = 3;
+constexpr size_t kFirstGroup = 2;   // blocks of the first group (planned at depth <= 2)
 constexpr int kFeatureDepth = 1;
 
 // CTAs of one kernel that fit on an SM at once: registers (allocated per warp
@@ -875,7 +876,7 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
 {
     constexpr int K = 2 << KQ;
     constexpr size_t kGroup = 8;                       // blocks per group after the first
-    constexpr size_t kFirst = 2;                       // blocks in the first group
+    constexpr size_t kFirst = kFirstGroup;
     const int n = s->n;
     const size_t ng = g.size();
     // per call: gate lists (<= ng FGates, <= 2 ng + 1 offsets), W slots (2 x kGroup blocks)
@@ -1012,10 +1013,13 @@ int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t 
 {
     std::vector<SGate> g;
     lower_gates(gates, n_gates, &g);
-    BlockPlanner planner(g, k, n, depth > 0 ? depth : kRunDepth);
+    // the same schedule as the run: the first group's blocks at depth <= 2
+    const int d = depth > 0 ? depth : kRunDepth;
+    BlockPlanner planner(g, k, n, std::min(d, 2));
     Block b;
     int64_t nb = 0;
-    while (planner.next(&b)) ++nb;
+    while (planner.next(&b))
+        if (++nb == (int64_t)kFirstGroup) planner.set_depth(d);
     if (blocks_out) *blocks_out = nb;
     return SIM_OK;
 }
