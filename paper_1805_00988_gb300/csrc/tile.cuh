@@ -209,6 +209,27 @@ __device__ __forceinline__ void xop(Regs<R, RA> &v, uint64_t act, const CoefS<R>
                     }
                 }
             }
+        } else if constexpr (sizeof(R) == 4 && J == 0) {
+            // packed, the pair inside one pack: pack p = (amplitude 2p, 2p + 1)
+            const float2 q1 = make_float2(c.ar, c.dr), q2 = make_float2(c.br, c.cr);
+            const float2 q3 = make_float2(-c.ai, -c.di), q4 = make_float2(-c.bi, -c.ci);
+            const float2 q5 = make_float2(c.ai, c.di), q6 = make_float2(c.bi, c.ci);
+#pragma unroll
+            for (int p = 0; p < RA / 2; ++p) {
+                if (!PLAIN && !((act >> (2 * p)) & 1)) continue;
+                const float2 R0 = v.r[p], I0 = v.i[p];
+                const float2 Rs = make_float2(R0.y, R0.x), Is = make_float2(I0.y, I0.x);
+                if (KIND == SK_DENSE) {
+                    v.r[p] = __ffma2_rn(q1, R0, __ffma2_rn(q2, Rs, __ffma2_rn(q3, I0, __fmul2_rn(q4, Is))));
+                    v.i[p] = __ffma2_rn(q1, I0, __ffma2_rn(q2, Is, __ffma2_rn(q5, R0, __fmul2_rn(q6, Rs))));
+                } else if (KIND == SK_ANTI) {
+                    v.r[p] = __ffma2_rn(q2, Rs, __fmul2_rn(q4, Is));
+                    v.i[p] = __ffma2_rn(q2, Is, __fmul2_rn(q6, Rs));
+                } else {
+                    v.r[p] = Rs;
+                    v.i[p] = Is;
+                }
+            }
         } else {
 #pragma unroll
             for (int k = 0; k < RA; ++k) {

@@ -276,3 +276,29 @@ def test_launches_are_counted(sim):
     st.apply(C.random_gates(10, 25, seed=1))
     assert sim.sim_launch_count(st.h) - c0 >= 20
     st.close()
+
+
+def test_maximum_register_34_qubits(sim):
+    """n = 34, the largest register the ABI accepts (2^34 complex64
+    amplitudes, 128 GiB): H on the lowest and highest qubit and a CNOT from
+    qubit 0 to qubit 20 make |psi> = (|0> + |x1> + |x2> + |x3>) / 2 with
+    x1 = 2^0 + 2^20, x2 = 2^33, x3 = 2^33 + 2^0 + 2^20; every other amplitude
+    stays exactly zero and every shot lands on one of the four."""
+    import torch
+    n = 34
+    free, _ = torch.cuda.mem_get_info()
+    if free < (2 ** n) * 8 + (4 << 30):
+        pytest.skip("needs 132 GiB of free device memory")
+    g = C.concat([C.gate("h", 0), C.gate("h", 33), C.gate("x", 20, controls=(0,))])
+    st = sim.State(n, "c64")
+    st.apply(g)
+    support = [0, (1 << 0) | (1 << 20), 1 << 33, (1 << 33) | (1 << 0) | (1 << 20)]
+    for j in support:
+        assert abs(complex(st.tensor[j].item()) - 0.5) < 1e-7
+    for j in (1, 1 << 20, (1 << 33) | 1, (1 << 34) - 1):
+        assert complex(st.tensor[j].item()) == 0
+    assert abs(st.norm2() - 1.0) < 1e-6
+    shots = st.sample(20000, seed=34)
+    assert set(np.unique(shots).tolist()) <= set(support)
+    assert len(np.unique(shots)) == 4
+    st.close()
