@@ -329,7 +329,7 @@ def run_ours(args, rank, world, local_rank):
     gbs = (dbytes / dl) / sec / 1e9
     tflops = (dflops / dl) / sec / 1e12
     hbm_frac = gbs / peaks["hbm_gbs"]
-    if dname == "fused":
+    if dname in ("fused", "fused_multi"):
         # tensor-core TF32 work: the measured sustained bf16 peak scaled by the
         # nominal TF32 / bf16 dense ratio (1.1 / 2.25 PFLOP/s)
         cpeak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)

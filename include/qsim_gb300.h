@@ -88,8 +88,15 @@ typedef struct sim_plan_opts {
     int32_t plan;            /* sim_plan_kind */
     int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block, 3..6 (0 = 5) */
     int32_t tile_qubits;     /* SIM_PLAN_STAGED: tile size log2 (0 = default) */
-    int32_t flags;           /* reserved, 0 */
+    int32_t flags;           /* SIM_FLAG_* bits, 0 = defaults */
 } sim_plan_opts;
+
+/* SIM_PLAN_FUSED, k = 5: apply each pair of consecutive blocks whose qubits
+ * (with qubit 0) fit one 12-qubit tile in a single pass over the state (the
+ * tile stays in shared memory between the two blocks).  Off by default: on
+ * this GPU the pass costs more than two single-block passes (the per-tile
+ * chain convert -> MMA -> write-back -> convert -> MMA runs serially). */
+#define SIM_FLAG_MULTI_BLOCK_PASSES 1
 
 /* ---- handles --------------------------------------------------------------
  * sim_create: allocate a 2^n state on the current CUDA device and set it to
@@ -227,9 +234,11 @@ int sim_last_plan(sim_t s, int32_t *variants, size_t cap, size_t *len);
  *   a SWAP appears three times, lowered to three CNOT-type moves; identity
  *   gates are dropped) -- up to order_cap entries, the full length in
  *   *order_len.  SIM_EINVAL if no tile fits (n below 11) or a gate is invalid.
- *   With opts->plan = SIM_PLAN_FUSED, *passes gets the number of fused blocks
- *   the fused plan forms for opts->fuse_k (0 = 5); *ops, *layout_changes and
- *   *order_len are set to 0.  Other plans: SIM_EUNSUPPORTED. */
+ *   With opts->plan = SIM_PLAN_FUSED (fuse_k 0 = 5): *passes gets the passes
+ *   the fused plan makes over the state (a multi-block pass counts once,
+ *   see SIM_FLAG_MULTI_BLOCK_PASSES),
+ *   *ops the fused blocks; *layout_changes and *order_len are set to 0.
+ *   Other plans: SIM_EUNSUPPORTED. */
 int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts,
                       int64_t *passes, int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap,
                       size_t *order_len);

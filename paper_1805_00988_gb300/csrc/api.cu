@@ -34,7 +34,8 @@ int cuda_fail(cudaError_t e, const char *what)
 const char *kernel_class_name(int k)
 {
     static const char *names[KC_COUNT] = {"init", "dense", "diag", "perm", "swap", "staged", "fused",
-                                          "fuse_build", "prob", "reduce", "collapse", "sample", "batch", "mlp"};
+                                          "fuse_build", "prob", "reduce", "collapse", "sample", "batch", "mlp",
+                                          "fused_multi"};
     return (k >= 0 && k < KC_COUNT) ? names[k] : "?";
 }
 
@@ -372,10 +373,15 @@ int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, c
     }
     const int plan = opts ? opts->plan : SIM_PLAN_PER_GATE;
     if (plan == SIM_PLAN_FUSED) {
-        if (ops) *ops = 0;
+        // *passes: passes over the state; *ops: fused blocks
         if (layout_changes) *layout_changes = 0;
         if (order_len) *order_len = 0;
-        return describe_fused(n, gates, n_gates, opts->fuse_k ? opts->fuse_k : 5, passes);
+        int64_t blocks = 0, np = 0;
+        const int rc = describe_fused(n, gates, n_gates, opts->fuse_k ? opts->fuse_k : 5, &blocks, 0,
+                                      (opts->flags & SIM_FLAG_MULTI_BLOCK_PASSES) != 0, &np);
+        if (passes) *passes = np;
+        if (ops) *ops = blocks;
+        return rc;
     }
     if (plan != SIM_PLAN_STAGED) return fail(SIM_EUNSUPPORTED, "sim_plan_describe: staged or fused plans only");
     return describe_staged(n, dtype, gates, n_gates, opts->tile_qubits, passes, ops, layout_changes, order,

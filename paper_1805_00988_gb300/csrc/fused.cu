@@ -689,6 +689,309 @@ size_t stream_smem_bytes()
            (size_t)(2 * StreamCfg<KQ>::AB * kRows * K + 2 * K * K) * sizeof(float);
 }
 
+// ------------------------------------------------------------------ multi-block passes (k = 5)
+// Several consecutive blocks whose qubits fit one 12-qubit tile set T are
+// applied to each tile while it stays in shared memory: one HBM read and one
+// write for the whole run of blocks instead of one per block.  For block j the
+// tile is viewed as 128 rows (the 7 qubits of T outside the block) x 32
+// columns (the block's qubits); the tile is kept in T's own index order.
+//   warps 9-10: load tiles into a ring of two stages with 16-byte cp.async
+//       (T may be any 12 qubits that include qubit 0, so runs can be as short
+//       as two amplitudes); each loader thread's arrival on the stage's
+//       mbarrier fires when its copies have landed;
+//   warps 0-3: per block, row r of the current view into A (hi / lo, one
+//       buffer, after the MMAs of the previous step are done with it);
+//   warp 8: the 3xTF32 MMAs of the step with that block's W;
+//   warps 4-7: drain the accumulator -- back into the tile in shared memory
+//       for every block but the last, to HBM for the last.
+// Steps s = (tile, block) run in order; every wait is bounded.
+constexpr int kMaxPass = 2;
+constexpr int kMultiThreads = 352;
+
+struct PassArgs {
+    int m;                       // blocks in the pass, 2..kMaxPass
+    int tpos[12];                // tile qubits, ascending (tpos[0] = 0)
+    int pos[kMaxPass][5];        // qubits of block j, ascending, all in tpos
+};
+
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive(uint64_t *bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kMultiThreads, 1)
+    k_fused_multi(float *__restrict__ st, const float *__restrict__ bmat, PassArgs a, uint64_t ntiles,
+                  int *__restrict__ status)
+{
+    constexpr int KQ = 5;
+    constexpr int D = 1 << KQ;
+    constexpr int K = 2 * D;
+    constexpr int N = K;
+    constexpr int TB = 12;
+    constexpr int TAMP = 1 << TB;
+    constexpr uint32_t NC = 2 * N;
+    constexpr uint32_t NCOLS = 2 * NC;
+    constexpr uint32_t SBO = (K / 4) * 128;
+    constexpr uint32_t IDESC2 = make_idesc_tf32(kRows, 2 * N);
+    constexpr uint32_t IDESC1 = make_idesc_tf32(kRows, N);
+    constexpr int ABUF = kRows * K;
+    constexpr int WBLK = 2 * N * K;              // floats of one block's W (hi then lo)
+    constexpr int kLoaders = 64;
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float2 *stage = reinterpret_cast<float2 *>(smem);                               // 2 x TAMP
+    float *a_hi = reinterpret_cast<float *>(smem + 2 * (size_t)TAMP * sizeof(float2));
+    float *a_lo = a_hi + ABUF;
+    float *wbuf = a_lo + ABUF;                                                        // m x WBLK
+    __shared__ uint64_t bar_full[2], bar_empty[2], bar_a, bar_d[2], bar_e[2], bar_w;
+    __shared__ uint32_t tslot;
+    __shared__ int tpos[TB];
+    __shared__ uint32_t uc[kMaxPass][D];         // tile-local offset of column c in view j
+    __shared__ uint32_t urs[kMaxPass][kRows];    // tile-local offset of row r in view j
+    __shared__ uint64_t gr_last[kRows];          // global offset of row r in the last view
+    __shared__ uint64_t gc_last[D];              // global offset of column c in the last view
+    __shared__ uint64_t dlo[64], dhi[64];        // global offsets of tile-local index bits 0-5 / 6-11
+    __shared__ int xs[kMaxPass];                 // bank spreading: zc of view j
+    __shared__ int failed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = a.m;
+    if (tid == 0) failed = *reinterpret_cast<volatile int *>(status);
+    if (tid < TB) tpos[tid] = a.tpos[tid];
+    __syncthreads();
+    if (failed) return;
+    if (warp == 0) tmem_alloc(&tslot, NCOLS);
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_full[b], kLoaders);
+            mbar_init(&bar_empty[b], kRows);
+            mbar_init(&bar_d[b], 1);
+            mbar_init(&bar_e[b], kRows);
+        }
+        mbar_init(&bar_a, kRows);
+        mbar_init(&bar_w, kRows);
+    }
+    // view tables
+    auto local_of = [&](int q) {
+        for (int t = 0; t < TB; ++t)
+            if (tpos[t] == q) return t;
+        return 0;
+    };
+    for (int e = tid; e < kMaxPass * D; e += kMultiThreads) {
+        const int j = e / D, c = e % D;
+        uint32_t u = 0;
+        if (j < m)
+            for (int i = 0; i < KQ; ++i)
+                if ((c >> i) & 1) u |= 1u << local_of(a.pos[j][i]);
+        uc[j][c] = u;
+        if (j == m - 1) {
+            uint64_t g = 0;
+            for (int i = 0; i < KQ; ++i)
+                if ((c >> i) & 1) g |= 1ull << a.pos[j][i];
+            gc_last[c] = g;
+        }
+    }
+    for (int e = tid; e < kMaxPass * kRows; e += kMultiThreads) {
+        const int j = e / kRows, r = e % kRows;
+        uint32_t u = 0;
+        uint64_t g = 0;
+        if (j < m) {
+            uint32_t pm = 0;
+            for (int i = 0; i < KQ; ++i) pm |= 1u << local_of(a.pos[j][i]);
+            for (int t = 0, i = 0; t < TB; ++t) {
+                if ((pm >> t) & 1) continue;
+                if ((r >> i) & 1) {
+                    u |= 1u << t;
+                    g |= 1ull << tpos[t];
+                }
+                ++i;
+            }
+        }
+        urs[j][r] = u;
+        if (j == m - 1) gr_last[r] = g;
+    }
+    for (int e = tid; e < 128; e += kMultiThreads) {
+        const int hi = e >> 6, v = e & 63;
+        uint64_t g = 0;
+        for (int b = 0; b < 6; ++b)
+            if ((v >> b) & 1) g |= 1ull << tpos[6 * hi + b];
+        (hi ? dhi : dlo)[v] = g;
+    }
+    if (tid < kMaxPass) {
+        int zc = 0;
+        if (tid < m)
+            for (int t = 0; t < 4; ++t)
+                for (int i = 0; i < KQ; ++i) zc += (a.pos[tid][i] == tpos[t]);
+        xs[tid] = zc;
+    }
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(bmat);
+        float4 *dst = reinterpret_cast<float4 *>(wbuf);
+        for (int e = tid; e < m * WBLK / 4; e += kMultiThreads) dst[e] = __ldg(src + e);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = tslot;
+    volatile int *vfailed = &failed;
+    const uint64_t step = gridDim.x;
+    const int iters = ((uint64_t)blockIdx.x < ntiles) ? (int)((ntiles - 1 - blockIdx.x) / step + 1) : 0;
+    auto tile_base = [&](uint64_t t) {
+        uint64_t b = t;
+#pragma unroll
+        for (int q = 0; q < TB; ++q) {
+            const int p = tpos[q];
+            b = ((b >> p) << (p + 1)) | (b & ((1ull << p) - 1ull));
+        }
+        return b;
+    };
+
+    if (warp >= 9) {
+        // loaders: thread lt copies 16-byte pairs of amplitudes u = 2 (lt + 64 k)
+        const int lt = tid - 9 * 32;
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int sg = i & 1;
+            if (i >= 2 && !mbar_wait_bounded(&bar_empty[sg], (uint32_t)(((i >> 1) - 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step);
+            float2 *dst = stage + (size_t)sg * TAMP;
+#pragma unroll 4
+            for (int k = 0; k < TAMP / 2 / kLoaders; ++k) {
+                const uint32_t u = 2u * (uint32_t)(lt + kLoaders * k);
+                const uint64_t g = base | dlo[u & 63] | dhi[u >> 6];
+                cp_async16(dst + u, st + 2 * g);
+            }
+            cp_async_arrive(&bar_full[sg]);
+        }
+        cp_async_wait_all();
+    } else if (warp < 4) {
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int sg = i & 1;
+            const float2 *X = stage + (size_t)sg * TAMP;
+            for (int j = 0; j < m && !*vfailed; ++j) {
+                const int s = i * m + j;
+                bool ok;
+                if (j == 0) ok = mbar_wait_bounded(&bar_full[sg], (uint32_t)((i >> 1) & 1));
+                else ok = mbar_wait_bounded(&bar_w, (uint32_t)((i * (m - 1) + j - 1) & 1));
+                if (!ok) { *vfailed = 1; break; }
+                const int zc = xs[j];
+                const int x = (tid >> (4 - zc)) & ((1 << zc) - 1);
+                const uint32_t ur = urs[j][tid], ux = uc[j][x];
+                float2 v[D];
+#pragma unroll
+                for (int c = 0; c < D; ++c) v[c] = X[(ur | uc[j][c]) ^ ux];
+                if (j == m - 1) mbar_arrive(&bar_empty[sg]);
+                if (s >= 1 && !mbar_wait_bounded(&bar_d[(s - 1) & 1], (uint32_t)(((s - 1) >> 1) & 1))) {
+                    *vfailed = 1;
+                    break;
+                }
+                unsigned char *ahi = reinterpret_cast<unsigned char *>(a_hi);
+                unsigned char *alo = reinterpret_cast<unsigned char *>(a_lo);
+#pragma unroll
+                for (int c = 0; c < D; c += 2) {
+                    const uint32_t off = kmajor_off(tid, 2 * ((c ^ x) & ~1), K);
+                    const float2 e0 = (x & 1) ? v[c + 1] : v[c], e1 = (x & 1) ? v[c] : v[c + 1];
+                    const float h0 = tf32_rn(e0.x), h1 = tf32_rn(e0.y);
+                    const float h2 = tf32_rn(e1.x), h3 = tf32_rn(e1.y);
+                    *reinterpret_cast<float4 *>(ahi + off) = make_float4(h0, h1, h2, h3);
+                    *reinterpret_cast<float4 *>(alo + off) = make_float4(tf32_rn(e0.x - h0), tf32_rn(e0.y - h1),
+                                                                         tf32_rn(e1.x - h2), tf32_rn(e1.y - h3));
+                }
+                fence_async_smem();
+                mbar_arrive(&bar_a);
+            }
+        }
+    } else if (warp < 8) {
+        const int r = tid - 128;
+        const uint64_t gr = gr_last[r];
+        const bool q0_last = a.pos[m - 1][0] == 0;
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int sg = i & 1;
+            float2 *X = stage + (size_t)sg * TAMP;
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
+            for (int j = 0; j < m && !*vfailed; ++j) {
+                const int s = i * m + j;
+                const int sb = s & 1;
+                if (!mbar_wait_bounded(&bar_d[sb], (uint32_t)((s >> 1) & 1))) { *vfailed = 1; break; }
+                tc_fence_after();
+                const uint32_t lane_base = taddr + (uint32_t)(sb * NC) + ((uint32_t)((warp - 4) * 32) << 16);
+                const bool last = j == m - 1;
+                const uint32_t ur = urs[j][r];
+#pragma unroll
+                for (int col = 0; col < N; col += 32) {
+                    uint32_t hi[32], lo[32];
+                    tmem_ld32_nowait(lane_base + (uint32_t)col, hi);
+                    tmem_ld32_nowait(lane_base + (uint32_t)(N + col), lo);
+                    tmem_wait_ld();
+                    float v[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(hi[e]) + __uint_as_float(lo[e]);
+                    if (!last) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            X[ur | uc[j][col / 2 + e]] = make_float2(v[2 * e], v[2 * e + 1]);
+                    } else if (q0_last) {
+#pragma unroll
+                        for (int e = 0; e < 16; e += 2)
+                            *reinterpret_cast<float4 *>(st + 2 * (base | gc_last[col / 2 + e])) =
+                                make_float4(v[2 * e], v[2 * e + 1], v[2 * e + 2], v[2 * e + 3]);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            *reinterpret_cast<float2 *>(st + 2 * (base | gc_last[col / 2 + e])) =
+                                make_float2(v[2 * e], v[2 * e + 1]);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&bar_e[sb]);
+                if (!last) mbar_arrive(&bar_w);
+            }
+        }
+    } else if (lane == 0) {
+        const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo);
+        for (int i = 0; i < iters && !*vfailed; ++i)
+            for (int j = 0; j < m && !*vfailed; ++j) {
+                const int s = i * m + j;
+                const int sb = s & 1;
+                if (!mbar_wait_bounded(&bar_a, (uint32_t)(s & 1))) { *vfailed = 1; break; }
+                if (s >= 2 && !mbar_wait_bounded(&bar_e[sb], (uint32_t)(((s - 2) >> 1) & 1))) { *vfailed = 1; break; }
+                tc_fence_after();
+                const uint32_t sb_hi = smem_u32(wbuf + (size_t)j * WBLK);
+                const uint32_t d = taddr + (uint32_t)(sb * NC);
+#pragma unroll 1
+                for (int ks = 0; ks < K / 8; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256;
+                    mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC2, ks > 0);
+                    mma_tf32(d, make_desc(sa_lo + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC1, 1);
+                }
+                mma_commit(&bar_d[sb]);
+            }
+    }
+    if (*vfailed) {
+        if (tid == 0) atomicExch(status, SIM_ETIMEOUT);
+        const int last = iters * m - 1;
+        if (tid == 256 && last >= 0) mbar_wait_bounded(&bar_d[last & 1], (uint32_t)((last >> 1) & 1));
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, NCOLS);
+}
+
+size_t multi_smem_bytes(int m)
+{
+    constexpr int K = 64;
+    return 2 * (size_t)4096 * sizeof(float2) + (size_t)(2 * kRows * K) * sizeof(float) +
+           (size_t)m * 2 * K * K * sizeof(float);
+}
+
 template <int KQ>
 size_t apply_smem_bytes()
 {
@@ -836,10 +1139,31 @@ private:
     uint64_t touched_ = 0;
 };
 
+// Multi-block passes (k = 5): consecutive pairs of blocks whose qubits, with
+// qubit 0, fit one 12-qubit tile run as one pass; tileset[b] = the tile's
+// qubits (padded with the lowest others) for the first block of a pair, 0
+// otherwise; second[b] marks the pair's second block.
+void pair_blocks(const std::vector<Block> &blocks, int n, bool on, std::vector<uint64_t> *tileset,
+                 std::vector<char> *second)
+{
+    tileset->assign(blocks.size(), 0);
+    second->assign(blocks.size(), 0);
+    if (!on || n < 12) return;
+    for (size_t bi = 0; bi + 1 < blocks.size(); ++bi) {
+        if (blocks[bi].wide || blocks[bi + 1].wide || (*second)[bi]) continue;
+        uint64_t T = blocks[bi].qmask | blocks[bi + 1].qmask | 1ull;
+        if (__builtin_popcountll(T) > 12) continue;
+        for (int extra = 0; extra < n && __builtin_popcountll(T) < 12; ++extra) T |= 1ull << extra;
+        (*tileset)[bi] = T;
+        (*second)[bi + 1] = 1;
+    }
+}
+
 // the planner depth the fused plan runs with, and the cheaper one the learned
 // plan uses to predict block counts for its features
 constexpr int kRunDepth = 3;
 constexpr size_t kFirstGroup = 2;   // blocks of the first group (planned at depth <= 2)
+constexpr size_t kGroupBlocks = 8;  // blocks of every later group
 constexpr int kFeatureDepth = 1;
 
 // CTAs of one kernel that fit on an SM at once: registers (allocated per warp
@@ -872,10 +1196,10 @@ int resident_ctas(int dev, const void *fn, int threads, size_t dyn_smem)
 // reuse within a call); the W matrices use two device slots, reused in
 // stream order.
 template <int KQ>
-int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
+int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_multi)
 {
     constexpr int K = 2 << KQ;
-    constexpr size_t kGroup = 8;                       // blocks per group after the first
+    constexpr size_t kGroup = kGroupBlocks;
     constexpr size_t kFirst = kFirstGroup;
     const int n = s->n;
     const size_t ng = g.size();
@@ -925,6 +1249,17 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
             pipe_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms * per_sm);
         }
         // the first group is planned at depth <= 2 (its planning time is exposed)
+        int multi_grid = 0;
+        size_t smm = 0;
+        const bool multi = KQ == 5 && n >= 12 && allow_multi;
+        if (multi) {
+            smm = multi_smem_bytes(kMaxPass);
+            cudaFuncSetAttribute(k_fused_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm);
+            cudaFuncSetAttribute(k_fused_multi, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared);
+            const uint64_t tiles = (rows + kRows - 1) / kRows;
+            multi_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms);
+        }
         BlockPlanner planner(g, KQ, n, std::min(depth, 2));
         size_t fg_used = 0, go_used = 0;
         int slot = 0;
@@ -936,14 +1271,23 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
             while (blocks.size() < want && planner.next(&b)) blocks.push_back(b);
             if (blocks.empty()) break;
             if (grp == 0) planner.set_depth(depth);
-            // pad every block to KQ qubits (identity on the added ones); gates in block-local qubits
+            // k = 5: consecutive pairs of blocks whose qubits, with qubit 0,
+            // fit one 12-qubit tile run as one multi-block pass
+            std::vector<uint64_t> tileset;   // T of the pass a block opens, 0 = single
+            std::vector<char> second;        // block runs inside the previous block's pass
+            pair_blocks(blocks, n, KQ == 5 && multi, &tileset, &second);
+            // pad every block to KQ qubits (identity on the added ones): a block
+            // of a pass pads with qubits of the pass's tile, others with the
+            // lowest qubits; gates in block-local qubits
             const size_t fg0 = fg_used, go0 = go_used;
             std::vector<std::vector<int>> pos(blocks.size());
             ho[go_used++] = 0;
             for (size_t bi = 0; bi < blocks.size(); ++bi) {
                 if (!blocks[bi].wide) {
                     uint64_t q = blocks[bi].qmask;
-                    for (int extra = 0; extra < n && __builtin_popcountll(q) < KQ; ++extra) q |= 1ull << extra;
+                    const uint64_t T = tileset[bi] ? tileset[bi] : (second[bi] ? tileset[bi - 1] : ~0ull);
+                    for (int extra = 0; extra < n && __builtin_popcountll(q) < KQ; ++extra)
+                        if ((T >> extra) & 1) q |= 1ull << extra;
                     for (int i = 0; i < n; ++i)
                         if ((q >> i) & 1) pos[bi].push_back(i);
                     auto loc = [&](int qubit) {
@@ -981,6 +1325,24 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
                     rc = launch_sgate(s, g[blocks[bi].members[0]]);
                     continue;
                 }
+                if constexpr (KQ == 5) {
+                    if (tileset[bi]) {
+                        // blocks bi, bi + 1 in one pass
+                        PassArgs pa{};
+                        pa.m = 2;
+                        for (int i = 0, t = 0; i < n; ++i)
+                            if ((tileset[bi] >> i) & 1) pa.tpos[t++] = i;
+                        for (int j = 0; j < 2; ++j)
+                            for (int i = 0; i < KQ; ++i) pa.pos[j][i] = pos[bi + j][i];
+                        launch_begin(s, KC_FUSED_MULTI, 2.0 * (double)s->bytes, 2 * 3.0 * 2.0 * (double)rows * K * K);
+                        k_fused_multi<<<(unsigned)multi_grid, kMultiThreads, smm, s->stream>>>(
+                            (float *)s->amps, dw + bi * 2 * (size_t)K * K, pa, (rows + kRows - 1) / kRows,
+                            s->dev_status);
+                        rc = launch_end(s, "fused multi-block pass");
+                        ++bi;
+                        continue;
+                    }
+                }
                 ApplyArgs a{};
                 a.nq = KQ;
                 for (int i = 0; i < KQ; ++i) a.pos[i] = pos[bi][i];
@@ -1009,18 +1371,30 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth)
 
 }  // namespace
 
-int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out, int depth)
+int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out, int depth, bool multi,
+                   int64_t *passes_out)
 {
     std::vector<SGate> g;
     lower_gates(gates, n_gates, &g);
     // the same schedule as the run: the first group's blocks at depth <= 2
     const int d = depth > 0 ? depth : kRunDepth;
     BlockPlanner planner(g, k, n, std::min(d, 2));
-    Block b;
-    int64_t nb = 0;
-    while (planner.next(&b))
-        if (++nb == (int64_t)kFirstGroup) planner.set_depth(d);
+    int64_t nb = 0, np = 0;
+    for (size_t grp = 0;; ++grp) {
+        std::vector<Block> blocks;
+        Block b;
+        const size_t want = grp == 0 ? kFirstGroup : kGroupBlocks;
+        while (blocks.size() < want && planner.next(&b)) blocks.push_back(b);
+        if (blocks.empty()) break;
+        if (grp == 0) planner.set_depth(d);
+        std::vector<uint64_t> tileset;
+        std::vector<char> second;
+        pair_blocks(blocks, n, k == 5 && multi, &tileset, &second);
+        nb += (int64_t)blocks.size();
+        for (size_t i = 0; i < blocks.size(); ++i) np += second[i] ? 0 : 1;
+    }
     if (blocks_out) *blocks_out = nb;
+    if (passes_out) *passes_out = np;
     return SIM_OK;
 }
 
@@ -1035,11 +1409,12 @@ int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, co
     std::vector<SGate> g;
     lower_gates(gates, n_gates, &g);
     if (g.empty()) return SIM_OK;
+    const bool multi = (o.flags & SIM_FLAG_MULTI_BLOCK_PASSES) != 0;
     switch (k) {
-    case 3: return run_fused<3>(s, g, kRunDepth);
-    case 4: return run_fused<4>(s, g, kRunDepth);
-    case 5: return run_fused<5>(s, g, kRunDepth);
-    default: return run_fused<6>(s, g, kRunDepth);
+    case 3: return run_fused<3>(s, g, kRunDepth, multi);
+    case 4: return run_fused<4>(s, g, kRunDepth, multi);
+    case 5: return run_fused<5>(s, g, kRunDepth, multi);
+    default: return run_fused<6>(s, g, kRunDepth, multi);
     }
 }
 

@@ -43,6 +43,7 @@ enum KernelClass {
     KC_SAMPLE,       // block sums, scans, shot location, resolution
     KC_BATCH,        // batched persistent circuits
     KC_MLP,          // cost-model forward / backward / Adam
+    KC_FUSED_MULTI,  // several fused blocks applied per pass over the state
     KC_COUNT
 };
 const char *kernel_class_name(int k);
@@ -163,8 +164,11 @@ int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, c
 int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
 int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
 int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out);
-// blocks of the fused plan; depth 0 = the depth the plan runs with
-int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out, int depth = 0);
+// blocks of the fused plan (depth 0 = the depth the plan runs with) and, when
+// passes_out is given, the passes over the state (multi-block passes pair
+// blocks when multi is set)
+int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t *blocks_out, int depth = 0,
+                   bool multi = true, int64_t *passes_out = nullptr);
 // the (cheaper) planner depth the learned plan's features are computed with
 int fused_feature_depth();
 int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,

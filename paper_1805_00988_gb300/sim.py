@@ -167,6 +167,9 @@ def to_sim_gates(gates: np.ndarray) -> np.ndarray:
     return out
 
 
+SIM_FLAG_MULTI_BLOCK_PASSES = 1
+
+
 def plan_opts(plan="per_gate", fuse_k=0, tile_qubits=0, flags=0) -> sim_plan_opts:
     p = PLANS[plan] if isinstance(plan, str) else int(plan)
     return sim_plan_opts(p, fuse_k, tile_qubits, flags)

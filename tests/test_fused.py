@@ -17,10 +17,16 @@ from paper_1805_00988_gb300 import circuits as C
 def test_block_counts_cpu():
     from paper_1805_00988_gb300 import sim
     g = sim.to_sim_gates(C.haar_cz(30, 20, seed=1234))
-    counts = [sim.sim_plan_describe(30, 0, g, sim.plan_opts("fused", fuse_k=k))[0] for k in (3, 4, 5, 6)]
+    desc = {k: sim.sim_plan_describe(30, 0, g, sim.plan_opts("fused", fuse_k=k)) for k in (3, 4, 5, 6)}
+    blocks = [desc[k][1] for k in (3, 4, 5, 6)]
     # larger blocks never need more of them
-    assert counts == sorted(counts, reverse=True)
-    assert counts[-1] < 900
+    assert blocks == sorted(blocks, reverse=True)
+    assert blocks[-1] < 900
+    # one pass per block by default; with multi-block passes k = 5 pairs blocks
+    for k in (3, 4, 5, 6):
+        assert desc[k][0] == desc[k][1]
+    multi = sim.sim_plan_describe(30, 0, g, sim.plan_opts("fused", fuse_k=5, flags=sim.SIM_FLAG_MULTI_BLOCK_PASSES))
+    assert multi[1] == desc[5][1] and multi[0] < multi[1]
 
 
 @pytest.fixture(scope="module")
@@ -145,5 +151,24 @@ def test_fused_wide_gates(gsim, orc, where):
     psi = C.random_state(n, seed=2)
     st.load(psi)
     st.apply(g, plan="fused", fuse_k=3)
+    check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))
+    st.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", [12, 16, 22])
+def test_fused_multi_block_passes(gsim, orc, n):
+    """Pairs of blocks applied to one tile kept in shared memory: the tile's
+    12 qubits hold both blocks' qubits and qubit 0 (loaded with 16-byte async
+    copies); every pair, and the single blocks between them, against the
+    oracle."""
+    g = C.concat([C.haar_cz(n, 8, seed=n), C.random_gates(n, 150, seed=n + 1)])
+    opts = dict(plan="fused", fuse_k=5, flags=gsim.SIM_FLAG_MULTI_BLOCK_PASSES)
+    passes, blocks = gsim.sim_plan_describe(n, 0, gsim.to_sim_gates(g), gsim.plan_opts(**opts))[:2]
+    assert passes < blocks
+    st = gsim.State(n, "c64")
+    psi = C.random_state(n, seed=n + 2)
+    st.load(psi)
+    st.apply(g, **opts)
     check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))
     st.close()
