@@ -28,8 +28,10 @@ namespace qsim {
 
 namespace {
 
+// complex64 tiles of up to 12 qubits hold 16 amplitudes a thread and fit 80
+// registers: three CTAs per SM; 13-qubit and complex128 tiles two
 template <typename R, int M>
-__global__ void __launch_bounds__(kThr, 2)
+__global__ void __launch_bounds__(kThr, (sizeof(R) == 4 && M <= 12 ? 3 : 2))
 k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
                                                    TileGeom geo)
 {
