@@ -21,7 +21,9 @@
  * Ownership and ordering: host arrays passed in are copied before the call
  * returns.  Work is enqueued on the handle's CUDA stream and is asynchronous
  * unless the entry point returns a host value (it then synchronises that
- * stream).  Device pointers passed in stay owned by the caller.
+ * stream).  Device pointers passed in stay owned by the caller.  A handle
+ * (state, batch or cost model) is used by one host thread at a time; distinct
+ * handles may be used from different threads.
  *
  * Errors: every entry point returns a sim_status; nothing throws or aborts
  * across the ABI.  Arguments are validated on the host before any launch.

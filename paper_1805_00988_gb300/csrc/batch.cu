@@ -425,8 +425,11 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
             break;
         }
         // two CTAs per SM (128 registers a thread, 70 KB of shared memory each)
-        cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+        if (cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
+            rc = cuda_fail(cudaGetLastError(), "batch carveout attribute");
+            break;
+        }
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -1219,12 +1219,18 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
             rc = cuda_fail(cudaGetLastError(), "status reset");
             break;
         }
+        // shared-memory limits and carveouts of the kernels this plan launches
+        auto attrs = [](const void *fn, size_t dyn) {
+            return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) == cudaSuccess &&
+                   cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                        (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
+        };
         const size_t smb = (size_t)(1 << KQ) * (1 << KQ) * sizeof(double2);
-        cudaFuncSetAttribute(k_fuse_build<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smb);
         const size_t sma = apply_smem_bytes<KQ>();
-        cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sma);
-        cudaFuncSetAttribute(k_fused_apply<KQ>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             (int)cudaSharedmemCarveoutMaxShared);
+        if (!attrs((const void *)k_fuse_build<KQ>, smb) || !attrs((const void *)k_fused_apply<KQ>, sma)) {
+            rc = cuda_fail(cudaGetLastError(), "fused kernel attributes");
+            break;
+        }
         const uint64_t rows = 1ull << (n - KQ);
         // k <= 5: the persistent streamed kernel, as many CTAs as fit at once
         // (k = 6 does not fit W, a stage ring and A in shared memory)
@@ -1232,9 +1238,10 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
         size_t smp = 0;
         if constexpr (KQ <= 5) {
             smp = stream_smem_bytes<KQ>();
-            cudaFuncSetAttribute(k_fused_stream<KQ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smp);
-            cudaFuncSetAttribute(k_fused_stream<KQ>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
+            if (!attrs((const void *)k_fused_stream<KQ>, smp)) {
+                rc = cuda_fail(cudaGetLastError(), "streamed kernel attributes");
+                break;
+            }
             // CTAs per SM from the kernel's own register and shared-memory
             // footprint; the CTAs never wait on one another, so this only
             // sets the grid
@@ -1254,9 +1261,10 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
         const bool multi = KQ == 5 && n >= 12 && allow_multi;
         if (multi) {
             smm = multi_smem_bytes(kMaxPass);
-            cudaFuncSetAttribute(k_fused_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smm);
-            cudaFuncSetAttribute(k_fused_multi, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared);
+            if (!attrs((const void *)k_fused_multi, smm)) {
+                rc = cuda_fail(cudaGetLastError(), "multi-block kernel attributes");
+                break;
+            }
             const uint64_t tiles = (rows + kRows - 1) / kRows;
             multi_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms);
         }

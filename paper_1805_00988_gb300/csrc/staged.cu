@@ -125,11 +125,9 @@ template <typename R, int M>
 int launch_staged(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &geo, double flops)
 {
     const size_t smem = ((size_t)1 << M) * 2 * sizeof(R) + op_stage_bytes<R>();
-    static bool attr_set = false;   // per template instance
-    if (!attr_set) {
-        QSIM_CUDA(cudaFuncSetAttribute(k_staged<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
+    // set on every launch: the attribute belongs to the current device's
+    // context, and the call costs a microsecond against a multi-ms pass
+    QSIM_CUDA(cudaFuncSetAttribute(k_staged<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const uint64_t tiles = 1ull << (s->n - M);
     launch_begin(s, KC_STAGED, 2.0 * (double)s->bytes, flops);
     k_staged<R, M><<<(unsigned)tiles, kThr, smem, s->stream>>>((R *)s->amps, dops, nops, geo);
