@@ -500,6 +500,40 @@ def run_extras(args, sim, C, dev, model):
             res[plan] = {"ms": ms, "gates_per_s": len(g) / (ms / 1e3)}
         out["qft28_" + dt] = res
         st.close()
+    # one launch per gate kind at 30 qubits (complex64): device time against the
+    # algorithmic bytes of the pairs it must touch (S = state bytes): dense 2S,
+    # CNOT S (control = 1 pairs), Toffoli S/2, CZ S/2 (the |11> quarter, read +
+    # write), SWAP S (the |01>, |10> halves' quarter each, read + write); then a
+    # single-qubit measurement (FP64 sum of one half + collapse pass)
+    n = 30
+    st = sim.State(n, "c64", device=dev)
+    S = (2 ** n) * 8.0
+    peaks, _ = load_peaks()
+    kinds = {"dense_H": (C.gate("h", 17), 2 * S), "cnot": (C.gate("x", 17, controls=(3,)), S),
+             "toffoli": (C.gate("x", 17, controls=(3, 25)), S / 2), "cz": (C.gate("z", 17, controls=(3,)), S / 2),
+             "swap": (C.gate("swap", 17, target2=3), S)}
+    res = {}
+    for name, (gate, alg) in kinds.items():
+        sg = sim.to_sim_gates(gate)
+        o = sim.plan_opts("per_gate")
+
+        def run():
+            for _ in range(4):
+                sim.sim_apply_circuit(st.h, sg, o)
+        run()
+        ms = _timed(run, st.stream, 3) / 4
+        gbs = alg / (ms / 1e3) / 1e9
+        res[name] = {"ms": ms, "alg_GBps": gbs, "frac_of_copy_peak": gbs / peaks["hbm_gbs"]}
+    sim.sim_set_basis_state(st.h, 0)
+    sim.sim_apply_circuit(st.h, sim.to_sim_gates(C.concat([C.gate("h", q) for q in range(n)])), sim.plan_opts("staged"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    m, p = sim.sim_measure(st.h, 11, seed=5, draw=0)
+    torch.cuda.synchronize()
+    res["measure_qubit"] = {"ms_wall": (time.perf_counter() - t0) * 1e3, "outcome": m, "probability": p,
+                            "note": "FP64 sum over the state + collapse pass, host round trip included"}
+    out["gate_kernels_30q_c64"] = res
+    st.close()
     # batched variational circuits: 4096 circuits of 8..20 qubits, 4..12 layers, one graph launch
     ns, offs, bg = C.variational(4096, 8, 20, 4, 12, seed=SEED)
     t0 = time.perf_counter()
