@@ -3,8 +3,10 @@
 //
 // Probabilities are |a_j|^2 (App. B.3).  Every sum of probabilities (norm,
 // the two halves of a single-qubit measurement, <sum Z>, the sampling CDF) is
-// accumulated in FP64 from squares taken in FP64, over a fixed grid and a
-// fixed tree, so results are bit-reproducible run to run.
+// accumulated in FP64 over a fixed grid and a fixed tree, so results are
+// bit-reproducible run to run.  complex128 squares are FP64 FMAs; complex64
+// squares are exact FP32 products summed with compensation in short chunks
+// that are carried into FP64 (see "compensated FP32 sums of squares").
 //
 // Sampling (§2.4: many outcomes from one state without re-running the gates)
 // is an inverse CDF over the FP64 prefix of |a_j|^2 that is never
@@ -116,6 +118,96 @@ __device__ __forceinline__ void acc_sq<float>(double &a, float re, float im)
     a = fma(i, i, a);
 }
 
+// ---------------------------------------------------------------- compensated FP32 sums of squares
+// The FP64 pipe of this GPU runs at about 1/64 of the FP32 rate, so two FP64
+// FMAs per complex64 amplitude make a sum of |a|^2 FP64-bound, at about 2.7x
+// the time it takes to read the state.  The complex64 reductions therefore
+// take their squares and partial sums with error-free FP32 transformations and
+// carry them into FP64 once per 8 amplitudes (16 squares):
+//  * a chunk is rescaled by an exact power of two 2^(127 - k), k the exponent
+//    of its largest component, so that no square overflows or is lost to
+//    underflow (the scaling is undone exactly in the FP64 exponent);
+//  * x^2 = h + l exactly, with h = fl(x * x) and l = fma(x, x, -h) (Dekker's
+//    product, formed with an FMA); h enters the running sum s through Knuth's
+//    TwoSum (s + h = t + err exactly), and err + l accumulate in e: the Dot2
+//    scheme of Ogita, Rump & Oishi (SIAM J. Sci. Comput. 26(6), 2005);
+//  * for m non-negative terms |(s + e) - sum| <= (m + 1)^2 u^2 sum (u = 2^-24,
+//    m = 16: about 1e-12 relative in the worst case, where every rounding
+//    error takes its maximum with the same sign; around 1e-15 in practice);
+//  * s and e widen to FP64 exactly.
+// The __f*_rn intrinsics keep the compiler from contracting a product and a
+// sum into one FMA, which would break the exactness of the transformations.
+struct Sq32 {
+    float s = 0.f, e = 0.f;                  // value = s + e
+    __device__ __forceinline__ void two_sum(float h)
+    {
+        const float t = __fadd_rn(s, h);
+        const float z = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(h, z));
+        s = t;
+        e = __fadd_rn(e, err);
+    }
+    // += x^2
+    __device__ __forceinline__ void add_sq(float x)
+    {
+        const float h = __fmul_rn(x, x);
+        const float l = __fmaf_rn(x, x, -h);
+        const float t = __fadd_rn(s, h);
+        const float z = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(h, z));
+        s = t;
+        e = __fadd_rn(e, __fadd_rn(err, l));
+    }
+    // += x * w (w a small integer; the product is split exactly like a square)
+    __device__ __forceinline__ void add_prod(float x, float w)
+    {
+        const float h = __fmul_rn(x, w);
+        const float l = __fmaf_rn(x, w, -h);
+        two_sum(h);
+        e = __fadd_rn(e, l);
+    }
+};
+
+// Exact power-of-two rescaling of a chunk.  amax = the largest |component|;
+// k = its biased exponent clamped to [1, 253], so 2^(127 - k) is a normal float
+// and the largest scaled component lies in [1, 2) (k = 1 covers zero and
+// subnormal chunks).  Squares of the scaled chunk are the true squares times
+// 2^-sh, with sh = 2 (k - 127).
+struct Pow2 {
+    float scale;
+    int sh;
+};
+__device__ __forceinline__ Pow2 pow2_for(float amax)
+{
+    const int k = min(max((int)(__float_as_uint(amax) >> 23), 1), 253);
+    return {__uint_as_float((uint32_t)(254 - k) << 23), 2 * (k - 127)};
+}
+__device__ __forceinline__ float absmax4(float m, const float4 &v)
+{
+    return fmaxf(fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y))), fmaxf(fabsf(v.z), fabsf(v.w)));
+}
+__device__ __forceinline__ float4 scale4(const float4 &v, float c)
+{
+    return make_float4(__fmul_rn(v.x, c), __fmul_rn(v.y, c), __fmul_rn(v.z, c), __fmul_rn(v.w, c));
+}
+
+// f * 2^sh as an FP64, exactly, by integer operations on the exponent field
+// (|sh| <= 252 and f a partial sum of a rescaled chunk, so the FP64 exponent
+// stays in range); zero and subnormal f give 0.
+__device__ __forceinline__ double widen_pow2(float f, int sh)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xFFu;
+    const int ex = (int)e + 896 + sh;
+    const uint64_t d = ((uint64_t)(u & 0x80000000u) << 32) | ((uint64_t)ex << 52) |
+                       ((uint64_t)(u & 0x007FFFFFu) << 29);
+    return e ? __longlong_as_double((long long)d) : 0.0;
+}
+__device__ __forceinline__ double widen_sum(const Sq32 &a, int sh)
+{
+    return widen_pow2(a.s, sh) + widen_pow2(a.e, sh);
+}
+
 // VEC amplitudes per 16-byte vector: 2 for complex64, 1 for complex128.
 // raw() issues the load only; sq2() turns it into |a|^2 in FP64.  Callers
 // issue a batch of raw loads before any arithmetic so that each thread keeps
@@ -209,6 +301,67 @@ __global__ void __launch_bounds__(kRedThreads) k_masked_sum(const R *__restrict_
     }
 }
 
+// complex64 norm (MODE RED_NORM) and the two halves of qubit q (RED_BIT) with
+// the compensated FP32 sums above: per batch of 8 16-byte vectors (16
+// amplitudes) one power-of-two scale, two carries into FP64 (8 amplitudes
+// each).  The batches, the grid and the FP64 tree are those of k_masked_sum.
+template <int MODE>
+__global__ void __launch_bounds__(kRedThreads) k_sum_sq32(const float *__restrict__ st, uint64_t nvec, uint64_t per,
+                                                          int q, double *__restrict__ partial)
+{
+    static_assert(MODE == RED_NORM || MODE == RED_BIT, "norm or one qubit's halves");
+    __shared__ double sh[2 * kRedThreads / 32];
+    const uint64_t lo = (uint64_t)blockIdx.x * per;
+    const uint64_t hi = min(nvec, lo + per);
+    const float4 *st4 = reinterpret_cast<const float4 *>(st);
+    double a = 0.0, b = 0.0;
+    // the amplitudes of vector v (indices 2v, 2v + 1) go to A (bit q = 0) or B
+    auto add_vec = [&](Sq32 &A, Sq32 &B, uint64_t v, const float4 &y) {
+        if (MODE == RED_NORM) {
+            A.add_sq(y.x); A.add_sq(y.y); A.add_sq(y.z); A.add_sq(y.w);
+        } else {
+            const bool b0 = ((2 * v) >> q) & 1ull, b1 = ((2 * v + 1) >> q) & 1ull;
+            Sq32 c = b0 ? B : A;
+            c.add_sq(y.x); c.add_sq(y.y);
+            if (b0) B = c; else A = c;
+            c = b1 ? B : A;
+            c.add_sq(y.z); c.add_sq(y.w);
+            if (b1) B = c; else A = c;
+        }
+    };
+    uint64_t v = lo + threadIdx.x;
+    for (; v + (uint64_t)(kBatch - 1) * kRedThreads < hi; v += (uint64_t)kBatch * kRedThreads) {
+        float4 x[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) x[u] = st4[v + (uint64_t)u * kRedThreads];
+        float m = 0.f;
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) m = absmax4(m, x[u]);
+        const Pow2 p = pow2_for(m);
+#pragma unroll
+        for (int h = 0; h < kBatch; h += 4) {
+            Sq32 A, B;
+#pragma unroll
+            for (int u = h; u < h + 4; ++u) add_vec(A, B, v + (uint64_t)u * kRedThreads, scale4(x[u], p.scale));
+            a += widen_sum(A, p.sh);
+            if (MODE == RED_BIT) b += widen_sum(B, p.sh);
+        }
+    }
+    for (; v < hi; v += kRedThreads) {
+        const float4 x = st4[v];
+        const Pow2 p = pow2_for(absmax4(0.f, x));
+        Sq32 A, B;
+        add_vec(A, B, v, scale4(x, p.scale));
+        a += widen_sum(A, p.sh);
+        if (MODE == RED_BIT) b += widen_sum(B, p.sh);
+    }
+    block_sum2<kRedThreads>(a, b, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
 // <sum Z> over chunks of 16 consecutive amplitudes (n >= 4): for x = 16 ch +
 // e, popcount(x) = popcount(ch) + popcount(e), so a thread sums the squares of
 // a chunk into five bins by popcount(e) (two FP64 FMAs per amplitude, e known
@@ -252,6 +405,55 @@ __global__ void __launch_bounds__(kRedThreads) k_expz_chunks(const R *__restrict
         const int pc = __popcll(ch);
 #pragma unroll
         for (int j = 0; j < 5; ++j) a = fma(wtab[pc + j], bin[j], a);
+    }
+    block_sum2<kRedThreads>(a, b, sh);
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = a;
+        partial[2 * blockIdx.x + 1] = b;
+    }
+}
+
+// complex64 <sum Z> over chunks of 16 consecutive amplitudes (n >= 4): the
+// same popcount bins as k_expz_chunks, each a compensated FP32 sum of squares
+// of the chunk rescaled by one power of two; the bins are weighted by the
+// integers n - 2 (popcount(ch) + j) with exact FP32 products into one
+// compensated sum, carried into FP64 once per chunk.  Bins hold at most 12
+// squares; the weighted sum cancels, so its error is relative to
+// sum_j |w_j| bin_j <= n * (the chunk's sum of squares).
+__global__ void __launch_bounds__(kRedThreads) k_expz32(const float *__restrict__ st, uint64_t nch, uint64_t per,
+                                                        int n, double *__restrict__ partial)
+{
+    __shared__ double sh[2 * kRedThreads / 32];
+    const uint64_t lo = (uint64_t)blockIdx.x * per;
+    const uint64_t hi = min(nch, lo + per);
+    const float4 *st4 = reinterpret_cast<const float4 *>(st);
+    double a = 0.0, b = 0.0;
+    for (uint64_t ch = lo + threadIdx.x; ch < hi; ch += kRedThreads) {
+        float4 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = st4[ch * 8 + u];
+        float m = 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) m = absmax4(m, x[u]);
+        const Pow2 p = pow2_for(m);
+        Sq32 bin[5];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const float4 y = scale4(x[u], p.scale);
+            bin[__builtin_popcount(2 * u)].add_sq(y.x);
+            bin[__builtin_popcount(2 * u)].add_sq(y.y);
+            bin[__builtin_popcount(2 * u + 1)].add_sq(y.z);
+            bin[__builtin_popcount(2 * u + 1)].add_sq(y.w);
+        }
+        const int pc = __popcll(ch);
+        Sq32 w;
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const float wj = (float)(n - 2 * (pc + j));
+            w.add_prod(bin[j].s, wj);
+            w.e = __fmaf_rn(bin[j].e, wj, w.e);
+        }
+        a += widen_sum(w, p.sh);
     }
     block_sum2<kRedThreads>(a, b, sh);
     if (threadIdx.x == 0) {
@@ -355,10 +557,11 @@ __device__ __forceinline__ double warp_incl_scan(double x, int lane)
 
 // One CTA (8 warps) per block of bs amplitudes.  Groups of 8 lanes own one
 // sub-block each (4 per warp, 32 per CTA): lane g of a group accumulates a
-// contiguous eighth of the sub-block with two FP64 FMAs per amplitude, and a
-// 3-step xor tree inside the group gives the sub-sum.  Warp 0 then scans the
-// block's sub-sums (warp_incl_scan) and the block sum is the scan's last
-// element -- k_resolve repeats that scan bit for bit.
+// contiguous eighth of the sub-block (complex64 full sub-blocks: compensated
+// FP32 squares carried into FP64 every 8 amplitudes; otherwise two FP64 FMAs
+// per amplitude), and a 3-step xor tree inside the group gives the sub-sum.
+// Warp 0 then scans the block's sub-sums (warp_incl_scan) and the block sum is
+// the scan's last element -- k_resolve repeats that scan bit for bit.
 template <typename R>
 __global__ void __launch_bounds__(256) k_sub_sums(const R *__restrict__ st, uint64_t bs, double *__restrict__ sub,
                                                   double *__restrict__ bsum)
@@ -376,17 +579,28 @@ __global__ void __launch_bounds__(256) k_sub_sums(const R *__restrict__ st, uint
         if (gl * per < g.sub) {
             const T *a = reinterpret_cast<const T *>(st) + base + (uint64_t)j * g.sub + (uint64_t)gl * per;
             if (sizeof(R) == 4 && per == 32) {
-                // complex64, full sub-block: 16 aligned 16-byte loads per lane, 8 in flight
+                // complex64, full sub-block: 16 aligned 16-byte loads per lane,
+                // 8 in flight; compensated FP32 squares, one scale per 16
+                // amplitudes, carried into FP64 every 8
                 const float4 *a4 = reinterpret_cast<const float4 *>(a);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float4 x[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) x[u] = a4[h * 8 + u];
+                    float m = 0.f;
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        acc_sq<float>(t, x[u].x, x[u].y);
-                        acc_sq<float>(t, x[u].z, x[u].w);
+                    for (int u = 0; u < 8; ++u) m = absmax4(m, x[u]);
+                    const Pow2 pw = pow2_for(m);
+#pragma unroll
+                    for (int c = 0; c < 8; c += 4) {
+                        Sq32 A;
+#pragma unroll
+                        for (int u = c; u < c + 4; ++u) {
+                            const float4 y = scale4(x[u], pw.scale);
+                            A.add_sq(y.x); A.add_sq(y.y); A.add_sq(y.z); A.add_sq(y.w);
+                        }
+                        t += widen_sum(A, pw.sh);
                     }
                 }
             } else {
@@ -485,6 +699,56 @@ __global__ void k_scatter(uint64_t shots, const uint32_t *__restrict__ shot_blk,
     }
 }
 
+// complex64, full sub-blocks (8 amplitudes per lane): lane `lane`'s part of
+// the in-sub-block search.  The lane's prefix is kept as compensated FP32
+// partial sums of its rescaled squares; its total (FP64) feeds the warp scan
+// that gives the lane's start; the target relative to that start, rescaled by
+// the same power of two and clamped far outside the lane's range, is split
+// into a float pair th + tl that each partial sum is compared with.  An
+// amplitude that is exactly zero leaves the prefix unchanged and is never the
+// first crossing.  first = the first crossing in the lane (-1: none), last_nz =
+// the last amplitude with non-zero probability (-1: none).  All 32 lanes call it.
+__device__ __forceinline__ void lane_locate32(const float *st, uint64_t base, uint32_t j, int lane, double pre,
+                                              double t, int &first, int &last_nz)
+{
+    const float4 *a4 =
+        reinterpret_cast<const float4 *>(st) + (base + (uint64_t)j * (1u << kSubLog) + (uint64_t)lane * 8) / 2;
+    float4 x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) x[u] = a4[u];
+    float m = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) m = absmax4(m, x[u]);
+    const Pow2 pw = pow2_for(m);
+    float cs[8], ce[8];
+    bool nz[8];
+    Sq32 A;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const float4 y = scale4(x[u], pw.scale);
+        A.add_sq(y.x); A.add_sq(y.y);
+        cs[2 * u] = A.s; ce[2 * u] = A.e;
+        nz[2 * u] = x[u].x != 0.f || x[u].y != 0.f;
+        A.add_sq(y.z); A.add_sq(y.w);
+        cs[2 * u + 1] = A.s; ce[2 * u + 1] = A.e;
+        nz[2 * u + 1] = x[u].z != 0.f || x[u].w != 0.f;
+    }
+    const double run = widen_sum(A, pw.sh);
+    const double incl = warp_incl_scan(run, lane);
+    const double start = pre + (incl - run);
+    double T = (t - start) * __longlong_as_double((long long)((uint64_t)(1023 - pw.sh) << 52));
+    T = fmin(fmax(T, -0x1p100), 0x1p100);
+    const float th = __double2float_rn(T);
+    const float tl = __double2float_rn(T - (double)th);
+    first = -1;
+    last_nz = -1;
+#pragma unroll
+    for (int e = 7; e >= 0; --e) {
+        if (nz[e] && __fadd_rn(__fsub_rn(cs[e], th), __fsub_rn(ce[e], tl)) > 0.f) first = e;
+        if (last_nz < 0 && nz[e]) last_nz = e;
+    }
+}
+
 // One CTA per block that received shots.  Warp 0 rebuilds the block's
 // inclusive scan of sub-sums P (the same operations as k_sub_sums); warp w
 // then takes shots w, w + 8, ... of the block: t = u_s * total; the sub-block
@@ -519,21 +783,25 @@ __global__ void __launch_bounds__(256) k_resolve(const R *__restrict__ st, uint6
         const unsigned hit = __ballot_sync(0xffffffffu, (uint32_t)lane < g.nsub && be + P[lane] > t);
         const uint32_t j = hit ? (uint32_t)(__ffs(hit) - 1) : (sub_nz ? (uint32_t)(31 - __clz(sub_nz)) : 0u);
         const double pre = be + (j > 0 ? P[j - 1] : 0.0);
-        double p[8];
-        lane_squares<R>(st, base, g, j, lane, p);
-        double c[8], run = 0.0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-            run += p[e];
-            c[e] = run;
-        }
-        const double incl = warp_incl_scan(run, lane);
-        const double start = pre + (incl - run);
         int first = -1, last_nz = -1;
+        if (sizeof(R) == 4 && g.apl == 8) {
+            lane_locate32(reinterpret_cast<const float *>(st), base, j, lane, pre, t, first, last_nz);
+        } else {
+            double p[8];
+            lane_squares<R>(st, base, g, j, lane, p);
+            double c[8], run = 0.0;
 #pragma unroll
-        for (int e = 7; e >= 0; --e) {
-            if ((uint32_t)e < g.apl && start + c[e] > t) first = e;
-            if (last_nz < 0 && p[e] > 0.0) last_nz = e;
+            for (int e = 0; e < 8; ++e) {
+                run += p[e];
+                c[e] = run;
+            }
+            const double incl = warp_incl_scan(run, lane);
+            const double start = pre + (incl - run);
+#pragma unroll
+            for (int e = 7; e >= 0; --e) {
+                if ((uint32_t)e < g.apl && start + c[e] > t) first = e;
+                if (last_nz < 0 && p[e] > 0.0) last_nz = e;
+            }
         }
         const unsigned fl = __ballot_sync(0xffffffffu, first >= 0);
         uint64_t idx;
@@ -602,9 +870,9 @@ int reduce_sums(qsim_state *s, int mode, int qubit, double out[2])
         else k_masked_sum<double, RED_EXPZ><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
     } else {
         const float *st = (const float *)s->amps;
-        if (mode == RED_NORM) k_masked_sum<float, RED_NORM><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
-        else if (mode == RED_BIT) k_masked_sum<float, RED_BIT><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
-        else if (s->n >= 4) k_expz_chunks<float><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, N / 16, (N / 16 + kRedBlocks - 1) / kRedBlocks, s->n, s->red_partial);
+        if (mode == RED_NORM) k_sum_sq32<RED_NORM><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->red_partial);
+        else if (mode == RED_BIT) k_sum_sq32<RED_BIT><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->red_partial);
+        else if (s->n >= 4) k_expz32<<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, N / 16, (N / 16 + kRedBlocks - 1) / kRedBlocks, s->n, s->red_partial);
         else k_masked_sum<float, RED_EXPZ><<<kRedBlocks, kRedThreads, 0, s->stream>>>(st, nvec, per, qubit, s->n, s->red_partial);
     }
     int rc = launch_end(s, "masked sum");
