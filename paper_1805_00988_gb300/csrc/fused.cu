@@ -18,17 +18,20 @@
 // accumulated in FP32 in tensor memory (3xTF32; Ootomo & Yokota 2022).  U_blk
 // itself is formed in FP64 (k_fuse_build) before the split.
 //
-// Apply kernel: one CTA of 128 threads per 128 rows (MMA M = 128); thread r
-// owns row r: it gathers the row's 2^k amplitudes (coalesced across threads),
-// writes A_hi / A_lo in shared memory in the canonical no-swizzle K-major
-// layout (8-row x 16-byte core matrices), one thread issues the MMAs, the
-// commit arrives on an mbarrier, and each warp reads its 32 TMEM lanes back
-// (tcgen05.ld 32x32b) and scatters the row.  Every wait is bounded; on a
-// timeout the kernel records SIM_ETIMEOUT in a device status word, frees its
-// tensor memory and returns.
+// Apply kernels: persistent, warp-specialised CTAs stream tiles of 128 rows
+// (MMA M = 128) through shared memory with bulk copies; converter warps split
+// each row into A_hi / A_lo (k <= 5: shared memory, canonical no-swizzle
+// K-major layout of 8-row x 16-byte core matrices; k = 6: tensor memory), one
+// thread issues the MMAs against W in shared memory, commits arrive on
+// mbarriers, and consumer warps read the accumulator back (tcgen05.ld 32x32b)
+// and write the rows to HBM.  Every wait is bounded; on a timeout the kernel
+// records SIM_ETIMEOUT in a device status word, frees its tensor memory and
+// returns.
 #include <algorithm>
 #include <cstring>
 #include <vector>
+
+#include <cuda_fp16.h>
 
 #include "internal.cuh"
 
@@ -37,7 +40,6 @@ namespace qsim {
 namespace {
 
 constexpr int kRows = 128;              // MMA M, rows per CTA
-constexpr int kNChunk = 64;             // N columns per MMA sequence
 constexpr unsigned long long kWaitNs = 200000000ull;   // 0.2 s: a tensor-core wait gives up after this
 
 struct FGate {                          // one gate of a block, in block-local qubits
@@ -128,20 +130,6 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
-{
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
 // 32 consecutive columns of the warp's 32 lanes into r[]; the caller issues
 // tmem_wait_ld() before reading r
 __device__ __forceinline__ void tmem_ld32_nowait(uint32_t taddr, uint32_t *r)
@@ -186,18 +174,28 @@ __host__ __device__ __forceinline__ uint32_t kmajor_off(uint32_t row, uint32_t k
     return (((row >> 3) * (K >> 2) + (kk >> 2)) << 7) + ((row & 7) << 4) + ((kk & 3) << 2);
 }
 
+// byte offset of element (row, kk) of a 16-bit K-major no-swizzle operand
+// (core matrices of 8 rows x 8 elements)
+__host__ __device__ __forceinline__ uint32_t kmajor16_off(uint32_t row, uint32_t kk, uint32_t K)
+{
+    return (((row >> 3) * (K >> 3) + (kk >> 3)) << 7) + ((row & 7) << 4) + ((kk & 7) << 1);
+}
+
+// k = 6 runs on FP16 operands scaled by 2^14 (see k_fused_tmem6)
+constexpr float kF16Scale = 16384.0f;
+
 // ------------------------------------------------------------------ FP64 builder
 // One CTA per block: U = G_m ... G_1 applied to the identity column by column
 // in FP64 (the columns are 2^k-amplitude states of the block's qubits), then
 // W (the real form) split into TF32 hi / lo in the B-operand layout:
-// per N-chunk of kNChunk columns, [hi | lo], each chunk N_C x K K-major.
+// [hi | lo], each K x K, K-major.  k = 6: 2^14 W split into FP16 hi / lo
+// (both rounded to nearest) in the 16-bit layout, [hi | lo] again.
 template <int KQ>
 __global__ void __launch_bounds__(256) k_fuse_build(const FGate *__restrict__ gates, const int *__restrict__ goff,
                                                     float *__restrict__ bout)
 {
     constexpr int D = 1 << KQ;
     constexpr int K = 2 * D;
-    constexpr int NC = K < kNChunk ? K : kNChunk;
     extern __shared__ double2 U[];          // U[i * D + c], row i, column c
     const int blk = blockIdx.x;
     for (int e = threadIdx.x; e < D * D; e += 256) U[e] = make_double2((e / D) == (e % D) ? 1.0 : 0.0, 0.0);
@@ -224,13 +222,21 @@ __global__ void __launch_bounds__(256) k_fuse_build(const FGate *__restrict__ ga
         const int i = n >> 1, b = n & 1, j = kk >> 1, a = kk & 1;
         const double2 u = U[i * D + j];
         const double w = (a == b) ? u.x : (a == 1 ? -u.y : u.y);
-        const float hi = tf32_rn((float)w);
-        const float lo = tf32_rn((float)(w - (double)hi));
-        const int ch = n / NC, nl = n % NC;
-        float *chunk = out + (size_t)ch * 2 * NC * K;
-        const uint32_t off = kmajor_off(nl, kk, K) >> 2;
-        chunk[off] = hi;
-        chunk[NC * K + off] = lo;
+        if constexpr (KQ == 6) {
+            __half *o16 = reinterpret_cast<__half *>(out);
+            const double ws = w * (double)kF16Scale;
+            const __half hi = __double2half(ws);
+            const __half lo = __double2half(ws - (double)__half2float(hi));
+            const uint32_t off = kmajor16_off(n, kk, K) >> 1;
+            o16[off] = hi;
+            o16[K * K + off] = lo;
+        } else {
+            const float hi = tf32_rn((float)w);
+            const float lo = tf32_rn((float)(w - (double)hi));
+            const uint32_t off = kmajor_off(n, kk, K) >> 2;
+            out[off] = hi;
+            out[K * K + off] = lo;
+        }
     }
 }
 
@@ -241,130 +247,7 @@ struct ApplyArgs {
     uint64_t rows;      // 2^(n - KQ)
 };
 
-template <int KQ>
-__global__ void __launch_bounds__(kRows, 1) k_fused_apply(float *__restrict__ st, const float *__restrict__ bmat,
-                                                          ApplyArgs a, int *__restrict__ status)
-{
-    constexpr int D = 1 << KQ;
-    constexpr int K = 2 * D;
-    constexpr int NC = K < kNChunk ? K : kNChunk;
-    constexpr int NCH = K / NC;
-    constexpr uint32_t NCOLS = (K < 32) ? 32 : K;              // TMEM columns (power of two >= 32)
-    constexpr uint32_t SBO = (K / 4) * 128;                    // 8-row group stride, bytes
-    constexpr uint32_t IDESC = make_idesc_tf32(kRows, NC);
-
-    extern __shared__ __align__(1024) unsigned char smem[];
-    float *a_hi = reinterpret_cast<float *>(smem);              // kRows x K
-    float *a_lo = a_hi + kRows * K;
-    float *b_s = a_lo + kRows * K;                              // [hi | lo] NC x K each
-    __shared__ uint64_t bar;
-    __shared__ uint32_t tslot;
-    __shared__ uint64_t dep[D];
-    __shared__ int failed;
-
-    const int tid = threadIdx.x, warp = tid >> 5;
-    // a CTA that timed out already: the rest of the launch stops at once
-    if (*reinterpret_cast<volatile int *>(status) != 0) return;
-    if (warp == 0) tmem_alloc(&tslot, NCOLS);
-    if (tid == 0) {
-        mbar_init(&bar, 1);
-        failed = 0;
-    }
-    for (int c = tid; c < D; c += kRows) {
-        uint64_t o = 0;
-        for (int i = 0; i < KQ; ++i)
-            if ((c >> i) & 1) o |= 1ull << a.pos[i];
-        dep[c] = o;
-    }
-    __syncthreads();
-
-    // row tid: base index = global row with zero bits inserted at the block positions
-    const uint64_t R = (uint64_t)blockIdx.x * kRows + tid;
-    uint64_t base = R;
-#pragma unroll
-    for (int i = 0; i < KQ; ++i) {
-        const int p = a.pos[i];
-        base = ((base >> p) << (p + 1)) | (base & ((1ull << p) - 1ull));
-    }
-    const bool live = R < a.rows;
-    // gather the row in batches of independent loads (one batch in flight per thread)
-    constexpr int BATCH = D < 16 ? D : 16;
-#pragma unroll 1
-    for (int c0 = 0; c0 < D; c0 += BATCH) {
-        float2 v[BATCH];
-#pragma unroll
-        for (int u = 0; u < BATCH; ++u)
-            v[u] = live ? *reinterpret_cast<const float2 *>(st + 2 * (base | dep[c0 + u])) : make_float2(0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u < BATCH; ++u) {
-            const float hr = tf32_rn(v[u].x), hi = tf32_rn(v[u].y);
-            const uint32_t off = kmajor_off(tid, 2 * (c0 + u), K);    // (re, im) share one 16-byte row chunk
-            *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_hi) + off) = make_float2(hr, hi);
-            *reinterpret_cast<float2 *>(reinterpret_cast<unsigned char *>(a_lo) + off) =
-                make_float2(tf32_rn(v[u].x - hr), tf32_rn(v[u].y - hi));
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t taddr = tslot;
-
-    for (int ch = 0; ch < NCH; ++ch) {
-        // B chunk: hi and lo, copied as 16-byte vectors
-        const float4 *src = reinterpret_cast<const float4 *>(bmat + (size_t)ch * 2 * NC * K);
-        float4 *dst = reinterpret_cast<float4 *>(b_s);
-        constexpr int NV = 2 * NC * K / 4;                      // float4 per chunk, a multiple of 128
-#pragma unroll 4
-        for (int e = tid; e < NV; e += kRows) dst[e] = __ldg(src + e);
-        fence_async_smem();
-        __syncthreads();
-        if (tid == 0) {
-            tc_fence_after();
-            const uint32_t sa_hi = smem_u32(a_hi), sa_lo = smem_u32(a_lo);
-            const uint32_t sb_hi = smem_u32(b_s), sb_lo = smem_u32(b_s + NC * K);
-            const uint32_t d = taddr + (uint32_t)(ch * NC);
-#pragma unroll 1
-            for (int ks = 0; ks < K / 8; ++ks) {
-                const uint32_t ko = (uint32_t)ks * 256;       // two 16-byte core-matrix columns per K = 8
-                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC, ks > 0);
-                mma_tf32(d, make_desc(sa_hi + ko, 128, SBO), make_desc(sb_lo + ko, 128, SBO), IDESC, 1);
-                mma_tf32(d, make_desc(sa_lo + ko, 128, SBO), make_desc(sb_hi + ko, 128, SBO), IDESC, 1);
-            }
-            mma_commit(&bar);
-        }
-        if (!mbar_wait_bounded(&bar, (uint32_t)(ch & 1))) failed = 1;
-        tc_fence_after();
-        __syncthreads();
-        if (failed) break;
-    }
-
-    if (!failed) {
-        // each warp reads its 32 lanes (= rows 32w .. 32w+31) column block by column block
-        const uint32_t lane_base = taddr + ((uint32_t)(warp * 32) << 16);
-#pragma unroll 1
-        for (int col = 0; col < K; col += 16) {
-            float v[16];
-            tmem_ld16(lane_base + (uint32_t)col, v);
-            if (live) {
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int c = col / 2 + e;
-                    *reinterpret_cast<float2 *>(st + 2 * (base | dep[c])) = make_float2(v[2 * e], v[2 * e + 1]);
-                }
-            }
-        }
-    } else {
-        if (tid == 0) atomicExch(status, SIM_ETIMEOUT);
-        // give MMAs still in flight one more bounded wait before the memory is released
-        mbar_wait_bounded(&bar, 0u);
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(taddr, NCOLS);
-}
-
 // ------------------------------------------------------------------ streamed apply (k <= 5)
-// A persistent, warp-specialised version for blocks whose W fits one N chunk.
 // A tile is 128 rows x 2^k amplitudes: the 2^(k+7) amplitudes that share
 // every index bit outside T = (block qubits) u (the 7 lowest other qubits).
 // Bits 0 .. L-1 of the index all lie in T (L >= 7), so a tile is
@@ -424,7 +307,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
     constexpr int D = 1 << KQ;
     constexpr int K = 2 * D;
     constexpr int N = K;
-    static_assert(N <= kNChunk, "the streamed apply takes W in one N chunk");
+    static_assert(4 * N <= 256, "two accumulators of 2N columns in half of tensor memory");
     constexpr int TB = KQ + 7;                       // tile bits
     constexpr int TAMP = 1 << TB;                    // amplitudes per tile = kRows * D
     constexpr uint32_t TBYTES = (uint32_t)TAMP * 8u;
@@ -688,6 +571,343 @@ size_t stream_smem_bytes()
     return (size_t)StreamCfg<KQ>::S * ((size_t)kRows << KQ) * 8 +
            (size_t)(2 * StreamCfg<KQ>::AB * kRows * K + 2 * K * K) * sizeof(float);
 }
+
+// ------------------------------------------------------------------ k = 6: FP16 split, A in tensor memory
+// For k = 6 (K = N = 128) the tensor work per amplitude doubles and 3xTF32
+// operands do not fit next to a stage ring (W hi | lo alone is 128 KB), so
+// this kernel splits into FP16 instead: x = x_hi + x_lo with both parts FP16
+// rounded to nearest, after scaling the state by 2^14 and W by 2^14 (exact
+// powers of two).  An FP16 part carries 11 significant bits like a TF32 part,
+// so hi + lo keeps 22 bits as in 3xTF32, and kind::f16 runs at twice the rate
+// of kind::tf32.  The scaling keeps normalised amplitudes (|a| <= 1) below the
+// FP16 maximum and the parts of typical amplitudes (|a| ~ 2^-15 at 30 qubits)
+// in the normal range; an amplitude below 2^-28 loses relative precision but
+// keeps an absolute error below 2^-38.  A converter that meets |a| >= 2 records
+// SIM_EUNSUPPORTED (the result of that call is not usable).
+// D = A_lo W_hi + A_hi W_lo + A_hi W_hi is accumulated in FP32 in tensor
+// memory, the two small products first over all K-steps: the tensor core's
+// accumulation truncates, and adding the small products before the
+// accumulator is large keeps their share of that bias negligible.  The
+// consumer multiplies by 2^-28.
+// Tensor memory: A buffers of 128 columns (FP16 pairs: A_hi in the first 64,
+// A_lo in the next 64) at [0, 128) and [128, 256), accumulators at [256, 384)
+// and [384, 512).  Shared memory: two 64 KB stages and W (hi | lo, 32 KB each).
+// Roles (320 threads), tile i uses stage, A buffer and accumulator i mod 2:
+//   warp 9: the stage <- tile i (bulk copies of the runs of T) once the
+//       converters have read tile i - 2 out of it;
+//   warps 0-3: row r of the stage -> registers -> scaled FP16 hi / lo ->
+//       TMEM lane r of A buffer i mod 2, once the MMAs of tile i - 2 are done;
+//   warp 8 (one thread): the 24 MMAs of tile i once A is written and the
+//       accumulator has been drained (tile i - 2);
+//   warps 4-7: accumulator -> 2^-28 x -> HBM.
+// Every wait is bounded as in k_fused_stream.
+constexpr int kT6Threads = 320;
+
+__host__ __device__ constexpr uint32_t make_idesc_f16(int M, int N)
+{
+    return (1u << 4)                        // D format F32
+           | (0u << 7)                      // A format F16
+           | (0u << 10)                     // B format F16
+           | ((uint32_t)(N >> 3) << 17)     // N / 8
+           | ((uint32_t)(M >> 4) << 24);    // M / 16   (A, B K-major; no negate, no sparsity)
+}
+
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+// r[0..31] -> 32 consecutive columns of the warp's 32 lanes
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t *r)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kT6Threads, 1)
+    k_fused_tmem6(float *__restrict__ st, const __half *__restrict__ bmat, ApplyArgs a, uint64_t ntiles,
+                  int *__restrict__ status)
+{
+    constexpr int KQ = 6;
+    constexpr int D = 1 << KQ;
+    constexpr int K = 2 * D;
+    constexpr int TB = KQ + 7;                       // tile bits
+    constexpr int TAMP = 1 << TB;                    // amplitudes per tile
+    constexpr uint32_t TBYTES = (uint32_t)TAMP * 8u;
+    constexpr uint32_t NCOLS = 512;
+    constexpr uint32_t COL_A = 0, COL_D = 256;       // + 128 per buffer
+    constexpr uint32_t SBO = (K / 8) * 128;          // 8-row group stride of W, bytes
+    constexpr uint32_t WLO = (uint32_t)K * K * 2u;   // byte offset of W_lo
+    constexpr uint32_t IDESC = make_idesc_f16(kRows, K);
+    constexpr float kUnscale = 1.0f / (kF16Scale * kF16Scale);
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float2 *stage = reinterpret_cast<float2 *>(smem);                    // 2 x TAMP amplitudes
+    __half *wsm = reinterpret_cast<__half *>(smem + 2 * (size_t)TBYTES); // [hi | lo] K x K each
+    __shared__ uint64_t bar_full[2], bar_empty[2], bar_a[2], bar_d[2], bar_e[2];
+    __shared__ uint32_t tslot;
+    __shared__ int tpos[TB];          // global bit of tile-local bit j (ascending)
+    __shared__ uint64_t pmask;        // block bits
+    __shared__ int lrun;              // L: tile-local bits 0 .. L-1 are global bits 0 .. L-1
+    __shared__ uint32_t uc[D];        // tile-local offset of column c
+    __shared__ uint64_t gc[D];        // global offset of column c
+    __shared__ int failed, too_large;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        failed = *reinterpret_cast<volatile int *>(status);
+        too_large = 0;
+        uint64_t pm = 0;
+        for (int i = 0; i < KQ; ++i) pm |= 1ull << a.pos[i];
+        uint64_t tm = pm;
+        for (int b = 0, cnt = 0; cnt < 7; ++b)
+            if (!((pm >> b) & 1)) { tm |= 1ull << b; ++cnt; }
+        for (int b = 0, j = 0; j < TB; ++b)
+            if ((tm >> b) & 1) tpos[j++] = b;
+        int L = 0;
+        while (L < TB && tpos[L] == L) ++L;
+        lrun = L;
+        pmask = pm;
+    }
+    __syncthreads();
+    if (failed) return;
+    if (warp == 0) tmem_alloc(&tslot, NCOLS);
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_full[b], 1);
+            mbar_init(&bar_empty[b], kRows);
+            mbar_init(&bar_a[b], kRows);
+            mbar_init(&bar_d[b], 1);
+            mbar_init(&bar_e[b], kRows);
+        }
+    }
+    for (int c = tid; c < D; c += kT6Threads) {
+        uint32_t u = 0;
+        uint64_t g = 0;
+        for (int i = 0; i < KQ; ++i)
+            if ((c >> i) & 1) {
+                g |= 1ull << a.pos[i];
+                for (int j = 0; j < TB; ++j)
+                    if (tpos[j] == a.pos[i]) u |= 1u << j;
+            }
+        uc[c] = u;
+        gc[c] = g;
+    }
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(bmat);
+        float4 *dst = reinterpret_cast<float4 *>(wsm);
+        for (int e = tid; e < 2 * K * K * 2 / 16; e += kT6Threads) dst[e] = __ldg(src + e);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = tslot;
+    volatile int *vfailed = &failed;
+    const uint64_t step = gridDim.x;
+    const int iters = ((uint64_t)blockIdx.x < ntiles) ? (int)((ntiles - 1 - blockIdx.x) / step + 1) : 0;
+
+    auto tile_base = [&](uint64_t t) {
+        uint64_t b = t;
+#pragma unroll
+        for (int j = 0; j < TB; ++j) {
+            const int p = tpos[j];
+            b = ((b >> p) << (p + 1)) | (b & ((1ull << p) - 1ull));
+        }
+        return b;
+    };
+    auto row_offsets = [&](int r, uint32_t &u, uint64_t &g) {
+        u = 0;
+        g = 0;
+        const uint64_t pm = pmask;
+        for (int j = 0, i = 0; j < TB; ++j) {
+            const int p = tpos[j];
+            if ((pm >> p) & 1) continue;
+            if ((r >> i) & 1) {
+                u |= 1u << j;
+                g |= 1ull << p;
+            }
+            ++i;
+        }
+    };
+
+    if (warp == 9) {
+        // loader warp: lane j copies runs j, j + 32 of every tile (T holds
+        // qubits 0..6, so L >= 7 and there are at most 2^(TB - 7) = 64 runs)
+        const int L = lrun;
+        const int nrun = 1 << (TB - L);
+        const uint32_t rbytes = 8u << L;
+        int issued = 0;
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int s = i & 1;
+            if (i >= 2 && !mbar_wait_bounded(&bar_empty[s], (uint32_t)(((i - 2) >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step);
+            if (lane == 0) mbar_arrive_expect_tx(&bar_full[s], TBYTES);
+            __syncwarp();
+            for (int rr = lane; rr < nrun; rr += 32) {
+                uint64_t go = 0;
+                for (int b = 0; b < TB - L; ++b)
+                    if ((rr >> b) & 1) go |= 1ull << tpos[L + b];
+                bulk_load(stage + (size_t)s * TAMP + ((size_t)rr << L), st + 2 * (base | go), rbytes, &bar_full[s]);
+            }
+            issued = i + 1;
+        }
+        // copies still in flight land before the CTA may exit
+        if (lane == 0)
+            for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
+                mbar_wait_bounded(&bar_full[i & 1], (uint32_t)((i >> 1) & 1));
+    } else if (warp < 4) {
+        uint32_t ur;
+        uint64_t gr;
+        row_offsets(tid, ur, gr);
+        // bank spreading as in k_fused_stream: thread r reads column c ^ x,
+        // then puts its registers back in column order by conditional swaps
+        // (x < 16, so a half row of 32 columns maps onto itself)
+        int zc = 0;
+        for (int j = 0; j < 4; ++j) zc += (int)((pmask >> tpos[j]) & 1);
+        const int x = (tid >> (4 - zc)) & ((1 << zc) - 1);
+        const uint32_t ux = uc[x];
+        const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
+        float amax = 0.f;
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int s = i & 1, b = i & 1;
+            if (!mbar_wait_bounded(&bar_full[s], (uint32_t)((i >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            // A buffer b: the MMAs of tile i - 2 must be done reading it
+            if (i >= 2 && !mbar_wait_bounded(&bar_d[b], (uint32_t)(((i - 2) >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            tc_fence_after();
+            const float2 *sg = stage + (size_t)s * TAMP;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                float2 v[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = sg[(ur | uc[32 * h + j]) ^ ux];
+                if (h == 1) mbar_arrive(&bar_empty[s]);
+                if (zc > 0) {
+#pragma unroll
+                    for (int bb = 0; bb < 4; ++bb) {
+                        if (bb < zc) {
+                            const bool f = (x >> bb) & 1;
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (!((j >> bb) & 1)) {
+                                    const float2 t0 = v[j], t1 = v[j | (1 << bb)];
+                                    v[j] = f ? t1 : t0;
+                                    v[j | (1 << bb)] = f ? t0 : t1;
+                                }
+                        }
+                    }
+                }
+                // complex column j = K-elements 2j (re), 2j + 1 (im) = one 32-bit TMEM column
+                uint32_t rh[32], rl[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    amax = fmaxf(amax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
+                    const float xr = v[j].x * kF16Scale, xi = v[j].y * kF16Scale;
+                    const __half2 hh = __floats2half2_rn(xr, xi);
+                    const float2 hf = __half22float2(hh);
+                    const __half2 hl = __floats2half2_rn(xr - hf.x, xi - hf.y);
+                    rh[j] = *reinterpret_cast<const uint32_t *>(&hh);
+                    rl[j] = *reinterpret_cast<const uint32_t *>(&hl);
+                }
+                const uint32_t ab = tl + COL_A + 128u * (uint32_t)b + 32u * (uint32_t)h;
+                tmem_st32(ab, rh);
+                tmem_st32(ab + 64u, rl);
+                tmem_wait_st();
+            }
+            tc_fence_before();
+            mbar_arrive(&bar_a[b]);
+        }
+        if (amax >= 2.0f) too_large = 1;
+    } else if (warp < 8) {
+        // consumers: warp w reads TMEM lanes 32 (w - 4) .. + 31 = rows of the tile
+        const int r = tid - 128;
+        uint32_t ur;
+        uint64_t gr;
+        row_offsets(r, ur, gr);
+        const bool q0_in_block = (pmask & 1ull) != 0;
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int b = i & 1;
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
+            if (!mbar_wait_bounded(&bar_d[b], (uint32_t)((i >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t lane_base = taddr + COL_D + 128u * (uint32_t)b + ((uint32_t)((warp - 4) * 32) << 16);
+#pragma unroll
+            for (int col = 0; col < K; col += 32) {
+                uint32_t d[32];
+                tmem_ld32_nowait(lane_base + (uint32_t)col, d);
+                tmem_wait_ld();
+                float v[32];
+#pragma unroll
+                for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(d[e]) * kUnscale;
+                if (q0_in_block) {
+#pragma unroll
+                    for (int e = 0; e < 16; e += 2)
+                        *reinterpret_cast<float4 *>(st + 2 * (base | gc[col / 2 + e])) =
+                            make_float4(v[2 * e], v[2 * e + 1], v[2 * e + 2], v[2 * e + 3]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e)
+                        *reinterpret_cast<float2 *>(st + 2 * (base | gc[col / 2 + e])) =
+                            make_float2(v[2 * e], v[2 * e + 1]);
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(&bar_e[b]);
+        }
+    } else if (warp == 8 && lane == 0) {
+        // issuer (one thread): per tile 8 K-steps x (A_lo W_hi), then A_hi W_lo, then A_hi W_hi
+        const uint32_t sw = smem_u32(wsm);
+        int nd = 0;                   // commits issued
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int b = i & 1;
+            if (!mbar_wait_bounded(&bar_a[b], (uint32_t)((i >> 1) & 1))) { *vfailed = 1; break; }
+            if (i >= 2 && !mbar_wait_bounded(&bar_e[b], (uint32_t)(((i - 2) >> 1) & 1))) { *vfailed = 1; break; }
+            tc_fence_after();
+            const uint32_t d = taddr + COL_D + 128u * (uint32_t)b;
+            const uint32_t ahi = taddr + COL_A + 128u * (uint32_t)b, alo = ahi + 64u;
+#pragma unroll 1
+            for (int pass = 0; pass < 3; ++pass) {
+                const uint32_t ac = pass == 0 ? alo : ahi;
+                const uint32_t bw = sw + (pass == 1 ? WLO : 0u);
+#pragma unroll 1
+                for (int ks = 0; ks < K / 16; ++ks)
+                    mma_f16_ta(d, ac + 8u * (uint32_t)ks, make_desc(bw + (uint32_t)ks * 256u, 128, SBO), IDESC,
+                               (pass | ks) != 0);
+            }
+            mma_commit(&bar_d[b]);
+            nd = i + 1;
+        }
+        // tensor-core work still in flight finishes before tensor memory is freed
+        if (*vfailed && nd > 0) mbar_wait_bounded(&bar_d[(nd - 1) & 1], (uint32_t)(((nd - 1) >> 1) & 1));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (*vfailed) atomicExch(status, SIM_ETIMEOUT);
+        else if (too_large) atomicCAS(status, 0, SIM_EUNSUPPORTED);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, NCOLS);
+}
+
+constexpr size_t tmem6_smem_bytes() { return 2 * ((size_t)kRows << 6) * 8 + (size_t)2 * 128 * 128 * sizeof(__half); }
 
 // ------------------------------------------------------------------ multi-block passes (k = 5)
 // Several consecutive blocks whose qubits fit one 12-qubit tile set T are
@@ -992,14 +1212,6 @@ size_t multi_smem_bytes(int m)
            (size_t)m * 2 * K * K * sizeof(float);
 }
 
-template <int KQ>
-size_t apply_smem_bytes()
-{
-    constexpr int K = 2 << KQ;
-    constexpr int NC = K < kNChunk ? K : kNChunk;
-    return (size_t)(2 * kRows * K + 2 * NC * K) * sizeof(float);
-}
-
 // ------------------------------------------------------------------ host planner
 struct Block {
     uint64_t qmask;
@@ -1226,8 +1438,7 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
                                         (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
         };
         const size_t smb = (size_t)(1 << KQ) * (1 << KQ) * sizeof(double2);
-        const size_t sma = apply_smem_bytes<KQ>();
-        if (!attrs((const void *)k_fuse_build<KQ>, smb) || !attrs((const void *)k_fused_apply<KQ>, sma)) {
+        if (!attrs((const void *)k_fuse_build<KQ>, smb)) {
             rc = cuda_fail(cudaGetLastError(), "fused kernel attributes");
             break;
         }
@@ -1254,6 +1465,19 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
             per_sm = std::min(per_sm, 512 / cols);
             const uint64_t tiles = (rows + kRows - 1) / kRows;
             pipe_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms * per_sm);
+        } else {
+            // k = 6: one CTA per SM (all of tensor memory, 192 KB of shared memory)
+            smp = tmem6_smem_bytes();
+            if (!attrs((const void *)k_fused_tmem6, smp)) {
+                rc = cuda_fail(cudaGetLastError(), "k = 6 kernel attributes");
+                break;
+            }
+            if (resident_ctas(s->device, (const void *)k_fused_tmem6, kT6Threads, smp) < 1) {
+                rc = fail(SIM_ECUDA, "fused apply: the k = 6 kernel does not fit on an SM");
+                break;
+            }
+            const uint64_t tiles = (rows + kRows - 1) / kRows;
+            pipe_grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms);
         }
         // the first group is planned at depth <= 2 (its planning time is exposed)
         int multi_grid = 0;
@@ -1362,8 +1586,9 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
                     k_fused_stream<KQ><<<(unsigned)pipe_grid, kStreamThreads, smp, s->stream>>>(
                         (float *)s->amps, bm, a, (rows + kRows - 1) / kRows, s->dev_status);
                 } else {
-                    k_fused_apply<KQ><<<(unsigned)((rows + kRows - 1) / kRows), kRows, sma, s->stream>>>(
-                        (float *)s->amps, bm, a, s->dev_status);
+                    k_fused_tmem6<<<(unsigned)pipe_grid, kT6Threads, smp, s->stream>>>(
+                        (float *)s->amps, reinterpret_cast<const __half *>(bm), a, (rows + kRows - 1) / kRows,
+                        s->dev_status);
                 }
                 rc = launch_end(s, "fused apply");
             }
@@ -1373,7 +1598,10 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
     int hstatus = 0;
     QSIM_CUDA(cudaMemcpyAsync(&hstatus, s->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     QSIM_CUDA(cudaStreamSynchronize(s->stream));
-    if (rc == SIM_OK && hstatus != 0) rc = fail(SIM_ETIMEOUT, "fused apply: a tensor-core wait gave up");
+    if (rc == SIM_OK && hstatus == SIM_EUNSUPPORTED)
+        rc = fail(SIM_EUNSUPPORTED, "fused apply, k = 6: an amplitude has |a| >= 2 (the FP16 split needs a normalised state)");
+    else if (rc == SIM_OK && hstatus != 0)
+        rc = fail(SIM_ETIMEOUT, "fused apply: a tensor-core wait gave up");
     return rc;
 }
 
