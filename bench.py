@@ -52,12 +52,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # captures stay at a few GB on the device) and the traffic of a launch grows
 # with the state, so it is scaled by 2^n.
 TRAFFIC = {
-    # k_fused_stream<5>, 27 qubits: dram__bytes_read.sum 1.073867 GB + dram__bytes_write.sum 1.012783 GB
-    "fused": {"bytes_per_amp": (1.073867e9 + 1.012783e9) / 2 ** 27,
-              "source": "paper_1805_00988_gb300/csrc/fused.cu",
-              "until": "template <int KQ>\nsize_t stream_smem_bytes()",
-              "sha256": "1aeffcf38407989e360c1daddafb5ef4bc4526d40d61b5907cd8f0cc757b1b6f",
-              "profile": "profiles/k_fused_stream5_27q.md"},
+    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073968 GB + dram__bytes_write.sum 1.012258 GB
+    "fused_f16": {"bytes_per_amp": (1.073968e9 + 1.012258e9) / 2 ** 27,
+                  "source": "paper_1805_00988_gb300/csrc/fused.cu",
+                  "until": "// ------------------------------------------------------------------ multi-block passes",
+                  "sha256": "c7c6bb6910e41b5af6fe2a00fa56a78dfe8c64c29dfc91f14047c41a5836c4ae",
+                  "profile": "profiles/k_fused_tmem6_27q.md"},
 }
 
 
@@ -85,7 +85,7 @@ def traffic_for(kind: str, n: int):
     of the kernels; the host planner after it does not change the traffic)."""
     import hashlib
     t = TRAFFIC.get(kind)
-    if not t or t["bytes_per_amp"] is None:
+    if not t or t["bytes_per_amp"] is None or t["sha256"] is None:
         return None, None
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
     with open(path, "r") as f:
@@ -334,6 +334,10 @@ def run_ours(args, rank, world, local_rank):
         # nominal TF32 / bf16 dense ratio (1.1 / 2.25 PFLOP/s)
         cpeak = peaks.get("bf16_tflops_sustained", 1700.0) * (1.1 / 2.25)
         cbound, csrc = "tensor", "MEASURED_PEAKS.json bf16_tflops_sustained x (1.1 / 2.25) nominal TF32/bf16"
+    elif dname == "fused_f16":
+        # tensor-core FP16 work (kind::f16): the dense FP16 rate is the bf16 rate
+        cpeak = peaks.get("bf16_tflops_sustained", 1700.0)
+        cbound, csrc = "tensor", "MEASURED_PEAKS.json bf16_tflops_sustained (FP16 dense = bf16 dense rate)"
     else:
         cpeak = FP32_PEAK_TFLOPS
         cbound, csrc = "alu", "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz"

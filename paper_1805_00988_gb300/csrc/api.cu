@@ -35,7 +35,7 @@ const char *kernel_class_name(int k)
 {
     static const char *names[KC_COUNT] = {"init", "dense", "diag", "perm", "swap", "staged", "fused",
                                           "fuse_build", "prob", "reduce", "collapse", "sample", "batch", "mlp",
-                                          "fused_multi"};
+                                          "fused_multi", "fused_f16"};
     return (k >= 0 && k < KC_COUNT) ? names[k] : "?";
 }
 

@@ -1579,8 +1579,9 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
                 a.nq = KQ;
                 for (int i = 0; i < KQ; ++i) a.pos[i] = pos[bi][i];
                 a.rows = rows;
-                // tensor-core flops: three real GEMMs [rows x K] x [K x K] (3xTF32)
-                launch_begin(s, KC_FUSED, 2.0 * (double)s->bytes, 3.0 * 2.0 * (double)rows * K * K);
+                // tensor-core flops: three real GEMMs [rows x K] x [K x K] (3xTF32; k = 6: FP16 split)
+                launch_begin(s, KQ <= 5 ? KC_FUSED : KC_FUSED_F16, 2.0 * (double)s->bytes,
+                             3.0 * 2.0 * (double)rows * K * K);
                 const float *bm = dw + bi * 2 * (size_t)K * K;
                 if constexpr (KQ <= 5) {
                     k_fused_stream<KQ><<<(unsigned)pipe_grid, kStreamThreads, smp, s->stream>>>(

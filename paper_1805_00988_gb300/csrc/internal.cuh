@@ -44,6 +44,7 @@ enum KernelClass {
     KC_BATCH,        // batched persistent circuits
     KC_MLP,          // cost-model forward / backward / Adam
     KC_FUSED_MULTI,  // several fused blocks applied per pass over the state
+    KC_FUSED_F16,    // fused 6-qubit unitary apply on FP16-split operands
     KC_COUNT
 };
 const char *kernel_class_name(int k);

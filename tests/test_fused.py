@@ -1,6 +1,7 @@
 """The fused plan: gates grouped into blocks of at most k qubits, each block's
-2^k x 2^k unitary formed in FP64 on the GPU and applied with TF32-split
-tensor-core GEMMs (complex64 states).
+2^k x 2^k unitary formed in FP64 on the GPU and applied with split-precision
+tensor-core GEMMs (complex64 states): 3xTF32 for k <= 5, FP16 hi / lo parts
+of 2^14-scaled operands for k = 6 (the same 22 significant bits).
 
 Tolerance: infidelity <= 1e-6 (the bound the fused path is held to).
 Element-wise: 3xTF32 keeps the low parts of both operands with 11 mantissa
@@ -111,12 +112,33 @@ def test_fused_rejects_c128_and_small(gsim):
 
 
 @pytest.mark.gpu
-def test_fused_haar_cz_30q_vs_c128(gsim):
+def test_fused_k6_scaled_states(gsim, orc):
+    """k = 6 splits 2^14-scaled amplitudes into FP16 parts: a state with
+    |a| < 2 is applied exactly like any other (the apply is linear), one with
+    |a| >= 2 is refused with SIM_EUNSUPPORTED instead of overflowing."""
+    n = 14
+    g = C.haar_cz(n, 3, seed=8)
+    st = gsim.State(n, "c64")
+    st.tensor.mul_(1.5)
+    st.apply(g, plan="fused", fuse_k=6)
+    check(orc, st.state().astype(np.complex128) / 1.5, orc.apply_circuit(orc.basis_state(n, 0), g))
+    st.close()
+    st = gsim.State(n, "c64")
+    st.tensor.mul_(4.0)
+    with pytest.raises(gsim.SimError) as e:
+        st.apply(g, plan="fused", fuse_k=6)
+    assert e.value.status == gsim.SIM_EUNSUPPORTED
+    st.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [5, 6])
+def test_fused_haar_cz_30q_vs_c128(gsim, k):
     import torch
     n = 30
     g = C.haar_cz(n, 20, seed=1234)
     a = gsim.State(n, "c64")
-    a.apply(g, plan="fused", fuse_k=5)
+    a.apply(g, plan="fused", fuse_k=k)
     b = gsim.State(n, "c128")
     b.apply(g, plan="staged")
     ip = torch.zeros((), dtype=torch.complex128, device="cuda")
