@@ -88,7 +88,10 @@ typedef enum {
 
 typedef struct sim_plan_opts {
     int32_t plan;            /* sim_plan_kind */
-    int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block, 3..6 (0 = 5) */
+    int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block, 3..6 (0 = 5); k <= 5 runs
+                                3xTF32, k = 6 an FP16 hi / lo split of 2^14-scaled operands (same 22
+                                significant bits), which needs |a_j| < 2 for every amplitude (every
+                                normalised state): SIM_EUNSUPPORTED otherwise */
     int32_t tile_qubits;     /* SIM_PLAN_STAGED: tile size log2 (0 = default) */
     int32_t flags;           /* SIM_FLAG_* bits, 0 = defaults */
 } sim_plan_opts;
@@ -129,14 +132,20 @@ int sim_copy_state(sim_t s, void *dst, int dst_is_host);
  *   updated (§2.3, App. B.2).  SIM_EINVAL if a qubit is out of range, a
  *   control equals the target or two controls are equal.
  * sim_apply_circuit: apply n_gates gates in order, scheduled by opts (NULL =
- *   SIM_PLAN_PER_GATE).  The whole list is validated before anything runs. */
+ *   SIM_PLAN_PER_GATE).  The whole list is validated before anything runs.
+ *   SIM_PLAN_FUSED with k = 6 checks |a_j| < 2 while it runs: a call that
+ *   meets a larger amplitude returns SIM_EUNSUPPORTED and leaves the state
+ *   unusable (reload it). */
 int sim_apply_gate(sim_t s, const double U[8], int target, const int *controls, int n_controls);
 int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts);
 
 /* ---- measurement ------------------------------------------------------------
  * sim_probabilities: p_j = |a_j|^2 for all j (App. B.3) into dev_out, a device
  *   array of 2^n floats (out_real = SIM_F32) or doubles (SIM_F64).
- * sim_norm: sum_j |a_j|^2 accumulated in FP64 (squares taken in FP64).
+ * sim_norm: sum_j |a_j|^2 accumulated in FP64 (complex128: squares in FP64;
+ *   complex64: exact FP32 squares summed with compensation in chunks of 8
+ *   amplitudes, each carried into FP64; within about 1e-12 relative of the
+ *   exact sum).
  * sim_measure: measure one qubit in the computational basis (§1.3.3):
  *   p0, p1 summed in FP64; outcome 0 iff p0 > u (p0 + p1) with
  *   u = (splitmix64(seed + draw) >> 11) * 2^-53 (SplitMix64, Steele et al.
