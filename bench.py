@@ -52,11 +52,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # captures stay at a few GB on the device) and the traffic of a launch grows
 # with the state, so it is scaled by 2^n.
 TRAFFIC = {
-    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073968 GB + dram__bytes_write.sum 1.012258 GB
-    "fused_f16": {"bytes_per_amp": (1.073968e9 + 1.012258e9) / 2 ** 27,
+    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073933 GB + dram__bytes_write.sum 1.012051 GB
+    "fused_f16": {"bytes_per_amp": (1.073933e9 + 1.012051e9) / 2 ** 27,
                   "source": "paper_1805_00988_gb300/csrc/fused.cu",
                   "until": "// ------------------------------------------------------------------ multi-block passes",
-                  "sha256": "c7c6bb6910e41b5af6fe2a00fa56a78dfe8c64c29dfc91f14047c41a5836c4ae",
+                  "sha256": "e1a6f382b0ff0372b0b7a5c134530a28edc1b8d252ebb2163a71ecaa00ff87f9",
                   "profile": "profiles/k_fused_tmem6_27q.md"},
 }
 

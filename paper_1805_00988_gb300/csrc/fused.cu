@@ -185,42 +185,51 @@ __host__ __device__ __forceinline__ uint32_t kmajor16_off(uint32_t row, uint32_t
 constexpr float kF16Scale = 16384.0f;
 
 // ------------------------------------------------------------------ FP64 builder
-// One CTA per block: U = G_m ... G_1 applied to the identity column by column
-// in FP64 (the columns are 2^k-amplitude states of the block's qubits), then
-// W (the real form) split into TF32 hi / lo in the B-operand layout:
-// [hi | lo], each K x K, K-major.  k = 6: 2^14 W split into FP16 hi / lo
-// (both rounded to nearest) in the 16-bit layout, [hi | lo] again.
+// U = G_m ... G_1 applied to the identity column by column in FP64 (the
+// columns are 2^k-amplitude states of the block's qubits and evolve
+// independently), then W (the real form) split into TF32 hi / lo in the
+// B-operand layout: [hi | lo], each K x K, K-major.  k = 6: 2^14 W split into
+// FP16 hi / lo (both rounded to nearest) in the 16-bit layout, [hi | lo] again.
+// Each block's columns are spread over kBuildSplit<KQ> CTAs of 8 columns
+// (this GPU's FP64 pipe is narrow: one CTA per block left the build
+// FP64-bound on a handful of SMs); CTA (block, part) writes the W entries of
+// its input columns, kk in [2 c0, 2 c0 + 2 DC), for every output n.
+template <int KQ>
+constexpr int kBuildSplit = (1 << KQ) >= 8 ? (1 << KQ) / 8 : 1;
+
 template <int KQ>
 __global__ void __launch_bounds__(256) k_fuse_build(const FGate *__restrict__ gates, const int *__restrict__ goff,
                                                     float *__restrict__ bout)
 {
     constexpr int D = 1 << KQ;
     constexpr int K = 2 * D;
-    extern __shared__ double2 U[];          // U[i * D + c], row i, column c
-    const int blk = blockIdx.x;
-    for (int e = threadIdx.x; e < D * D; e += 256) U[e] = make_double2((e / D) == (e % D) ? 1.0 : 0.0, 0.0);
+    constexpr int CS = kBuildSplit<KQ>;
+    constexpr int DC = D / CS;               // columns of this CTA
+    extern __shared__ double2 U[];          // U[i * DC + c], row i, local column c
+    const int blk = blockIdx.x / CS, c0 = (blockIdx.x % CS) * DC;
+    for (int e = threadIdx.x; e < D * DC; e += 256) U[e] = make_double2((e / DC) == (e % DC) + c0 ? 1.0 : 0.0, 0.0);
     __syncthreads();
     for (int g = goff[blk]; g < goff[blk + 1]; ++g) {
         const int t = gates[g].target;
         const uint32_t cm = gates[g].ctrl;
         const double ar = gates[g].m[0], ai = gates[g].m[1], br = gates[g].m[2], bi = gates[g].m[3];
         const double cr = gates[g].m[4], ci = gates[g].m[5], dr = gates[g].m[6], di = gates[g].m[7];
-        for (int e = threadIdx.x; e < D * (D / 2); e += 256) {
+        for (int e = threadIdx.x; e < DC * (D / 2); e += 256) {
             const int c = e / (D / 2), p = e % (D / 2);
             const int i0 = ((p >> t) << (t + 1)) | (p & ((1 << t) - 1));
             if (((uint32_t)i0 & cm) != cm) continue;
             const int i1 = i0 | (1 << t);
-            const double2 a = U[i0 * D + c], b = U[i1 * D + c];
-            U[i0 * D + c] = make_double2(ar * a.x - ai * a.y + br * b.x - bi * b.y, ar * a.y + ai * a.x + br * b.y + bi * b.x);
-            U[i1 * D + c] = make_double2(cr * a.x - ci * a.y + dr * b.x - di * b.y, cr * a.y + ci * a.x + dr * b.y + di * b.x);
+            const double2 a = U[i0 * DC + c], b = U[i1 * DC + c];
+            U[i0 * DC + c] = make_double2(ar * a.x - ai * a.y + br * b.x - bi * b.y, ar * a.y + ai * a.x + br * b.y + bi * b.x);
+            U[i1 * DC + c] = make_double2(cr * a.x - ci * a.y + dr * b.x - di * b.y, cr * a.y + ci * a.x + dr * b.y + di * b.x);
         }
         __syncthreads();
     }
     float *out = bout + (size_t)blk * 2 * K * K;
-    for (int e = threadIdx.x; e < K * K; e += 256) {
-        const int n = e / K, kk = e % K;            // B_store[n][kk] = W[kk][n]
+    for (int e = threadIdx.x; e < K * 2 * DC; e += 256) {
+        const int n = e / (2 * DC), kk = 2 * c0 + e % (2 * DC);   // B_store[n][kk] = W[kk][n]
         const int i = n >> 1, b = n & 1, j = kk >> 1, a = kk & 1;
-        const double2 u = U[i * D + j];
+        const double2 u = U[i * DC + (j - c0)];
         const double w = (a == b) ? u.x : (a == 1 ? -u.y : u.y);
         if constexpr (KQ == 6) {
             __half *o16 = reinterpret_cast<__half *>(out);
@@ -1437,7 +1446,7 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
                    cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                         (int)cudaSharedmemCarveoutMaxShared) == cudaSuccess;
         };
-        const size_t smb = (size_t)(1 << KQ) * (1 << KQ) * sizeof(double2);
+        const size_t smb = (size_t)(1 << KQ) * ((1 << KQ) / kBuildSplit<KQ>) * sizeof(double2);
         if (!attrs((const void *)k_fuse_build<KQ>, smb)) {
             rc = cuda_fail(cudaGetLastError(), "fused kernel attributes");
             break;
@@ -1550,7 +1559,7 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
                 break;
             }
             launch_begin(s, KC_FUSE_BUILD, (double)nb * 2 * K * K * sizeof(float));
-            k_fuse_build<KQ><<<(unsigned)nb, 256, smb, s->stream>>>(dg, dgo, dw);
+            k_fuse_build<KQ><<<(unsigned)(nb * kBuildSplit<KQ>), 256, smb, s->stream>>>(dg, dgo, dw);
             if ((rc = launch_end(s, "fused build"))) break;
             for (size_t bi = 0; bi < nb && rc == SIM_OK; ++bi) {
                 if (blocks[bi].wide) {
