@@ -749,40 +749,50 @@ __device__ __forceinline__ void lane_locate32(const float *st, uint64_t base, ui
     }
 }
 
-// One CTA per block that received shots.  Warp 0 rebuilds the block's
-// inclusive scan of sub-sums P (the same operations as k_sub_sums); warp w
-// then takes shots w, w + 8, ... of the block: t = u_s * total; the sub-block
-// is the first j with bexcl + P[j] > t; the warp scans its amplitudes (lane-
-// serial prefix, then a warp scan of lane totals) and the outcome is the
-// first index whose prefix exceeds t.  Where rounding leaves no crossing (t
-// within an ulp of a boundary), the last sub-block / amplitude with non-zero
-// probability is taken.
+// Persistent warps over the shots in block order (the counting sort puts the
+// shots of one block next to each other): warp w takes shots
+// [w * per, (w + 1) * per) of `order`.  On entering a new block the warp
+// rebuilds that block's inclusive scan of sub-sums P (lane j holds P[j]; the
+// same operations as k_sub_sums, so the same bits) and its exclusive prefix.
+// Per shot: t = u_s * total; the sub-block is the first j with
+// bexcl + P[j] > t; the warp scans its amplitudes (lane-serial prefix, then a
+// warp scan of lane totals) and the outcome is the first index whose prefix
+// exceeds t.  Where rounding leaves no crossing (t within an ulp of a
+// boundary), the last sub-block / amplitude with non-zero probability is
+// taken.
 template <typename R>
 __global__ void __launch_bounds__(256) k_resolve(const R *__restrict__ st, uint64_t bs, uint64_t seed,
                                                  const double *__restrict__ bexcl, const double *__restrict__ total,
-                                                 const double *__restrict__ sub, const uint32_t *__restrict__ counts,
-                                                 const uint32_t *__restrict__ offs, const uint32_t *__restrict__ order,
+                                                 const double *__restrict__ sub, const uint32_t *__restrict__ shot_blk,
+                                                 const uint32_t *__restrict__ order, uint64_t shots, uint64_t per,
                                                  uint64_t *__restrict__ out)
 {
-    const uint32_t cnt = counts[blockIdx.x];
-    if (cnt == 0) return;
     const SubGeo g(bs);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __shared__ double P[32];
-    if (warp == 0)
-        P[lane] = warp_incl_scan(((uint32_t)lane < g.nsub) ? sub[(uint64_t)blockIdx.x * g.nsub + lane] : 0.0, lane);
-    __syncthreads();
-    const double be = bexcl[blockIdx.x], tot = *total;
-    const uint64_t base = (uint64_t)blockIdx.x * bs;
-    const uint32_t o0 = offs[blockIdx.x];
-    const bool lane_nz = (uint32_t)lane < g.nsub && (lane == 0 ? P[0] > 0.0 : P[lane] > P[lane - 1]);
-    const unsigned sub_nz = __ballot_sync(0xffffffffu, lane_nz);
-    for (uint32_t k = warp; k < cnt; k += 8) {
-        const uint32_t s = order[o0 + k];
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t k0 = warp * per;
+    const uint64_t k1 = min(shots, k0 + per);
+    const double tot = *total;
+    uint32_t cur = 0xFFFFFFFFu;          // block whose scan the warp holds
+    double Pl = 0.0, be = 0.0;
+    unsigned sub_nz = 0u;
+    for (uint64_t k = k0; k < k1; ++k) {
+        const uint32_t s = order[k];
+        const uint32_t blk = shot_blk[s];
+        if (blk != cur) {
+            cur = blk;
+            Pl = warp_incl_scan(((uint32_t)lane < g.nsub) ? sub[(uint64_t)blk * g.nsub + lane] : 0.0, lane);
+            be = bexcl[blk];
+            const double prev = __shfl_up_sync(0xffffffffu, Pl, 1);
+            const bool lane_nz = (uint32_t)lane < g.nsub && (lane == 0 ? Pl > 0.0 : Pl > prev);
+            sub_nz = __ballot_sync(0xffffffffu, lane_nz);
+        }
+        const uint64_t base = (uint64_t)blk * bs;
         const double t = unif(seed, s) * tot;
-        const unsigned hit = __ballot_sync(0xffffffffu, (uint32_t)lane < g.nsub && be + P[lane] > t);
+        const unsigned hit = __ballot_sync(0xffffffffu, (uint32_t)lane < g.nsub && be + Pl > t);
         const uint32_t j = hit ? (uint32_t)(__ffs(hit) - 1) : (sub_nz ? (uint32_t)(31 - __clz(sub_nz)) : 0u);
-        const double pre = be + (j > 0 ? P[j - 1] : 0.0);
+        const double pj = __shfl_sync(0xffffffffu, Pl, (int)(j > 0 ? j - 1 : 0));
+        const double pre = be + (j > 0 ? pj : 0.0);
         int first = -1, last_nz = -1;
         if (sizeof(R) == 4 && g.apl == 8) {
             lane_locate32(reinterpret_cast<const float *>(st), base, j, lane, pre, t, first, last_nz);
@@ -981,14 +991,23 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
         launch_begin(s, KC_SAMPLE);
         k_scatter<<<grid_for(shots, 256, s->num_sms), 256, 0, s->stream>>>(shots, sblk, cur, order);
         if ((rc = launch_end(s, "scatter shots"))) break;
-        // per shot: one sub-block of amplitudes
+        // per shot: one sub-block of amplitudes; warps as many as are resident
         launch_begin(s, KC_SAMPLE, (double)shots * sg.sub * (c128 ? 16.0 : 8.0));
-        if (c128)
-            k_resolve<double><<<(unsigned)nb, 256, 0, s->stream>>>((const double *)s->amps, bs, seed, bexcl, tot, sub,
-                                                                   cnt, offs, order, dout);
-        else
-            k_resolve<float><<<(unsigned)nb, 256, 0, s->stream>>>((const float *)s->amps, bs, seed, bexcl, tot, sub,
-                                                                  cnt, offs, order, dout);
+        {
+            const void *fn = c128 ? (const void *)k_resolve<double> : (const void *)k_resolve<float>;
+            int per_sm = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1)
+                per_sm = 1;
+            const uint64_t warps = (uint64_t)s->num_sms * per_sm * 8;
+            const uint64_t per = (shots + warps - 1) / warps;
+            const unsigned grid = (unsigned)((shots + per * 8 - 1) / (per * 8));
+            if (c128)
+                k_resolve<double><<<grid, 256, 0, s->stream>>>((const double *)s->amps, bs, seed, bexcl, tot, sub, sblk,
+                                                               order, shots, per, dout);
+            else
+                k_resolve<float><<<grid, 256, 0, s->stream>>>((const float *)s->amps, bs, seed, bexcl, tot, sub, sblk,
+                                                              order, shots, per, dout);
+        }
         if ((rc = launch_end(s, "resolve shots"))) break;
         if (!out_on_device) {
             if (cudaMemcpyAsync(out, dout, shots * 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) {
