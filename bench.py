@@ -52,11 +52,11 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # captures stay at a few GB on the device) and the traffic of a launch grows
 # with the state, so it is scaled by 2^n.
 TRAFFIC = {
-    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073933 GB + dram__bytes_write.sum 1.012051 GB
-    "fused_f16": {"bytes_per_amp": (1.073933e9 + 1.012051e9) / 2 ** 27,
+    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073939 GB + dram__bytes_write.sum 1.011877 GB
+    "fused_f16": {"bytes_per_amp": (1.073939e9 + 1.011877e9) / 2 ** 27,
                   "source": "paper_1805_00988_gb300/csrc/fused.cu",
                   "until": "// ------------------------------------------------------------------ multi-block passes",
-                  "sha256": "e1a6f382b0ff0372b0b7a5c134530a28edc1b8d252ebb2163a71ecaa00ff87f9",
+                  "sha256": "2b903a67ccabcbf3248544d5556cf98fb1556f434207a69508a6590ae46280c0",
                   "profile": "profiles/k_fused_tmem6_27q.md"},
 }
 

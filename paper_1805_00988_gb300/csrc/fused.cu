@@ -15,7 +15,9 @@
 // 1e-6 over ~100 blocks.  Both operands are split x = x_hi + x_lo with x_hi
 // = x rounded to TF32 and x_lo = (x - x_hi) rounded to TF32 (both to nearest,
 // so the split carries no bias), and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is
-// accumulated in FP32 in tensor memory (3xTF32; Ootomo & Yokota 2022).  U_blk
+// accumulated in FP32 in tensor memory (3xTF32; Ootomo & Yokota 2022).  k = 6
+// splits into FP16 parts of 2^14-scaled operands instead (the same 22
+// significant bits at twice the tensor rate; see k_fused_tmem6).  U_blk
 // itself is formed in FP64 (k_fuse_build) before the split.
 //
 // Apply kernels: persistent, warp-specialised CTAs stream tiles of 128 rows
