@@ -147,15 +147,21 @@ int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_
  *   amplitudes, each carried into FP64; within about 1e-12 relative of the
  *   exact sum).
  * sim_measure: measure one qubit in the computational basis (§1.3.3):
- *   p0, p1 summed in FP64; outcome 0 iff p0 > u (p0 + p1) with
+ *   p0, p1 summed in FP64 (accumulated as for sim_norm); outcome 0 iff
+ *   p0 > u (p0 + p1) with
  *   u = (splitmix64(seed + draw) >> 11) * 2^-53 (SplitMix64, Steele et al.
  *   2014); the other half is zeroed and the kept half scaled by
  *   1 / sqrt(p_outcome).  *prob (may be NULL) gets p_outcome / (p0 + p1).
  * sim_sample: non-destructive shot sampling (§2.4): shot s is the smallest j
- *   with C_j > u_s C_total, C the inclusive FP64 prefix of |a_j|^2,
+ *   with C_j > u_s C_total, C the inclusive FP64 prefix of |a_j|^2 (partial
+ *   sums accumulated as for sim_norm; a shot whose target lies within about
+ *   1e-12 C_total of a prefix value may land on the neighbouring index, and
+ *   an amplitude that is exactly zero is never drawn),
  *   u_s = (splitmix64(seed + s) >> 11) * 2^-53.  out: shots uint64 indices,
  *   on the device when out_on_device, else host memory.
- * sim_expect_z_sum: <sum_i Z_i> = sum_x |a_x|^2 (n - 2 popcount x), FP64. */
+ * sim_expect_z_sum: <sum_i Z_i> = sum_x |a_x|^2 (n - 2 popcount x), FP64
+ *   (complex64: squares accumulated as for sim_norm, weighted by exact
+ *   products). */
 int sim_probabilities(sim_t s, void *dev_out, int out_real);
 int sim_norm(sim_t s, double *out);
 int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob);
