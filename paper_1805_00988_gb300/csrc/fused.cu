@@ -1269,9 +1269,17 @@ public:
             std::vector<int> cand;
             for (int q = 0; q < n_; ++q)
                 if (!((S >> q) & 1) && ((touched_ >> q) & 1)) cand.push_back(q);
+            // bounds pay for themselves only where pairs and triples are
+            // searched (measured: depth 1 runs faster without them)
+            const bool prune = depth_ >= 2 && free >= 2;
+            if (prune) load_bounds(S, std::min(depth_, free));
             int best = absorb(S);
             uint64_t best_add = 0;
+            // a candidate replaces the best only with a strictly larger count,
+            // so one whose bound is not larger is skipped without changing the
+            // outcome
             for (size_t i = 0; i < cand.size(); ++i) {
+                if (prune && bound1(cand[i]) <= best) continue;
                 const uint64_t a1 = 1ull << cand[i];
                 const int c1 = absorb(S | a1);
                 if (c1 > best) { best = c1; best_add = a1; }
@@ -1279,6 +1287,7 @@ public:
             if (depth_ >= 2 && free >= 2) {
                 for (size_t i = 0; i < cand.size(); ++i)
                     for (size_t j = i + 1; j < cand.size(); ++j) {
+                        if (bound2(cand[i], cand[j]) <= best) continue;
                         const uint64_t a2 = (1ull << cand[i]) | (1ull << cand[j]);
                         const int c2 = absorb(S | a2);
                         if (c2 > best) { best = c2; best_add = a2; }
@@ -1286,13 +1295,18 @@ public:
             }
             if (depth_ >= 3 && free >= 3) {
                 // triples, split by their first candidate over host threads;
-                // each slice keeps its first best, the earliest slice wins ties
+                // each slice keeps its first best, the earliest slice wins ties.
+                // A triple is skipped when its bound is not above both the
+                // best before the triples and its slice's best: it could then
+                // neither be its slice's first maximum nor win the merge.
                 const size_t nc = cand.size();
+                const int floor = best;
                 std::vector<int> sbest(nc, -1);
                 std::vector<uint64_t> sadd(nc, 0);
                 parallel_for(nc, [&](size_t i) {
                     for (size_t j = i + 1; j < nc; ++j)
                         for (size_t l = j + 1; l < nc; ++l) {
+                            if (bound3(cand[i], cand[j], cand[l]) <= std::max(floor, sbest[i])) continue;
                             const uint64_t a3 = (1ull << cand[i]) | (1ull << cand[j]) | (1ull << cand[l]);
                             const int c3 = absorb(S | a3);
                             if (c3 > sbest[i]) { sbest[i] = c3; sadd[i] = a3; }
@@ -1337,6 +1351,43 @@ private:
         }
     }
 
+    // Upper bounds on absorb(S | a) for the candidate sets a of one growth
+    // step: every window gate counted once, by its qubits outside S (at most
+    // `depth` of them); absorb(S | a) counts a subset of the gates whose
+    // outside qubits lie in a, so bound(a) >= absorb(S | a).
+    void load_bounds(uint64_t S, int depth)
+    {
+        c0_ = 0;
+        c1_.assign((size_t)n_, 0);
+        c2_.assign(depth >= 2 ? (size_t)n_ * n_ : 0, 0);
+        c3_.clear();
+        for (size_t i = 0; i < wx_.size(); ++i) {
+            const uint64_t r = (wx_[i] | wd_[i]) & ~S;
+            const int pc = __builtin_popcountll(r);
+            if (pc == 0) {
+                ++c0_;
+            } else if (pc == 1) {
+                ++c1_[(size_t)__builtin_ctzll(r)];
+            } else if (pc == 2 && depth >= 2) {
+                const int a = __builtin_ctzll(r), b = __builtin_ctzll(r & (r - 1));
+                ++c2_[(size_t)a * n_ + b];
+            } else if (pc == 3 && depth >= 3) {
+                c3_.push_back(r);
+            }
+        }
+        std::sort(c3_.begin(), c3_.end());
+    }
+    int bound1(int a) const { return c0_ + c1_[(size_t)a]; }
+    // a < b < c (candidates ascending)
+    int bound2(int a, int b) const { return c0_ + c1_[(size_t)a] + c1_[(size_t)b] + c2_[(size_t)a * n_ + b]; }
+    int bound3(int a, int b, int c) const
+    {
+        const uint64_t m = (1ull << a) | (1ull << b) | (1ull << c);
+        const auto r = std::equal_range(c3_.begin(), c3_.end(), m);
+        return bound2(a, b) + c1_[(size_t)c] + c2_[(size_t)a * n_ + c] + c2_[(size_t)b * n_ + c] +
+               (int)(r.second - r.first);
+    }
+
     // gates of the window that could join a block on qubit set S
     int absorb(uint64_t S) const
     {
@@ -1360,6 +1411,9 @@ private:
     size_t first_ = 0;
     std::vector<uint64_t> wx_, wd_;
     uint64_t touched_ = 0;
+    int c0_ = 0;                      // bounds of the current growth step (load_bounds)
+    std::vector<int> c1_, c2_;
+    std::vector<uint64_t> c3_;
 };
 
 // Multi-block passes (k = 5): consecutive pairs of blocks whose qubits, with

@@ -23,6 +23,9 @@ def test_block_counts_cpu():
     # larger blocks never need more of them
     assert blocks == sorted(blocks, reverse=True)
     assert blocks[-1] < 900
+    # the plans the timed runs use (depth 3 after a first group at depth 2);
+    # the planner's bound pruning must not change them
+    assert desc[5][1] == 73 and desc[6][1] == 54
     # one pass per block by default; with multi-block passes k = 5 pairs blocks
     for k in (3, 4, 5, 6):
         assert desc[k][0] == desc[k][1]
