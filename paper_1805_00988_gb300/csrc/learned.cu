@@ -127,7 +127,10 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
             if (feasible(s->n, s->dtype, v)) cand.push_back({w, v});
     std::vector<float> feat(cand.size() * SIM_FEATURES);
     std::vector<char> ok(cand.size(), 0);
-    parallel_for(cand.size(), [&](size_t r) {
+    // rows in reverse: the whole-circuit segment (the longest rows, its block
+    // planner runs over every gate) starts first instead of after the windows
+    parallel_for(cand.size(), [&](size_t i) {
+        const size_t r = cand.size() - 1 - i;
         const Window &w = seg[cand[r].first];
         ok[r] = plan_features(s->n, s->dtype, gates + w.first, w.count, cand[r].second,
                               feat.data() + r * SIM_FEATURES) == SIM_OK;
