@@ -76,7 +76,32 @@ def test_fused_random_circuits(gsim, orc, n, k):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("k", [3, 4, 5])
+@pytest.mark.parametrize("qubits", [(0, 1, 2, 3, 4, 5), (10, 11, 12, 13, 14, 15), (0, 3, 7, 9, 12, 15),
+                                    (1, 2, 5, 8, 11, 14)])
+def test_fused_k6_block_placements(gsim, orc, qubits):
+    """k = 6 on one block per placement, 16 qubits.  Qubits 0..5: a tile is a
+    single 64 KB run and every low tile bit is a block bit (the converters'
+    largest bank-spreading permutation); 10..15: 64 runs of 1 KB; the mixed
+    placements with and without qubit 0 take the consumer's 16-byte and
+    8-byte stores."""
+    n = 16
+    q = list(qubits)
+    g = C.concat([C.gate("h", t) for t in q] +
+                 [C.gate("z", q[i + 1], controls=(q[i],)) for i in range(5)] +
+                 [C.gate("rx", t, params=(0.3 + 0.1 * i,)) for i, t in enumerate(q)] +
+                 [C.gate("x", q[5], controls=(q[0],)), C.gate("t", q[2])])
+    blocks = gsim.sim_plan_describe(n, 0, gsim.to_sim_gates(g), gsim.plan_opts("fused", fuse_k=6))[1]
+    assert blocks == 1
+    st = gsim.State(n, "c64")
+    psi = C.random_state(n, seed=sum(q))
+    st.load(psi)
+    st.apply(g, plan="fused", fuse_k=6)
+    check(orc, st.state(), orc.apply_circuit(psi.astype(np.complex64).astype(np.complex128), g))
+    st.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k", [3, 4, 5, 6])
 def test_fused_many_tiles_per_cta(gsim, orc, k):
     """24 qubits: every CTA of the persistent kernel streams many tiles, so
     the stage ring and both accumulators wrap around many times."""
