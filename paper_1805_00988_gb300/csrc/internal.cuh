@@ -175,24 +175,14 @@ int fused_feature_depth();
 int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,
                     int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len);
 
-// f(0) .. f(count - 1) on up to 16 host threads (plain loop for one)
+// f(0) .. f(count - 1) on up to 16 host threads: the calling thread and a
+// persistent pool (pool.cu).  Serial for one index, inside a pool thread, or
+// on a one-core host.  The calling thread can finish any call alone.
+void parallel_run(size_t count, void (*fn)(void *, size_t), void *ctx);
 template <typename F>
 void parallel_for(size_t count, F f)
 {
-    size_t nt = std::min<size_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
-    nt = std::min(nt, count);
-    if (nt <= 1) {
-        for (size_t i = 0; i < count; ++i) f(i);
-        return;
-    }
-    std::atomic<size_t> next{0};
-    std::vector<std::thread> th;
-    th.reserve(nt);
-    for (size_t t = 0; t < nt; ++t)
-        th.emplace_back([&] {
-            for (size_t i; (i = next.fetch_add(1)) < count;) f(i);
-        });
-    for (auto &x : th) x.join();
+    parallel_run(count, [](void *c, size_t i) { (*static_cast<F *>(c))(i); }, &f);
 }
 
 // host-side SplitMix64 draw (Steele, Lea & Flood 2014)
