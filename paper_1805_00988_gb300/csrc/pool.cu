@@ -12,10 +12,10 @@
 // or missing can slow it but never block it.  This matters for a call made
 // from inside a job (it runs serially in a worker, and as a nested job from
 // the calling thread), for several host threads calling at once, and for a
-// child process forked while the pool was idle (it has no workers).  The caller then waits
-// until every worker that took the job has left it, because the job lives
-// on the caller's stack.  The pool is never destroyed; its threads end with
-// the process.
+// child process forked while the pool was idle (it has no workers).  The
+// caller then waits until every worker that took the job has left it,
+// because the job lives on the caller's stack.  The pool is never destroyed;
+// its threads end with the process.
 #include <condition_variable>
 #include <deque>
 #include <mutex>
