@@ -33,6 +33,36 @@ def test_block_counts_cpu():
     assert multi[1] == desc[5][1] and multi[0] < multi[1]
 
 
+def test_planner_concurrent_calls_cpu():
+    """The depth-3 block planner spreads its triple search over the host
+    thread pool; host threads planning at the same time (the binding releases
+    the GIL in the call) get the same plans as one thread alone."""
+    import threading
+    from paper_1805_00988_gb300 import sim
+    circ = {n: sim.to_sim_gates(C.haar_cz(n, 8, seed=n)) for n in (20, 24, 26)}
+    ref = {(n, k): sim.sim_plan_describe(n, 0, g, sim.plan_opts("fused", fuse_k=k))[:2]
+           for n, g in circ.items() for k in (5, 6)}
+    got, errs = [], []
+
+    def worker(seed):
+        try:
+            for i in range(6):
+                n = (20, 24, 26)[(seed + i) % 3]
+                k = 5 + (seed + i) % 2
+                got.append(((n, k), sim.sim_plan_describe(n, 0, circ[n], sim.plan_opts("fused", fuse_k=k))[:2]))
+        except Exception as e:          # pragma: no cover - reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=worker, args=(s,)) for s in range(6)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=120)
+    assert not errs and len(got) == 36
+    for key, r in got:
+        assert r == ref[key], (key, r, ref[key])
+
+
 @pytest.fixture(scope="module")
 def gsim():
     import torch
