@@ -97,6 +97,80 @@ def traffic_for(kind: str, n: int):
     return t["bytes_per_amp"] * 2.0 ** n, ("ncu capture in %s (27-qubit launch, scaled by 2^(n-27))" % t["profile"])
 
 
+# ---------------------------------------------------------------- the paper's own benchmark (opt-in)
+# Algorithm 2 ("Benchmarking algorithm"): for every register size, a number of
+# samples, each of a simulator type drawn at random, timing the App. A QFT
+# (controlled phases then H, no final swaps) including the register's
+# creation, until the device is done (§3, independence by shuffling).  The
+# simulator types here are this library's plans and precisions.  Sizes start
+# at 1 qubit (the algorithm's loop starts at 0, which is no register).
+PAPER_TYPES = ("per_gate_c64", "per_gate_c128", "learned_c64", "staged_c64")
+
+
+def paper_types(n: int):
+    """The types that run an n-qubit register (register tiles need n >= 11)."""
+    return [t for t in PAPER_TYPES if t != "staged_c64" or n >= 11]
+
+
+def paper_sweep_schedule(max_n: int, samples: int, seed: int):
+    """(n, type) in run order: n = 1 .. max_n, `samples` runs each, every run's
+    type drawn at random from the types that run n qubits."""
+    import random
+    rng = random.Random(seed)
+    return [(n, rng.choice(paper_types(n))) for n in range(1, max_n + 1) for _ in range(samples)]
+
+
+def summarize_sweep(rows):
+    """rows of (type, n, seconds) -> {type: {n: runs, mean / median / min ms}}."""
+    out = {}
+    for typ, n, sec in rows:
+        out.setdefault(typ, {}).setdefault(n, []).append(sec * 1e3)
+    return {typ: {str(n): {"runs": len(v), "mean_ms": statistics.fmean(v), "median_ms": statistics.median(v),
+                           "min_ms": min(v)} for n, v in sorted(per.items())}
+            for typ, per in sorted(out.items())}
+
+
+def run_paper_sweep(args):
+    """One JSON line with the sweep's rows and their summary (rank 0 only)."""
+    import torch
+    from paper_1805_00988_gb300 import build
+    build.build()
+    from paper_1805_00988_gb300 import circuits as C
+    from paper_1805_00988_gb300 import costmodel, sim
+    model, _ = costmodel.load()
+
+    def opts_for(plan, n):
+        if plan == "staged":
+            return sim.plan_opts("staged", tile_qubits=min(13, n))
+        return sim.plan_opts(plan)
+
+    def one(n, typ):
+        plan, dt = typ.rsplit("_", 1)
+        g = sim.to_sim_gates(C.qft_paper(n))
+        o = opts_for(plan, n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = sim.State(n, dt)
+        if plan == "learned":
+            sim.sim_set_cost_model(st.h, model)
+        sim.sim_apply_circuit(st.h, g, o)
+        sim.sim_synchronize(st.h)
+        sec = time.perf_counter() - t0
+        st.close()
+        return sec
+
+    warm = min(12, args.paper_sweep)
+    for typ in paper_types(warm):            # one untimed run per type (library and context start-up)
+        one(warm, typ)
+    rows = [(typ, n, one(n, typ)) for n, typ in paper_sweep_schedule(args.paper_sweep, args.paper_samples, SEED)]
+    print(json.dumps({"mode": "paper_qft_sweep", "circuit": "App. A QFT order (no swaps), from |0...0>",
+                      "timed": "wall time: register creation + the whole QFT + device synchronisation",
+                      "max_qubits": args.paper_sweep, "samples": args.paper_samples, "seed": SEED,
+                      "summary": summarize_sweep(rows),
+                      "rows": [[t, n, round(s * 1e3, 4)] for t, n, s in rows]}))
+    return 0
+
+
 def workload_name(n, depth):
     return "haar_cz: %d qubits, depth %d (Haar U(2) on every qubit + CZ on a random matching per layer)" % (n, depth)
 
@@ -602,6 +676,9 @@ def main():
     ap.add_argument("--no-c5", dest="c5", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--paper-sweep", type=int, default=0,
+                    help="instead of the timed step: the paper's QFT sweep up to this many qubits (rank 0)")
+    ap.add_argument("--paper-samples", type=int, default=5)
     args = ap.parse_args()
     args.variant_plans = [p for p in args.variant_plans.split(",") if p]
     rank = int(os.environ.get("RANK", "0"))
@@ -609,6 +686,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.paper_sweep > 0:
+        return run_paper_sweep(args) if rank == 0 else 0
     if world > 1:
         import torch
         import torch.distributed as dist
