@@ -49,7 +49,11 @@ class Pool {
 public:
     explicit Pool(int workers)
     {
-        for (int w = 0; w < workers; ++w) std::thread([this] { work(); }).detach();
+        // a thread that cannot be started leaves fewer workers (callers finish alone)
+        try {
+            for (int w = 0; w < workers; ++w) std::thread([this] { work(); }).detach();
+        } catch (...) {
+        }
     }
 
     void run(Job *j)
