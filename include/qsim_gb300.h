@@ -89,9 +89,12 @@ typedef enum {
 typedef struct sim_plan_opts {
     int32_t plan;            /* sim_plan_kind */
     int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block, 3..6 (0 = 5); k <= 5 runs
-                                3xTF32, k = 6 an FP16 hi / lo split of 2^14-scaled operands (same 22
-                                significant bits), which needs |a_j| < 2 for every amplitude (every
-                                normalised state): SIM_EUNSUPPORTED otherwise */
+                                3xTF32, k = 6 an FP16 hi / lo split (same 22 significant bits) of
+                                operands scaled by powers of two: the state by one chosen from its
+                                norm (one extra pass over the state per call), each block's matrix
+                                by one chosen from the product of its gates' spectral norms, so
+                                states of any magnitude are applied at the same precision relative
+                                to their norm; SIM_EUNSUPPORTED if that product exceeds 2^114 */
     int32_t tile_qubits;     /* SIM_PLAN_STAGED: tile size log2 (0 = default) */
     int32_t flags;           /* SIM_FLAG_* bits, 0 = defaults */
 } sim_plan_opts;
@@ -132,10 +135,7 @@ int sim_copy_state(sim_t s, void *dst, int dst_is_host);
  *   updated (§2.3, App. B.2).  SIM_EINVAL if a qubit is out of range, a
  *   control equals the target or two controls are equal.
  * sim_apply_circuit: apply n_gates gates in order, scheduled by opts (NULL =
- *   SIM_PLAN_PER_GATE).  The whole list is validated before anything runs.
- *   SIM_PLAN_FUSED with k = 6 checks |a_j| < 2 while it runs: a call that
- *   meets a larger amplitude returns SIM_EUNSUPPORTED and leaves the state
- *   unusable (reload it). */
+ *   SIM_PLAN_PER_GATE).  The whole list is validated before anything runs. */
 int sim_apply_gate(sim_t s, const double U[8], int target, const int *controls, int n_controls);
 int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts);
 

@@ -16,7 +16,7 @@
 // = x rounded to TF32 and x_lo = (x - x_hi) rounded to TF32 (both to nearest,
 // so the split carries no bias), and D = A_hi B_hi + A_hi B_lo + A_lo B_hi is
 // accumulated in FP32 in tensor memory (3xTF32; Ootomo & Yokota 2022).  k = 6
-// splits into FP16 parts of 2^14-scaled operands instead (the same 22
+// splits into FP16 parts of power-of-two-scaled operands instead (the same 22
 // significant bits at twice the tensor rate; see k_fused_tmem6).  U_blk
 // itself is formed in FP64 (k_fuse_build) before the split.
 //
@@ -183,15 +183,19 @@ __host__ __device__ __forceinline__ uint32_t kmajor16_off(uint32_t row, uint32_t
     return (((row >> 3) * (K >> 3) + (kk >> 3)) << 7) + ((row & 7) << 4) + ((kk & 7) << 1);
 }
 
-// k = 6 runs on FP16 operands scaled by 2^14 (see k_fused_tmem6)
-constexpr float kF16Scale = 16384.0f;
+// k = 6 runs on FP16 operands scaled by powers of two (see k_fused_tmem6):
+// the state by 2^se, se from a bound on its norm, each block's W by 2^we, we
+// from a host bound on the block's entries (kF16WExp for a unitary block).
+constexpr int kF16WExp = 14;
+constexpr int kF16WExpMin = -100, kF16WExpMax = 126;
 
 // ------------------------------------------------------------------ FP64 builder
 // U = G_m ... G_1 applied to the identity column by column in FP64 (the
 // columns are 2^k-amplitude states of the block's qubits and evolve
 // independently), then W (the real form) split into TF32 hi / lo in the
-// B-operand layout: [hi | lo], each K x K, K-major.  k = 6: 2^14 W split into
-// FP16 hi / lo (both rounded to nearest) in the 16-bit layout, [hi | lo] again.
+// B-operand layout: [hi | lo], each K x K, K-major.  k = 6: 2^we W split into
+// FP16 hi / lo (both rounded to nearest) in the 16-bit layout, [hi | lo] again,
+// we = wexp[block].
 // Each block's columns are spread over kBuildSplit<KQ> CTAs of 8 columns
 // (this GPU's FP64 pipe is narrow: one CTA per block left the build
 // FP64-bound on a handful of SMs); CTA (block, part) writes the W entries of
@@ -201,7 +205,7 @@ constexpr int kBuildSplit = (1 << KQ) >= 8 ? (1 << KQ) / 8 : 1;
 
 template <int KQ>
 __global__ void __launch_bounds__(256) k_fuse_build(const FGate *__restrict__ gates, const int *__restrict__ goff,
-                                                    float *__restrict__ bout)
+                                                    const int *__restrict__ wexp, float *__restrict__ bout)
 {
     constexpr int D = 1 << KQ;
     constexpr int K = 2 * D;
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(256) k_fuse_build(const FGate *__restrict__ ga
         const double w = (a == b) ? u.x : (a == 1 ? -u.y : u.y);
         if constexpr (KQ == 6) {
             __half *o16 = reinterpret_cast<__half *>(out);
-            const double ws = w * (double)kF16Scale;
+            const double ws = ldexp(w, wexp[blk]);
             const __half hi = __double2half(ws);
             const __half lo = __double2half(ws - (double)__half2float(hi));
             const uint32_t off = kmajor16_off(n, kk, K) >> 1;
@@ -256,6 +260,12 @@ struct ApplyArgs {
     int nq;             // qubits of the block (KQ)
     int pos[8];         // global qubits of the block, ascending (local bit i <-> pos[i])
     uint64_t rows;      // 2^(n - KQ)
+    // k = 6 only: W was scaled by 2^wexp before its FP16 split; the state's
+    // norm^2 at the start of the call is *nrm2 (device), and growth bounds
+    // how much the blocks and gates launched since then can have raised it
+    int wexp;
+    const double *nrm2;
+    double growth;
 };
 
 // ------------------------------------------------------------------ streamed apply (k <= 5)
@@ -587,19 +597,29 @@ size_t stream_smem_bytes()
 // For k = 6 (K = N = 128) the tensor work per amplitude doubles and 3xTF32
 // operands do not fit next to a stage ring (W hi | lo alone is 128 KB), so
 // this kernel splits into FP16 instead: x = x_hi + x_lo with both parts FP16
-// rounded to nearest, after scaling the state by 2^14 and W by 2^14 (exact
-// powers of two).  An FP16 part carries 11 significant bits like a TF32 part,
-// so hi + lo keeps 22 bits as in 3xTF32, and kind::f16 runs at twice the rate
-// of kind::tf32.  The scaling keeps normalised amplitudes (|a| <= 1) below the
-// FP16 maximum and the parts of typical amplitudes (|a| ~ 2^-15 at 30 qubits)
-// in the normal range; an amplitude below 2^-28 loses relative precision but
-// keeps an absolute error below 2^-38.  A converter that meets |a| >= 2 records
-// SIM_EUNSUPPORTED (the result of that call is not usable).
+// rounded to nearest, after scaling the state and W by exact powers of two.
+// An FP16 part carries 11 significant bits like a TF32 part, so hi + lo keeps
+// 22 bits as in 3xTF32, and kind::f16 runs at twice the rate of kind::tf32.
+// Scales.  FP16 has a 5-bit exponent, so the scales follow the data.  Every
+// amplitude is at most the state's norm, and a block multiplies the norm by
+// at most its spectral norm; so with B^2 = nrm2 x growth (the norm^2 measured
+// at the start of the call times the bound on what the blocks and gates
+// launched since then can have added), 2^E <= B < 2^(E+1) and se = 14 - E
+// (clamped to [-126, 126]), every scaled component is below 2^15, so the FP16
+// maximum (65504) is not reached even if rounding had raised the norm by
+// almost a factor 2, and amplitudes down to 2^-17 B keep 22 significant bits
+// whatever the state's magnitude; smaller ones keep an absolute error below
+// 2^-39 B (an infidelity contribution below 2^-78 per amplitude).  A state
+// whose norm^2 overflows FP64 or is not a number cannot occur for finite
+// complex64 amplitudes.
+// W is scaled by 2^we, we from a host bound on the block's entries (14 for a
+// unitary block).  The product is linear, so D = 2^(se + we) x (state W) up to
+// the split; the consumer multiplies by 2^-(se + we) (in two exact steps when
+// that factor is not a normal float).
 // D = A_lo W_hi + A_hi W_lo + A_hi W_hi is accumulated in FP32 in tensor
 // memory, the two small products first over all K-steps: the tensor core's
 // accumulation truncates, and adding the small products before the
-// accumulator is large keeps their share of that bias negligible.  The
-// consumer multiplies by 2^-28.
+// accumulator is large keeps their share of that bias negligible.
 // Tensor memory: A buffers of 128 columns (FP16 pairs: A_hi in the first 64,
 // A_lo in the next 64) at [0, 128) and [128, 256), accumulators at [256, 384)
 // and [384, 512).  Shared memory: two 64 KB stages and W (hi | lo, 32 KB each).
@@ -610,7 +630,7 @@ size_t stream_smem_bytes()
 //       TMEM lane r of A buffer i mod 2, once the MMAs of tile i - 2 are done;
 //   warp 8 (one thread): the 24 MMAs of tile i once A is written and the
 //       accumulator has been drained (tile i - 2);
-//   warps 4-7: accumulator -> 2^-28 x -> HBM.
+//   warps 4-7: accumulator -> 2^-(se + we) x -> HBM.
 // Every wait is bounded as in k_fused_stream.
 constexpr int kT6Threads = 320;
 
@@ -655,7 +675,6 @@ __global__ void __launch_bounds__(kT6Threads, 1)
     constexpr uint32_t SBO = (K / 8) * 128;          // 8-row group stride of W, bytes
     constexpr uint32_t WLO = (uint32_t)K * K * 2u;   // byte offset of W_lo
     constexpr uint32_t IDESC = make_idesc_f16(kRows, K);
-    constexpr float kUnscale = 1.0f / (kF16Scale * kF16Scale);
 
     extern __shared__ __align__(1024) unsigned char smem[];
     float2 *stage = reinterpret_cast<float2 *>(smem);                    // 2 x TAMP amplitudes
@@ -667,12 +686,17 @@ __global__ void __launch_bounds__(kT6Threads, 1)
     __shared__ int lrun;              // L: tile-local bits 0 .. L-1 are global bits 0 .. L-1
     __shared__ uint32_t uc[D];        // tile-local offset of column c
     __shared__ uint64_t gc[D];        // global offset of column c
-    __shared__ int failed, too_large;
+    __shared__ int failed, sexp;      // sexp: se, the state's scale exponent
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         failed = *reinterpret_cast<volatile int *>(status);
-        too_large = 0;
+        // B^2 = nrm2 x growth; 2^e2 <= B^2 < 2^(e2 + 1) gives 2^E <= B < 2^(E + 1)
+        // with E = floor(e2 / 2); se = 14 - E
+        double b2 = *a.nrm2 * a.growth;
+        if (!(b2 > 0.0)) b2 = 0.0;                                    // NaN or zero: any scale
+        const int e2 = (int)((__double_as_longlong(b2) >> 52) & 0x7ff) - 1023;   // -1023 for 0 / subnormal
+        sexp = max(-126, min(126, 14 - (e2 >> 1)));                    // E = floor(e2 / 2)
         uint64_t pm = 0;
         for (int i = 0; i < KQ; ++i) pm |= 1ull << a.pos[i];
         uint64_t tm = pm;
@@ -787,7 +811,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
         const int x = (tid >> (4 - zc)) & ((1 << zc) - 1);
         const uint32_t ux = uc[x];
         const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
-        float amax = 0.f;
+        const float xs = __uint_as_float((uint32_t)(sexp + 127) << 23);   // 2^se
         for (int i = 0; i < iters && !*vfailed; ++i) {
             const int s = i & 1, b = i & 1;
             if (!mbar_wait_bounded(&bar_full[s], (uint32_t)((i >> 1) & 1))) {
@@ -826,8 +850,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                 uint32_t rh[32], rl[32];
 #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    amax = fmaxf(amax, fmaxf(fabsf(v[j].x), fabsf(v[j].y)));
-                    const float xr = v[j].x * kF16Scale, xi = v[j].y * kF16Scale;
+                    const float xr = v[j].x * xs, xi = v[j].y * xs;
                     const __half2 hh = __floats2half2_rn(xr, xi);
                     const float2 hf = __half22float2(hh);
                     const __half2 hl = __floats2half2_rn(xr - hf.x, xi - hf.y);
@@ -842,7 +865,6 @@ __global__ void __launch_bounds__(kT6Threads, 1)
             tc_fence_before();
             mbar_arrive(&bar_a[b]);
         }
-        if (amax >= 2.0f) too_large = 1;
     } else if (warp < 8) {
         // consumers: warp w reads TMEM lanes 32 (w - 4) .. + 31 = rows of the tile
         const int r = tid - 128;
@@ -850,6 +872,13 @@ __global__ void __launch_bounds__(kT6Threads, 1)
         uint64_t gr;
         row_offsets(r, ur, gr);
         const bool q0_in_block = (pmask & 1ull) != 0;
+        // 2^-(se + we) as f1 f2, f2 = 1 unless 2^-t is not a normal float
+        // (t in [-226, 252])
+        const int t = sexp + a.wexp;
+        const int t1 = (t >= -126 && t <= 126) ? t : t / 2;
+        const float f1 = __uint_as_float((uint32_t)(127 - t1) << 23);
+        const float f2 = __uint_as_float((uint32_t)(127 - (t - t1)) << 23);
+        const bool two_step = t1 != t;
         for (int i = 0; i < iters && !*vfailed; ++i) {
             const int b = i & 1;
             const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
@@ -866,7 +895,11 @@ __global__ void __launch_bounds__(kT6Threads, 1)
                 tmem_wait_ld();
                 float v[32];
 #pragma unroll
-                for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(d[e]) * kUnscale;
+                for (int e = 0; e < 32; ++e) v[e] = __uint_as_float(d[e]) * f1;
+                if (two_step) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] *= f2;
+                }
                 if (q0_in_block) {
 #pragma unroll
                     for (int e = 0; e < 16; e += 2)
@@ -909,10 +942,7 @@ __global__ void __launch_bounds__(kT6Threads, 1)
         if (*vfailed && nd > 0) mbar_wait_bounded(&bar_d[(nd - 1) & 1], (uint32_t)(((nd - 1) >> 1) & 1));
     }
     __syncthreads();
-    if (tid == 0) {
-        if (*vfailed) atomicExch(status, SIM_ETIMEOUT);
-        else if (too_large) atomicCAS(status, 0, SIM_EUNSUPPORTED);
-    }
+    if (tid == 0 && *vfailed) atomicExch(status, SIM_ETIMEOUT);
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(taddr, NCOLS);
@@ -1465,6 +1495,48 @@ int resident_ctas(int dev, const void *fn, int threads, size_t dyn_smem)
     return std::min(by_regs, std::min(by_smem, by_thr));
 }
 
+// The spectral norm of one lowered gate as an operator on the register (a
+// controlled gate is the identity where a control is 0): an upper bound on
+// how much it can raise the state's norm.
+static double sgate_norm_bound(const SGate &g)
+{
+    const double *u = g.m;
+    const double f2 = u[0] * u[0] + u[1] * u[1] + u[2] * u[2] + u[3] * u[3] + u[4] * u[4] + u[5] * u[5] +
+                      u[6] * u[6] + u[7] * u[7];
+    // det = A D - B C
+    const double dr = (u[0] * u[6] - u[1] * u[7]) - (u[2] * u[4] - u[3] * u[5]);
+    const double di = (u[0] * u[7] + u[1] * u[6]) - (u[2] * u[5] + u[3] * u[4]);
+    // sigma_max^2 = (|G|_F^2 + sqrt(|G|_F^4 - 4 |det|^2)) / 2
+    const double disc = std::max(f2 * f2 - 4.0 * (dr * dr + di * di), 0.0);
+    const double sig = std::sqrt(0.5 * (f2 + std::sqrt(disc)));
+    return g.ctrl ? std::max(sig, 1.0) : sig;
+}
+
+// k = 6: the exponent we of the power-of-two scale of a block's W, and the
+// block's norm bound (every entry of U_blk = G_m ... G_1, and so of its real
+// form W, is at most the spectral norm of U_blk, which is at most the product
+// of its gates' spectral norms).  we = 14 - ceil(log2 bound) keeps |2^we W| <=
+// 2^14 (1 + 1e-6), far below the FP16 maximum; a unitary block gets 14.  we
+// lies in [kF16WExpMin, kF16WExpMax]; returns false when the bound is too
+// large (above 2^114) or not finite.
+static bool block_wexp(const std::vector<SGate> &g, const std::vector<int> &members, int *we, double *bound_out)
+{
+    double bound = 1.0;
+    for (int m : members) bound *= sgate_norm_bound(g[m]);
+    *bound_out = bound;
+    if (!std::isfinite(bound)) return false;
+    int eb = 0;
+    if (bound > 1.0 + 1e-6)
+        eb = (int)std::ceil(std::log2(bound / (1.0 + 1e-6)));
+    else if (bound < 1.0)
+        eb = bound > 0.0 ? std::max((int)std::ceil(std::log2(bound)), kF16WExp - kF16WExpMax)
+                         : kF16WExp - kF16WExpMax;
+    const int w = kF16WExp - eb;
+    if (w < kF16WExpMin) return false;
+    *we = std::min(w, kF16WExpMax);
+    return true;
+}
+
 // Plan and run the fused blocks in groups: each group of blocks is planned,
 // its gates uploaded, its W matrices built (one k_fuse_build launch) and its
 // applies launched; the host then plans the next group while the GPU works
@@ -1481,21 +1553,30 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
     const int n = s->n;
     const size_t ng = g.size();
     // per call: gate lists (<= ng FGates, <= 2 ng + 1 offsets), W slots (2 x kGroup blocks)
-    const size_t bytes_g = ng * sizeof(FGate), bytes_o = (2 * ng + 2) * sizeof(int);
+    const size_t bytes_g = ng * sizeof(FGate), bytes_o = (2 * ng + 2) * sizeof(int), bytes_e = (ng + 1) * sizeof(int);
     const size_t bytes_slot = kGroup * 2 * (size_t)K * K * sizeof(float);
-    const size_t o_g = 0, o_o = (bytes_g + 255) & ~(size_t)255, o_w = (o_o + bytes_o + 255) & ~(size_t)255;
+    const size_t o_g = 0, o_o = (bytes_g + 255) & ~(size_t)255, o_e = (o_o + bytes_o + 255) & ~(size_t)255,
+                 o_w = (o_e + bytes_e + 255) & ~(size_t)255;
     const size_t total = o_w + 2 * bytes_slot;
     if (int rc = ensure_host_pinned(&s->host_ops, &s->host_ops_bytes, o_w)) return rc;
     char *scratch = nullptr;
     QSIM_CUDA(cudaMallocAsync((void **)&scratch, total, s->stream));
     FGate *hg = (FGate *)((char *)s->host_ops + o_g);
     int *ho = (int *)((char *)s->host_ops + o_o);
+    int *he = (int *)((char *)s->host_ops + o_e);    // per block: W exponent (k = 6)
+    size_t be_used = 0;
+    double growth = 1.0;                             // k = 6: bound on norm^2 growth so far in this call
+    std::vector<double> bnd;                         // k = 6: per block of the group, its norm bound
     int rc = SIM_OK;
     do {
         if (cudaMemsetAsync(s->dev_status, 0, sizeof(int), s->stream) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "status reset");
             break;
         }
+        // k = 6: the state's norm^2 on the device (one pass over the state,
+        // overlapping the host's planning of the first group); the blocks
+        // derive their FP16 scale from it
+        if (KQ == 6 && (rc = reduce_norm_device(s)) != SIM_OK) break;
         // shared-memory limits and carveouts of the kernels this plan launches
         auto attrs = [](const void *fn, size_t dyn) {
             return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn) == cudaSuccess &&
@@ -1576,10 +1657,16 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
             // pad every block to KQ qubits (identity on the added ones): a block
             // of a pass pads with qubits of the pass's tile, others with the
             // lowest qubits; gates in block-local qubits
-            const size_t fg0 = fg_used, go0 = go_used;
+            const size_t fg0 = fg_used, go0 = go_used, be0 = be_used;
             std::vector<std::vector<int>> pos(blocks.size());
+            bnd.assign(blocks.size(), 1.0);
             ho[go_used++] = 0;
-            for (size_t bi = 0; bi < blocks.size(); ++bi) {
+            for (size_t bi = 0; bi < blocks.size() && rc == SIM_OK; ++bi) {
+                int we = kF16WExp;
+                if (KQ == 6 && !block_wexp(g, blocks[bi].members, &we, &bnd[bi]))
+                    rc = fail(SIM_EUNSUPPORTED, "fused apply, k = 6: the product of a block's gate norms is above "
+                                                "2^114 or not finite (beyond the range of its FP16 scale)");
+                he[be_used++] = we;
                 if (!blocks[bi].wide) {
                     uint64_t q = blocks[bi].qmask;
                     const uint64_t T = tileset[bi] ? tileset[bi] : (second[bi] ? tileset[bi - 1] : ~0ull);
@@ -1604,22 +1691,28 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
                 }
                 ho[go_used++] = (int)(fg_used - fg0);
             }
+            if (rc != SIM_OK) break;
             const size_t nb = blocks.size();
             FGate *dg = (FGate *)(scratch + o_g) + fg0;
             int *dgo = (int *)(scratch + o_o) + go0;
+            int *dge = (int *)(scratch + o_e) + be0;
             float *dw = (float *)(scratch + o_w + (size_t)slot * bytes_slot);
             if ((fg_used > fg0 && cudaMemcpyAsync(dg, hg + fg0, (fg_used - fg0) * sizeof(FGate), cudaMemcpyHostToDevice,
                                                   s->stream) != cudaSuccess) ||
-                cudaMemcpyAsync(dgo, ho + go0, (nb + 1) * sizeof(int), cudaMemcpyHostToDevice, s->stream) != cudaSuccess) {
+                cudaMemcpyAsync(dgo, ho + go0, (nb + 1) * sizeof(int), cudaMemcpyHostToDevice, s->stream) != cudaSuccess ||
+                (KQ == 6 &&
+                 cudaMemcpyAsync(dge, he + be0, nb * sizeof(int), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)) {
                 rc = cuda_fail(cudaGetLastError(), "fused upload");
                 break;
             }
             launch_begin(s, KC_FUSE_BUILD, (double)nb * 2 * K * K * sizeof(float));
-            k_fuse_build<KQ><<<(unsigned)(nb * kBuildSplit<KQ>), 256, smb, s->stream>>>(dg, dgo, dw);
+            k_fuse_build<KQ><<<(unsigned)(nb * kBuildSplit<KQ>), 256, smb, s->stream>>>(dg, dgo, dge, dw);
             if ((rc = launch_end(s, "fused build"))) break;
             for (size_t bi = 0; bi < nb && rc == SIM_OK; ++bi) {
                 if (blocks[bi].wide) {
                     rc = launch_sgate(s, g[blocks[bi].members[0]]);
+                    const double b = sgate_norm_bound(g[blocks[bi].members[0]]);
+                    growth *= b * b;
                     continue;
                 }
                 if constexpr (KQ == 5) {
@@ -1644,6 +1737,10 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
                 a.nq = KQ;
                 for (int i = 0; i < KQ; ++i) a.pos[i] = pos[bi][i];
                 a.rows = rows;
+                a.wexp = he[be0 + bi];
+                a.nrm2 = s->red_out;
+                a.growth = growth;
+                growth *= bnd[bi] * bnd[bi];
                 // tensor-core flops: three real GEMMs [rows x K] x [K x K] (3xTF32; k = 6: FP16 split)
                 launch_begin(s, KQ <= 5 ? KC_FUSED : KC_FUSED_F16, 2.0 * (double)s->bytes,
                              3.0 * 2.0 * (double)rows * K * K);
@@ -1664,9 +1761,7 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
     int hstatus = 0;
     QSIM_CUDA(cudaMemcpyAsync(&hstatus, s->dev_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
     QSIM_CUDA(cudaStreamSynchronize(s->stream));
-    if (rc == SIM_OK && hstatus == SIM_EUNSUPPORTED)
-        rc = fail(SIM_EUNSUPPORTED, "fused apply, k = 6: an amplitude has |a| >= 2 (the FP16 split needs a normalised state)");
-    else if (rc == SIM_OK && hstatus != 0)
+    if (rc == SIM_OK && hstatus != 0)
         rc = fail(SIM_ETIMEOUT, "fused apply: a tensor-core wait gave up");
     return rc;
 }

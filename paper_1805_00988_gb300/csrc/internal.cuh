@@ -135,6 +135,8 @@ int launch_pair_gate(qsim_state *s, const PairGate &g);
 enum RedMode { RED_NORM = 0, RED_BIT = 1, RED_EXPZ = 2 };
 int launch_init_basis(qsim_state *s, uint64_t j);
 int reduce_sums(qsim_state *s, int mode, int qubit, double out[2]);
+// sum_j |a_j|^2 into s->red_out[0] on the device, no host sync (stream-ordered)
+int reduce_norm_device(qsim_state *s);
 int launch_probabilities(qsim_state *s, void *dev_out, int out_real);
 int launch_collapse(qsim_state *s, int qubit, int outcome, double scale);
 int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);

@@ -898,6 +898,26 @@ int reduce_sums(qsim_state *s, int mode, int qubit, double out[2])
     return SIM_OK;
 }
 
+// sum_j |a_j|^2 into s->red_out[0] on the device (accumulated as for
+// sim_norm), for kernels that read it later in stream order; no host sync
+int reduce_norm_device(qsim_state *s)
+{
+    const uint64_t N = 1ull << s->n;
+    const uint64_t nvec = (s->dtype == SIM_C128) ? N : N / 2;
+    const uint64_t per = (nvec + kRedBlocks - 1) / kRedBlocks;
+    launch_begin(s, KC_REDUCE, (double)s->bytes);
+    if (s->dtype == SIM_C128)
+        k_masked_sum<double, RED_NORM><<<kRedBlocks, kRedThreads, 0, s->stream>>>((const double *)s->amps, nvec, per, 0,
+                                                                                  s->n, s->red_partial);
+    else
+        k_sum_sq32<RED_NORM><<<kRedBlocks, kRedThreads, 0, s->stream>>>((const float *)s->amps, nvec, per, 0,
+                                                                       s->red_partial);
+    if (int rc = launch_end(s, "norm pass")) return rc;
+    launch_begin(s, KC_REDUCE);
+    k_final_sum<<<1, kRedThreads, 0, s->stream>>>(s->red_partial, kRedBlocks, s->red_out);
+    return launch_end(s, "norm final sum");
+}
+
 int launch_probabilities(qsim_state *s, void *dev_out, int out_real)
 {
     const uint64_t N = 1ull << s->n;
