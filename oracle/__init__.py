@@ -3,9 +3,9 @@
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 ``bench.py``'s cpu_baseline / reference leg may import this package.  It
 shares no code with the CUDA library: the arithmetic lives in
-``qsim_oracle.c`` (plain C, FP64), compiled here with gcc; ``mlp.py`` and
-``fusion.py`` hold the numpy FP64 oracles of the cost model and of the fused
-block unitaries.
+``qsim_oracle.c`` (plain C, FP64), compiled here with gcc; ``mlp.py`` holds
+the numpy FP64 oracle of the cost model's network (forward, backward,
+Adam).
 
 States are numpy complex128 arrays of 2^n amplitudes (amplitude j <-> |j>,
 qubit t = bit t of j).  Gate lists are structured arrays with the fields of
@@ -76,6 +76,8 @@ def _load():
             lib.orc_infidelity.argtypes = [i32, P, P]
             lib.orc_infidelity.restype = f64
             lib.orc_num_threads.restype = i32
+            lib.orc_set_num_threads.argtypes = [i32]
+            lib.orc_set_num_threads.restype = None
             _lib = lib
     return _lib
 
@@ -93,6 +95,12 @@ def _nqubits(psi: np.ndarray) -> int:
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_num_threads(t: int) -> None:
+    """Threads of the oracle's per-gate loops from now on (results do not
+    depend on it; reductions are serial)."""
+    _load().orc_set_num_threads(int(t))
 
 
 def gate_matrix(name: str, params=(0.0, 0.0, 0.0), mat=None) -> np.ndarray:

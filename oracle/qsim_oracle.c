@@ -63,6 +63,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads the per-gate loops use from now on (t >= 1); for timing the same
+ * code on one core and on all cores.  Results do not depend on it. */
+void orc_set_num_threads(int t)
+{
+#ifdef _OPENMP
+    if (t >= 1) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}
+
 /* ------------------------------------------------------------------------
  * Gate matrices, out[8] = (A.re, A.im, B.re, B.im, C.re, C.im, D.re, D.im).
  * H, X, Y, Z, S, T follow the gate table in §1.3.2.  The paper does not

@@ -25,6 +25,8 @@ of the dense random / variational circuits the simulator is measured on):
     qft              textbook QFT (H + controlled phase, then qubit reversal)
     qft_paper        the App. A benchmark ordering (no final swaps)
     haar_cz          layers of Haar-random 1q unitaries + CZ on a random matching
+    phase_polynomial diagonal gates only (controlled phases, RZ, P, T, S, Z)
+    segments         consecutive stretches of the above (mixed circuits)
     variational      batched RY/RZ layers + CZ ring, uneven qubit counts
     bernstein_vazirani   the App. C worked example
 """
@@ -160,13 +162,62 @@ def qft(n: int, swaps: bool = True) -> np.ndarray:
 
 
 def qft_paper(n: int) -> np.ndarray:
-    """The benchmark circuit of App. A: for j = 0 .. n-1, for k < j a
-    controlled phase pi / 2^(j-k) on (j, k), then H(j); no final swaps."""
+    """The QFT benchmark circuit of §3 (App. A), built from the QFT's
+    structure (§2: a Hadamard per qubit, and between every pair of qubits
+    k < j a controlled phase of angle pi / 2^(j - k)): qubit j, taken from
+    qubit 0 upwards, first receives the phases it shares with each lower
+    qubit, then its Hadamard; no final swaps.  A controlled phase is
+    symmetric in its two qubits; here the higher qubit is the control.  The
+    circuit equals F P, the QFT of the bit-reversed input."""
+    pair_phase = {(k, j): math.pi / float(2 ** (j - k)) for j in range(n) for k in range(j)}
+    stages = [[gate("p", k, controls=(j,), params=(pair_phase[(k, j)],)) for k in range(j)] + [gate("h", j)]
+              for j in range(n)]
+    return concat([g for stage in stages for g in stage])
+
+
+def phase_polynomial(n: int, m: int, seed: int) -> np.ndarray:
+    """m diagonal gates (a phase polynomial, the shape of the cost layers of
+    QAOA and IQP circuits and of Trotterised ZZ couplings): each gate is,
+    with probability 1/2, a controlled phase P(theta) on a random pair of
+    qubits, else one of RZ(theta), P(theta), T, S, Z on a random qubit;
+    angles uniform in [0, 2 pi)."""
+    rng = np.random.default_rng(seed)
+    singles = ("rz", "p", "t", "s", "z")
+    g = empty(m)
+    for k in range(m):
+        qs = rng.permutation(n)
+        th = rng.uniform(0.0, 2.0 * math.pi)
+        if rng.random() < 0.5 and n >= 2:
+            g["name"][k] = "p"
+            g["target"][k] = qs[0]
+            g["nctrl"][k] = 1
+            g["ctrl"][k, 0] = qs[1]
+        else:
+            g["name"][k] = singles[int(rng.integers(0, len(singles)))]
+            g["target"][k] = qs[0]
+        g["params"][k, 0] = th
+    return g
+
+
+def segments(n: int, kinds, seg_gates: int, seed: int) -> np.ndarray:
+    """A circuit made of consecutive segments of about seg_gates gates each,
+    of the given kinds: "haar" (layers of haar_cz), "phase"
+    (phase_polynomial), "qft" (the textbook QFT, whatever its length),
+    "ladder" (layers of u3_cnot_ladder).  Circuits whose best plan differs
+    from one stretch of gates to the next."""
     parts = []
-    for j in range(n):
-        for k in range(j):
-            parts.append(gate("p", k, controls=(j,), params=(math.pi / float(2 ** (j - k)),)))
-        parts.append(gate("h", j))
+    for i, kind in enumerate(kinds):
+        sd = seed * 101 + i
+        if kind == "haar":
+            parts.append(haar_cz(n, max(1, round(seg_gates / (n + n // 2))), seed=sd))
+        elif kind == "phase":
+            parts.append(phase_polynomial(n, seg_gates, seed=sd))
+        elif kind == "qft":
+            parts.append(qft(n))
+        elif kind == "ladder":
+            parts.append(u3_cnot_ladder(n, max(1, round(seg_gates / (2 * n - 1))), seed=sd))
+        else:
+            raise ValueError(kind)
     return concat(parts)
 
 

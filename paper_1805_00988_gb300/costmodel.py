@@ -37,6 +37,7 @@ def families(n: int, seed: int):
     yield "u3_ladder", C.u3_cnot_ladder(n, 8, seed=seed)
     yield "variational", C.variational_layered(n, 8, rng)
     yield "random", C.random_gates(n, 12 * n, seed=seed)
+    yield "phase", C.phase_polynomial(n, 12 * n, seed=seed)
 
 
 def time_window(st, sg, opts, reps: int) -> float:

@@ -96,9 +96,12 @@ private:
     std::deque<Job *> q_;
 };
 
+// fixed at the first call, so the serial check below and the pool's size
+// always agree (and the planners' hot loops make no system call for it)
 int pool_threads()
 {
-    return (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+    static const int t = (int)std::min<unsigned>(std::max(1u, std::thread::hardware_concurrency()), 16u);
+    return t;
 }
 
 Pool *pool()

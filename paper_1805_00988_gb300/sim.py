@@ -118,6 +118,7 @@ def sim_create_from_buffer(n: int, dtype: int, dev_ptr: int, nbytes: int, stream
 
 def sim_destroy(h: int):
     check(_lib.sim_destroy(P(h)))
+    _COST_MODELS.pop(h, None)
 
 
 def sim_synchronize(h: int):
@@ -479,8 +480,18 @@ class MLP:
             pass
 
 
+# handle -> the MLP object its SIM_PLAN_LEARNED consults: the library keeps
+# only the pointer, so the binding holds the Python object (and with it the
+# model's device memory) until the handle is destroyed or given another model
+_COST_MODELS = {}
+
+
 def sim_set_cost_model(h: int, mlp):
     check(_lib.sim_set_cost_model(P(h), P(mlp.h if mlp is not None else None)))
+    if mlp is None:
+        _COST_MODELS.pop(h, None)
+    else:
+        _COST_MODELS[h] = mlp
 
 
 def sim_last_plan(h: int):

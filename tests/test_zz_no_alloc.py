@@ -32,13 +32,17 @@ def gsim():
     return S
 
 
-@pytest.mark.parametrize("dt,n", [("c64", 17), ("c128", 15), ("c64", 3)])
-def test_noalloc_norm_matches_sim_norm_twice(gsim, dt, n):
+@pytest.mark.parametrize("dt,n", [("c64", 17), ("c128", 15), ("c64", 3), ("c64", 23), ("c128", 22)])
+def test_noalloc_norm_matches_sim_norm_twice(gsim, orc, dt, n):
+    """n = 22, 23: thousands of amplitudes per block, so every thread of the
+    partial-sum kernel runs its strided loop many times.  Also against the
+    oracle's compensated FP64 sum of the same (copied) state."""
     lib = gsim.lib_handle()
     st = gsim.State(n, dt)
     st.apply(C.random_gates(n, 80, seed=n))
     st.synchronize()
     ref = st.norm2()
+    ref_orc = orc.norm2(st.state().astype(np.complex128))
     for _ in range(2):
         out = ctypes.c_double(-1.0)
         rc = lib.sim_norm_noalloc(ctypes.c_void_p(st.tensor.data_ptr()), n,
@@ -46,6 +50,7 @@ def test_noalloc_norm_matches_sim_norm_twice(gsim, dt, n):
                                   ctypes.c_void_p(st.stream_handle), ctypes.byref(out))
         assert rc == gsim.SIM_OK, gsim.last_error()
         assert abs(out.value - ref) <= 1e-12
+        assert abs(out.value - ref_orc) <= 1e-12
     st.close()
 
 
