@@ -52,12 +52,26 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # captures stay at a few GB on the device) and the traffic of a launch grows
 # with the state, so it is scaled by 2^n.
 TRAFFIC = {
-    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073939 GB + dram__bytes_write.sum 1.011877 GB
-    "fused_f16": {"bytes_per_amp": (1.073939e9 + 1.011877e9) / 2 ** 27,
-                  "source": "paper_1805_00988_gb300/csrc/fused.cu",
-                  "until": "// ------------------------------------------------------------------ multi-block passes",
-                  "sha256": "2b903a67ccabcbf3248544d5556cf98fb1556f434207a69508a6590ae46280c0"},
+    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073944 GB + dram__bytes_write.sum 1.011531 GB
+    "fused_f16": {"bytes_per_amp": (1.073944e9 + 1.011531e9) / 2 ** 27,
+                  "sources": [("paper_1805_00988_gb300/csrc/fused.cu",
+                               "// ------------------------------------------------------------------ multi-block passes"),
+                              ("paper_1805_00988_gb300/csrc/tc_ptx.cuh", None)],
+                  "sha256": "ac055de4a30559a8c0539d18eb91df83a28fb61a4d15871757f0a9cd80bc46e6"},
 }
+
+
+def source_digest(sources):
+    """SHA-256 over the kernel sources: each file up to its marker (the device
+    code; host code after it does not change a kernel's traffic)."""
+    import hashlib
+    h = hashlib.sha256()
+    for path, until in sources:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), path), "r") as f:
+            text = f.read()
+        cut = text.find(until) if until else -1
+        h.update(text[:cut if cut >= 0 else len(text)].encode())
+    return h.hexdigest()
 
 
 def max_over_ranks(x: float, world: int, device=None) -> float:
@@ -79,19 +93,12 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 
 
 def traffic_for(kind: str, n: int):
-    """DRAM bytes of one launch of the kernel class at n qubits, or None.
-    The hash covers the source file up to the marker `until` (the device code
-    of the kernels; the host planner after it does not change the traffic)."""
-    import hashlib
+    """DRAM bytes of one launch of the kernel class at n qubits, or None
+    when the kernel's sources changed since the capture."""
     t = TRAFFIC.get(kind)
-    if not t or t["bytes_per_amp"] is None or t["sha256"] is None:
+    if not t or t["bytes_per_amp"] is None:
         return None, None
-    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), t["source"])
-    with open(path, "r") as f:
-        text = f.read()
-    cut = text.find(t["until"])
-    digest = hashlib.sha256(text[:cut if cut >= 0 else len(text)].encode()).hexdigest()
-    if digest != t["sha256"]:
+    if t["sha256"] is None or source_digest(t["sources"]) != t["sha256"]:
         return None, "kernel source changed since the last ncu capture of its traffic"
     return t["bytes_per_amp"] * 2.0 ** n, "ncu capture of one 27-qubit launch, scaled by 2^(n-27)"
 
@@ -654,9 +661,15 @@ def run_extras(args, sim, C, dev, model):
     st = sim.State(n, "c64", device=dev)
     S = (2 ** n) * 8.0
     peaks, _ = load_peaks()
-    kinds = {"dense_H": (C.gate("h", 17), 2 * S), "cnot": (C.gate("x", 17, controls=(3,)), S),
-             "toffoli": (C.gate("x", 17, controls=(3, 25)), S / 2), "cz": (C.gate("z", 17, controls=(3,)), S / 2),
-             "swap": (C.gate("swap", 17, target2=3), S)}
+    kinds = {"dense_H": (C.gate("h", 17), 2 * S)}
+    # permutation and phase gates with the low qubit at 3, 8, 17 (target 12) and 25:
+    # a low qubit cuts the touched part of the state into runs of 2^q amplitudes
+    for c in (3, 8, 17, 25):
+        t = 12 if c == 17 else 17
+        kinds["cnot_c%d" % c] = (C.gate("x", t, controls=(c,)), S)
+        kinds["cz_c%d" % c] = (C.gate("z", t, controls=(c,)), S / 2)
+        kinds["swap_%d" % c] = (C.gate("swap", t, target2=c), S)
+        kinds["toffoli_c%d" % c] = (C.gate("x", t, controls=(c, 29 if c != 25 else 27)), S / 2)
     res = {}
     for name, (gate, alg) in kinds.items():
         sg = sim.to_sim_gates(gate)
@@ -679,10 +692,18 @@ def run_extras(args, sim, C, dev, model):
                             "note": "FP64 sum over the state + collapse pass, host round trip included"}
     out["gate_kernels_30q_c64"] = res
     st.close()
-    # batched variational circuits: 4096 circuits of 8..20 qubits, 4..12 layers, one graph launch
+    # batched variational circuits: 4096 circuits of 8..20 qubits, 4..12 layers, one graph launch;
+    # tile size and CTAs per SM from the autotuner (tuned here unless cached)
+    from paper_1805_00988_gb300 import autotune
     ns, offs, bg = C.variational(4096, 8, 20, 4, 12, seed=SEED)
+    wl = "variational4096_8-20q_4-12l_seed%d" % SEED
+    cached = autotune.batch_opts(wl)
+    tuned = None
+    if cached is None:
+        tuned = autotune.tune_batch(ns, offs, bg, wl, reps=2)
+        cached = (tuned["tile_qubits"], tuned["ctas_per_sm"])
     t0 = time.perf_counter()
-    b = sim.Batch(ns, offs, bg)
+    b = sim.Batch(ns, offs, bg, tile_qubits=cached[0], ctas_per_sm=cached[1])
     plan_s = time.perf_counter() - t0
     b.run()
     ts = []
@@ -690,13 +711,23 @@ def run_extras(args, sim, C, dev, model):
         t0 = time.perf_counter()
         b.run()
         ts.append(time.perf_counter() - t0)
-    info = b.info()
+    info, cfg = b.info(), b.config()
     b.close()
     tb = min(ts)
+    fl_peak = FP32_PEAK_TFLOPS
     out["batched_4096"] = {"ms": tb * 1e3, "circuits_per_s": 4096 / tb, "gates_per_s": len(bg) / tb,
                            "gates": int(len(bg)), "host_plan_s": plan_s, "work_items": info["items"],
-                           "persistent_ctas": info["grid"], "note": "wall time of sim_batch_run (graph launch + "
-                           "readback of 4096 <sum Z> values)"}
+                           "persistent_ctas": info["grid"], "tile_qubits": cfg["tile_qubits"],
+                           "ctas_per_sm": cfg["ctas_per_sm"],
+                           "autotune": tuned["all"] if tuned else "cached",
+                           "roofline": {"bound": "alu", "achieved": cfg["alg_flops"] / tb / 1e12, "peak": fl_peak,
+                                        "unit": "TFLOP/s", "frac": cfg["alg_flops"] / tb / 1e12 / fl_peak,
+                                        "alg_flops": cfg["alg_flops"],
+                                        "peak_source": "derived: 152 SMs x 128 FP32 FMA lanes x 2 flop x 2070 MHz",
+                                        "hbm": {"alg_scratch_bytes": cfg["alg_scratch_bytes"],
+                                                "achieved_GBps": cfg["alg_scratch_bytes"] / tb / 1e9,
+                                                "frac": cfg["alg_scratch_bytes"] / tb / 1e9 / peaks["hbm_gbs"]}},
+                           "note": "wall time of sim_batch_run (graph launch + readback of 4096 <sum Z> values)"}
     # 33 qubits, depth 24 (64 GiB complex64): learned plan vs the greedy tile planner, then 10^6 shots
     if args.c5:
         n5 = 33

@@ -114,7 +114,12 @@ typedef struct sim_plan_opts {
  *   the legacy default stream).
  * sim_create_from_buffer: wrap caller-owned device memory of at least
  *   2^n * sizeof(amplitude) bytes, 16-byte aligned; its contents are kept.
- * sim_destroy: free what the handle owns (not a wrapped buffer). */
+ * sim_destroy: free what the handle owns (not a wrapped buffer).
+ * The first handle created on a device sets that device's L2 fetch
+ * granularity hint for this process's CUDA context to 64 bytes
+ * (cudaLimitMaxL2FetchGranularity; it ends with the process): gates whose
+ * lowest control or target is qubit 3 touch 64-byte runs, and with the
+ * default the memory system fetched the unused half of every 128-byte line. */
 int sim_create(int n, int dtype, void *stream, sim_t *out);
 int sim_create_from_buffer(int n, int dtype, void *dev_ptr, size_t bytes, void *stream, sim_t *out);
 int sim_destroy(sim_t s);
@@ -191,6 +196,25 @@ int sim_expect_z_sum(sim_t s, double *out);
 typedef struct qsim_batch *sim_batch_t;
 int sim_batch_create(int count, const int32_t *n_qubits, const int64_t *gate_offsets, const sim_gate *gates,
                      void *stream, sim_batch_t *out);
+/* sim_batch_create_opts: as sim_batch_create, with the launch configuration
+ *   (no paper counterpart; the autotuner picks it per workload):
+ *   tile_qubits in {0, 11, 12, 13} (0 = 13): qubits per register tile (a
+ *   circuit of up to that many qubits lives in one CTA; larger ones run tile
+ *   passes over a scratch state); ctas_per_sm >= 0 (0 = as many as fit: two
+ *   with 13-qubit tiles, three with 11 or 12): persistent CTAs per SM.
+ *   SIM_EINVAL outside those ranges or above what fits.
+ * sim_batch_config: the configuration a batch uses, its algorithmic flops
+ *   (8 per complex multiply-add of the gates as given, summed over the
+ *   circuits) and the scratch-state bytes its plan must read and write per
+ *   run (any output may be NULL). */
+typedef struct sim_batch_opts {
+    int32_t tile_qubits;
+    int32_t ctas_per_sm;
+    int32_t reserved[2];     /* 0 */
+} sim_batch_opts;
+int sim_batch_create_opts(int count, const int32_t *n_qubits, const int64_t *gate_offsets, const sim_gate *gates,
+                          const sim_batch_opts *opts, void *stream, sim_batch_t *out);
+int sim_batch_config(sim_batch_t b, sim_batch_opts *used, double *alg_flops, double *alg_scratch_bytes);
 int sim_batch_run(sim_batch_t b, double *expz_out, int out_on_device);
 int sim_batch_info(sim_batch_t b, int64_t *items, int64_t *passes, int64_t *ops, int64_t *scratch_bytes, int *grid);
 int sim_batch_destroy(sim_batch_t b);

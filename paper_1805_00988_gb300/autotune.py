@@ -4,7 +4,10 @@
 11/12/13-qubit tiles, fused with k = 3..6) of a circuit on this GPU with CUDA
 events (best of ``reps`` after a warm run) and returns the fastest; results
 are cached in a JSON file keyed by "n/dtype/workload".  ``best_opts`` reads
-the cache.  Timing only: the library does all the work through the C ABI.
+the cache.  ``tune_batch`` does the same for a batch of small circuits: the
+persistent kernel's register-tile size (11, 12 or 13 qubits) and its CTAs
+per SM; ``batch_opts`` reads that choice back for sim.Batch.  Timing only:
+the library does all the work through the C ABI.
 """
 from __future__ import annotations
 
@@ -86,6 +89,47 @@ def tune(n: int, dtype: str, gates, workload: str, reps: int = 3, start_basis: i
     d[key(n, dtype, workload)] = res
     _store(d)
     return res
+
+
+BATCH_TILES = (11, 12, 13)
+
+
+def tune_batch(n_qubits, offsets, gates, workload: str, reps: int = 3, tiles=BATCH_TILES):
+    """Time one batch of circuits (sim_batch_run wall time, best of ``reps``
+    after a warm run) under every tile size and every CTA count per SM that
+    fits; cache and return {"tile_qubits", "ctas_per_sm", "ms", "all"}."""
+    import time
+    times = {}
+    for m in tiles:
+        per_sm = 1
+        while True:
+            try:
+                b = sim.Batch(n_qubits, offsets, gates, tile_qubits=m, ctas_per_sm=per_sm)
+            except sim.SimError:
+                break                      # more CTAs than fit on an SM
+            b.run()
+            best = None
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                b.run()
+                t = (time.perf_counter() - t0) * 1e3
+                best = t if best is None else min(best, t)
+            b.close()
+            times["%d/%d" % (m, per_sm)] = best
+            per_sm += 1
+    win = min(times, key=times.get)
+    m, per_sm = (int(x) for x in win.split("/"))
+    res = {"tile_qubits": m, "ctas_per_sm": per_sm, "ms": times[win], "all": times}
+    d = _load()
+    d["batch/" + workload] = res
+    _store(d)
+    return res
+
+
+def batch_opts(workload: str):
+    """Cached (tile_qubits, ctas_per_sm) of a batch workload, or None."""
+    r = _load().get("batch/" + workload)
+    return (r["tile_qubits"], r["ctas_per_sm"]) if r else None
 
 
 def best_opts(n: int, dtype: str, workload: str):

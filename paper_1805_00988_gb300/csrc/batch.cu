@@ -1,12 +1,13 @@
 // batch.cu -- many small circuits of uneven qubit counts in one persistent
 // launch, captured in a CUDA graph, returning <sum_i Z_i> per circuit.
 //
-// Every circuit is planned on the host like the staged plan (13-qubit tiles,
-// gates encoded per pass; adjacent single-qubit gates on the same qubit are
-// merged into one 2x2 first).  A circuit of at most 13 qubits is one tile: it
-// lives in the registers of one CTA from |0...0> to <Z> and never touches
-// global memory.  A larger circuit keeps its state in a scratch buffer and
-// runs pass after pass, each pass split into tiles.
+// Every circuit is planned on the host like the staged plan (M-qubit tiles,
+// M = 11, 12 or 13 per batch, chosen by the caller or the autotuner; gates
+// encoded per pass; adjacent single-qubit gates on the same qubit are merged
+// into one 2x2 first).  A circuit of at most M qubits is one tile: it lives in
+// the registers of one CTA from |0...0> to <Z> and never touches global
+// memory.  A larger circuit keeps its state in a scratch buffer and runs pass
+// after pass, each pass split into tiles.
 //
 // The launch is persistent: as many CTAs as fit on the GPU at once, each
 // taking work items (circuit, pass, tile) from a device queue in a host-built
@@ -32,7 +33,7 @@ namespace qsim {
 
 namespace {
 
-constexpr int kBM = 13;                 // tile qubits (complex64)
+constexpr int kBM = 13;                 // default tile qubits (complex64)
 constexpr unsigned long long kWaitNs = 1000000000ull;
 
 struct BCirc {
@@ -78,13 +79,15 @@ __global__ void k_batch_reset(BCtl *ctl, int *done, int64_t ndone, int *finished
     for (int64_t j = i; j < ncirc; j += stride) finished[j] = 0;
 }
 
-__global__ void __launch_bounds__(kThr, 2) k_batch(float2 *__restrict__ scratch, const BCirc *__restrict__ circs,
-                                                 const BPass *__restrict__ passes, const StOp<float> *__restrict__ ops,
-                                                 const BItem *__restrict__ items, int64_t nitems, BCtl *ctl,
-                                                 int *done, int *finished, double *__restrict__ partial,
-                                                 double *__restrict__ out)
+// tiles of up to 12 qubits fit three CTAs per SM (as the staged plan's),
+// 13-qubit tiles two
+template <int M>
+__global__ void __launch_bounds__(kThr, M <= 12 ? 3 : 2)
+    k_batch(float2 *__restrict__ scratch, const BCirc *__restrict__ circs, const BPass *__restrict__ passes,
+            const StOp<float> *__restrict__ ops, const BItem *__restrict__ items, int64_t nitems, BCtl *ctl, int *done,
+            int *finished, double *__restrict__ partial, double *__restrict__ out)
 {
-    constexpr int M = kBM, RB = M - kThrBits, RA = 1 << RB;
+    constexpr int RB = M - kThrBits, RA = 1 << RB;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *sm = reinterpret_cast<float *>(smem_raw);
     __shared__ long long cur;
@@ -103,7 +106,7 @@ __global__ void __launch_bounds__(kThr, 2) k_batch(float2 *__restrict__ scratch,
         const BItem it = items[cur];
         const BCirc c = circs[it.circ];
         const BPass &ps = passes[c.pass0 + it.pass];
-        const bool single = c.ntiles == 1 && c.npass == 1 && c.n <= kBM;
+        const bool single = c.ntiles == 1 && c.npass == 1 && c.n <= M;
 
         // wait for the previous pass of this circuit (bounded)
         if (it.pass > 0) {
@@ -124,22 +127,28 @@ __global__ void __launch_bounds__(kThr, 2) k_batch(float2 *__restrict__ scratch,
             if (stop) break;
         }
 
-        // tile base and I/O offsets (layout 0)
+        // tile base and I/O offsets (layout 0).  They are formed again after
+        // the gate sequence from inputs the compiler cannot prove equal
+        // instead of being held live across it (which spilled at two CTAs
+        // per SM), as in the staged kernel.
         uint64_t base = 0;
         for (int i = 0; i < ps.geo.n_outer; ++i) base |= ((uint64_t)(it.tile >> i) & 1ull) << ps.geo.outer_pos[i];
-        uint64_t toff = base;
+        uint64_t toff, roff[RB];
+        auto io_offsets = [&](const TileGeom &geo, int t, uint64_t b0) {
+            toff = b0;
 #pragma unroll
-        for (int i = 0; i < kThrBits; ++i) {
-            const int b = thr_local(M, RB, 2, 0, i);
-            const uint64_t g = (b < kLow) ? (1ull << b) : (1ull << ps.geo.hpos[b - kLow]);
-            if ((tid >> i) & 1) toff |= g;
-        }
-        uint64_t roff[RB];
+            for (int i = 0; i < kThrBits; ++i) {
+                const int b = thr_local(M, RB, 2, 0, i);
+                const uint64_t g = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
+                if ((t >> i) & 1) toff |= g;
+            }
 #pragma unroll
-        for (int j = 0; j < RB; ++j) {
-            const int b = reg_local(M, RB, 2, 0, j);
-            roff[j] = (b < kLow) ? (1ull << b) : (1ull << ps.geo.hpos[b - kLow]);
-        }
+            for (int j = 0; j < RB; ++j) {
+                const int b = reg_local(M, RB, 2, 0, j);
+                roff[j] = (b < kLow) ? (1ull << b) : (1ull << geo.hpos[b - kLow]);
+            }
+        };
+        io_offsets(ps.geo, tid, base);
         float *st = reinterpret_cast<float *>(scratch + c.state0);
 
         Regs<float, RA> v;
@@ -161,7 +170,14 @@ __global__ void __launch_bounds__(kThr, 2) k_batch(float2 *__restrict__ scratch,
         }
 
         apply_ops<float, M>(v, ops + ps.op0, ps.nops, base, tid, sm,
-                            reinterpret_cast<StOp<float> *>(smem_raw + ((size_t)1 << kBM) * 2 * sizeof(float)));
+                            reinterpret_cast<StOp<float> *>(smem_raw + ((size_t)1 << M) * 2 * sizeof(float)));
+        {
+            int t2 = tid;
+            uint64_t b2 = base;
+            const BPass *pp = passes + (c.pass0 + it.pass);
+            asm volatile("" : "+r"(t2), "+l"(b2), "+l"(pp));
+            io_offsets(pp->geo, t2, b2);
+        }
 
         if (it.pass + 1 < c.npass) {
 #pragma unroll
@@ -257,6 +273,8 @@ using namespace qsim;
 
 struct qsim_batch {
     int count = 0;
+    int tile_qubits = kBM, ctas_per_sm = 0;
+    double alg_flops = 0, alg_scratch_bytes = 0;
     cudaStream_t stream = nullptr;
     bool owns_stream = false;
     int grid = 0;
@@ -286,13 +304,30 @@ static void batch_free(qsim_batch *b)
     delete b;
 }
 
-extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_t *gate_offsets,
-                                const sim_gate *gates, void *stream, qsim_batch **out)
+namespace {
+
+template <int M>
+const void *batch_kernel() { return (const void *)k_batch<M>; }
+
+const void *batch_kernel_for(int M)
+{
+    return M == 11 ? batch_kernel<11>() : M == 12 ? batch_kernel<12>() : batch_kernel<13>();
+}
+
+}  // namespace
+
+extern "C" int sim_batch_create_opts(int count, const int32_t *n_qubits, const int64_t *gate_offsets,
+                                     const sim_gate *gates, const sim_batch_opts *opts, void *stream,
+                                     qsim_batch **out)
 {
     set_error("");
     if (!out || count <= 0 || !n_qubits || !gate_offsets || (gate_offsets[count] > 0 && !gates))
         return fail(SIM_EINVAL, "sim_batch_create: bad arguments");
     *out = nullptr;
+    const int M = (opts && opts->tile_qubits) ? opts->tile_qubits : kBM;
+    const int want_per_sm = opts ? opts->ctas_per_sm : 0;
+    if (M < 11 || M > 13) return fail(SIM_EINVAL, "sim_batch_create: tile_qubits must be 0 or 11..13");
+    if (want_per_sm < 0) return fail(SIM_EINVAL, "sim_batch_create: ctas_per_sm must be >= 0");
     for (int c = 0; c < count; ++c) {
         if (n_qubits[c] < 1 || n_qubits[c] > 24) return fail(SIM_EINVAL, "sim_batch_create: qubit counts must be 1..24");
         if (gate_offsets[c + 1] < gate_offsets[c]) return fail(SIM_EINVAL, "sim_batch_create: offsets must not decrease");
@@ -309,23 +344,28 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
     std::vector<BPass> passes;
     std::vector<StOp<float>> ops;
     int64_t state_amps = 0, parts = 0;
+    double alg_flops = 0, alg_scratch = 0;
     for (int c = 0; c < count; ++c) {
         const int n = n_qubits[c];
         std::vector<SGate> g;
         lower_gates(gates + gate_offsets[c], (size_t)(gate_offsets[c + 1] - gate_offsets[c]), &g);
+        for (const SGate &sg : g) alg_flops += sgate_flops(sg, n);
         merge_single_qubit(&g);
-        const int nplan = std::max(n, kBM);         // below 13 qubits: phantom qubits that stay |0>
-        std::vector<Pass> ps = form_passes(g, nplan, kBM);
+        const int nplan = std::max(n, M);           // below M qubits: phantom qubits that stay |0>
+        std::vector<Pass> ps = form_passes(g, nplan, M);
         if (ps.empty()) {
             Pass empty_pass;
-            for (int q = kLow; q < kBM; ++q) empty_pass.high.push_back(q);
+            for (int q = kLow; q < M; ++q) empty_pass.high.push_back(q);
             ps.push_back(empty_pass);
         }
-        PlanBuilder<float> pb{nplan, kBM, kBM - kThrBits, 2, {}, {}, 0};
+        // scratch traffic the plan must make: every pass but the first reads
+        // the state, every pass but the last writes it (8 B per amplitude)
+        if (ps.size() > 1) alg_scratch += 2.0 * (double)(ps.size() - 1) * std::ldexp(8.0, nplan);
+        PlanBuilder<float> pb{nplan, M, M - kThrBits, 2, {}, {}, 0};
         BCirc bc{};
         bc.n = n;
         bc.npass = (int)ps.size();
-        bc.ntiles = 1 << (nplan - kBM);
+        bc.ntiles = 1 << (nplan - M);
         bc.pass0 = (int64_t)passes.size();
         bc.part0 = parts;
         bc.state0 = 0;
@@ -369,6 +409,9 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
 
     qsim_batch *b = new qsim_batch();
     b->count = count;
+    b->tile_qubits = M;
+    b->alg_flops = alg_flops;
+    b->alg_scratch_bytes = alg_scratch;
     b->nitems = (int64_t)items.size();
     b->npasses = (int64_t)passes.size();
     b->nops = (int64_t)ops.size();
@@ -419,13 +462,14 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
             rc = cuda_fail(cudaGetLastError(), "sim_batch_create: upload");
             break;
         }
-        const size_t smem = ((size_t)1 << kBM) * 2 * sizeof(float) + op_stage_bytes<float>();
-        if (cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        const void *kern = batch_kernel_for(M);
+        const size_t smem = ((size_t)1 << M) * 2 * sizeof(float) + op_stage_bytes<float>();
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "batch smem attribute");
             break;
         }
-        // two CTAs per SM (128 registers a thread, 70 KB of shared memory each)
-        if (cudaFuncSetAttribute(k_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+        // up to two (13-qubit tiles) or three CTAs per SM
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "batch carveout attribute");
             break;
@@ -433,13 +477,21 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch, kThr, smem) != cudaSuccess || per_sm < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThr, smem) != cudaSuccess || per_sm < 1) {
             rc = fail(SIM_ECUDA, "sim_batch_create: persistent kernel does not fit on an SM");
             break;
         }
-        // one persistent CTA per resident slot.  A wait only ever waits on
-        // items earlier in the queue (pass-major order), which CTAs already
-        // running hold, so progress does not depend on residency.
+        if (want_per_sm > per_sm) {
+            rc = fail(SIM_EINVAL, "sim_batch_create: ctas_per_sm " + std::to_string(want_per_sm) + " above the " +
+                                      std::to_string(per_sm) + " that fit on an SM with " + std::to_string(M) +
+                                      "-qubit tiles");
+            break;
+        }
+        if (want_per_sm > 0) per_sm = want_per_sm;
+        b->ctas_per_sm = per_sm;
+        // persistent CTAs, at most one per resident slot.  A wait only ever
+        // waits on items earlier in the queue (pass-major order), which CTAs
+        // already running hold, so progress does not depend on residency.
         b->grid = sms * per_sm;
         // capture reset + persistent launch in a graph
         cudaStream_t cs;
@@ -449,8 +501,15 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
         }
         cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
         k_batch_reset<<<64, 256, 0, cs>>>(b->ctl, b->done, b->npasses, b->finished, count);
-        k_batch<<<b->grid, kThr, smem, cs>>>(b->scratch, b->circs, b->passes, b->ops, b->items, b->nitems, b->ctl,
-                                            b->done, b->finished, b->partial, b->out);
+        if (M == 11)
+            k_batch<11><<<b->grid, kThr, smem, cs>>>(b->scratch, b->circs, b->passes, b->ops, b->items, b->nitems,
+                                                    b->ctl, b->done, b->finished, b->partial, b->out);
+        else if (M == 12)
+            k_batch<12><<<b->grid, kThr, smem, cs>>>(b->scratch, b->circs, b->passes, b->ops, b->items, b->nitems,
+                                                    b->ctl, b->done, b->finished, b->partial, b->out);
+        else
+            k_batch<13><<<b->grid, kThr, smem, cs>>>(b->scratch, b->circs, b->passes, b->ops, b->items, b->nitems,
+                                                    b->ctl, b->done, b->finished, b->partial, b->out);
         cudaError_t ce = cudaStreamEndCapture(cs, &b->graph);
         cudaStreamDestroy(cs);
         if (ce != cudaSuccess) {
@@ -467,6 +526,25 @@ extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_
         return rc;
     }
     *out = b;
+    return SIM_OK;
+}
+
+extern "C" int sim_batch_create(int count, const int32_t *n_qubits, const int64_t *gate_offsets,
+                                const sim_gate *gates, void *stream, qsim_batch **out)
+{
+    return sim_batch_create_opts(count, n_qubits, gate_offsets, gates, nullptr, stream, out);
+}
+
+extern "C" int sim_batch_config(qsim_batch *b, sim_batch_opts *used, double *alg_flops, double *alg_scratch_bytes)
+{
+    if (!b) return fail(SIM_EINVAL, "sim_batch_config: null batch");
+    if (used) {
+        memset(used, 0, sizeof *used);
+        used->tile_qubits = b->tile_qubits;
+        used->ctas_per_sm = b->ctas_per_sm;
+    }
+    if (alg_flops) *alg_flops = b->alg_flops;
+    if (alg_scratch_bytes) *alg_scratch_bytes = b->alg_scratch_bytes;
     return SIM_OK;
 }
 

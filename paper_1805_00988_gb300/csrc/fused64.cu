@@ -1,0 +1,522 @@
+// fused64.cu -- complex128 fused blocks on the tensor cores.
+//
+// A fused block is the product of its gates restricted to k qubits (§1.3.2:
+// U_t = I (x) ... (x) U (x) ... (x) I restricted to the block's qubits), applied
+// to the state as the real GEMM D = X W described in fused.cu.  For complex128
+// states the GEMM must be exact to FP64 level, and this GPU's FP64 pipe is
+// narrow, so the products run on the FP16 tensor cores as exact integer
+// arithmetic, after the error-free splitting of Ozaki, Ogita, Oishi and Rump
+// (2012), in the fixed-point form used on tensor cores by Mukunoki, Ozaki,
+// Ogita and Imamura (2020):
+//   - each row r of X (the 2^k amplitudes sharing all index bits outside the
+//     block, as 2^(k+1) reals) is written in fixed point relative to its
+//     largest component: |x| < 2^E_r, t = trunc(|x| 2^(49 - E_r)) < 2^49, and t
+//     is cut into kPlanes = 7 base-128 digits (0..127) carrying the sign of x;
+//   - each column n of W likewise relative to its largest entry (2^F_n);
+//   - a digit is an integer of at most 7 bits, exact in FP16, and a product
+//     of two is below 2^14; a K = 32 sum of them is below 2^19, and the
+//     products of digit i of X with digit j of W are summed per level
+//     l = i + j (at most 7 products per level, below 2^22), so every FP32
+//     accumulator holds an exact integer (the tensor core adds integers below
+//     2^24 without rounding);
+//   - levels l = 0..6 are kept (pairs with i + j >= 7 are dropped, a relative
+//     error of about 2^-49 of the row and column maxima), and the consumer
+//     forms sum_l D_l 128^(6 - l) exactly in 64-bit integers, then the FP64
+//     result T 2^(E_r + F_n - 56).
+// One MMA per digit plane i of X and K-step: A = plane i (128 rows x 16), B =
+// W's planes 0 .. 6 - i side by side (N = (7 - i) x 32), D = accumulator
+// columns of levels i .. 6, so levels accumulate in place: 14 MMAs per tile.
+//
+// k = 4 (K = N = 32 per level): two accumulators of 7 x 32 columns fit in
+// tensor memory, the seven digit planes of A in shared memory.
+//   warp 9: loads tile i (128 rows x 16 amplitudes, runs of >= 2 KB) into
+//       stage i mod 2 with bulk copies;
+//   warps 0-3: thread r turns row r into its exponent and digit planes (A
+//       buffer i mod 2, K-major FP16), once the MMAs of tile i - 2 are done;
+//   warp 8 (one thread): the 14 MMAs of tile i once A is written and
+//       accumulator i mod 2 has been drained (tile i - 2);
+//   warps 4-7: thread r reads row r's levels, forms the FP64 results and
+//       stores them to HBM.
+// Row exponents pass from converter to consumer through four shared-memory
+// slots with their own full / empty barriers.  Every wait is bounded; on a
+// timeout the kernel records SIM_ETIMEOUT, lets work in flight land (bounded
+// again), frees its tensor memory and returns.
+#include <cstring>
+
+#include <cuda_fp16.h>
+
+#include "internal.cuh"
+#include "tc_ptx.cuh"
+
+namespace qsim {
+
+namespace {
+
+constexpr int kQ64 = 4;                       // qubits per block
+constexpr int kD64 = 1 << kQ64;               // amplitudes per row
+constexpr int kK64 = 2 * kD64;                // reals per row: MMA K, and N per level
+constexpr int kPlanes = 7;                    // base-128 digits per operand
+constexpr int kRows64 = 128;                  // MMA M, rows per tile
+constexpr int kTB64 = kQ64 + 7;               // tile bits
+constexpr int kTAmp64 = 1 << kTB64;           // amplitudes per tile
+constexpr int kT64Threads = 320;
+constexpr uint32_t kPlaneB = (uint32_t)kK64 * kK64 * 2;            // one W plane: 32 x 32 halves
+constexpr uint32_t kAPlaneB = (uint32_t)kRows64 * kK64 * 2;         // one A plane: 128 x 32 halves
+constexpr uint32_t kSlot64 = kPlanes * kPlaneB + kK64 * sizeof(int); // per block: W planes + column exponents
+constexpr int kSe64 = 4;                      // row-exponent slots
+
+struct FGate64 {                              // a gate in block-local qubits (the host's block-gate layout)
+    int32_t target;
+    uint32_t ctrl;
+    double m[8];
+};
+
+struct Apply64 {
+    int pos[kQ64];                            // global qubits of the block, ascending
+};
+
+__device__ __forceinline__ void mma_f16_ss(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// biased FP64 exponent of a component (0 for zero and subnormals, which are
+// taken as zero)
+__device__ __forceinline__ uint32_t bexp(double x) { return (uint32_t)(__double_as_longlong(x) >> 52) & 0x7FFu; }
+
+// |x| in fixed point relative to emax (|x| < 2^(emax - 1022)): trunc(|x| 2^(49 - E)), below 2^49
+__device__ __forceinline__ uint64_t fixed49(double x, uint32_t emax)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+    if (e == 0) return 0;
+    const uint32_t sh = emax - e + 4u;        // >= 4
+    const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    return sh < 64 ? (m >> sh) : 0ull;
+}
+
+// digit i (0 = most significant) of a 49-bit fixed-point value
+__device__ __forceinline__ uint32_t digit(uint64_t t, int i) { return (uint32_t)(t >> (42 - 7 * i)) & 127u; }
+
+// the same from the value's two 32-bit parts th = t >> 28 (digits 0..2) and
+// tl = t mod 2^28 (digits 3..6): one bit-field extract per digit
+__device__ __forceinline__ uint32_t digit2(uint32_t th, uint32_t tl, int i)
+{
+    return i < 3 ? (th >> (14 - 7 * i)) & 127u : (tl >> (21 - 7 * (i - 3))) & 127u;
+}
+
+// two digits (< 1024) as an FP16 pair with the given signs: 1024 + d is exact
+// in FP16 with mantissa d, and subtracting 1024 leaves d exactly
+__device__ __forceinline__ uint32_t digits_h2(uint32_t dlo, uint32_t dhi, uint32_t slo, uint32_t shi)
+{
+    const uint32_t w = 0x64006400u | dlo | (dhi << 16);
+    __half2 h = *reinterpret_cast<const __half2 *>(&w);
+    h = __hsub2(h, __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
+    return *reinterpret_cast<const uint32_t *>(&h) ^ ((slo << 15) | (shi << 31));
+}
+
+// ------------------------------------------------------------------ builder
+// U = G_m ... G_1 in FP64 (columns evolved from the identity), then its real
+// form W (fused.cu's convention), each column n in fixed point relative to
+// its largest entry, cut into kPlanes digit planes in the 16-bit K-major
+// B-operand layout ([plane][n][kk], plane j as rows 32 j .. 32 j + 31), and the
+// columns' biased exponents after the planes.  One CTA per block.
+__global__ void __launch_bounds__(256) k_fuse_build64(const FGate64 *__restrict__ gates, const int *__restrict__ goff,
+                                                      unsigned char *__restrict__ bout)
+{
+    constexpr int D = kD64, K = kK64;
+    __shared__ double2 U[D][D];               // U[i][c]: row i, column c
+    __shared__ uint32_t cmax[K];
+    const int blk = blockIdx.x, tid = threadIdx.x;
+    for (int e = tid; e < D * D; e += 256) U[e / D][e % D] = make_double2((e / D) == (e % D) ? 1.0 : 0.0, 0.0);
+    if (tid < K) cmax[tid] = 0;
+    __syncthreads();
+    for (int g = goff[blk]; g < goff[blk + 1]; ++g) {
+        const int t = gates[g].target;
+        const uint32_t cm = gates[g].ctrl;
+        const double ar = gates[g].m[0], ai = gates[g].m[1], br = gates[g].m[2], bi = gates[g].m[3];
+        const double cr = gates[g].m[4], ci = gates[g].m[5], dr = gates[g].m[6], di = gates[g].m[7];
+        for (int e = tid; e < D * (D / 2); e += 256) {
+            const int c = e / (D / 2), p = e % (D / 2);
+            const int i0 = ((p >> t) << (t + 1)) | (p & ((1 << t) - 1));
+            if (((uint32_t)i0 & cm) != cm) continue;
+            const int i1 = i0 | (1 << t);
+            const double2 a = U[i0][c], b = U[i1][c];
+            U[i0][c] = make_double2(ar * a.x - ai * a.y + br * b.x - bi * b.y, ar * a.y + ai * a.x + br * b.y + bi * b.x);
+            U[i1][c] = make_double2(cr * a.x - ci * a.y + dr * b.x - di * b.y, cr * a.y + ci * a.x + dr * b.y + di * b.x);
+        }
+        __syncthreads();
+    }
+    // W[kk][n]: input kk = 2 j + a, output n = 2 i + b
+    auto wval = [&](int n, int kk) {
+        const int i = n >> 1, b = n & 1, j = kk >> 1, a = kk & 1;
+        const double2 u = U[i][j];
+        return (a == b) ? u.x : (a == 1 ? -u.y : u.y);
+    };
+    for (int e = tid; e < K * K; e += 256) atomicMax(&cmax[e / K], bexp(wval(e / K, e % K)));
+    __syncthreads();
+    unsigned char *out = bout + (size_t)blk * kSlot64;
+    for (int e = tid; e < K * K; e += 256) {
+        const int n = e / K, kk = e % K;
+        const double w = wval(n, kk);
+        const uint64_t t = fixed49(w, cmax[n]);
+        const uint32_t sgn = (uint32_t)((uint64_t)__double_as_longlong(w) >> 63);
+        for (int p = 0; p < kPlanes; ++p) {
+            const uint32_t h = digits_h2(digit(t, p), 0u, sgn, 0u) & 0xFFFFu;
+            *reinterpret_cast<uint16_t *>(out + kmajor16_off((uint32_t)(p * K + n), (uint32_t)kk, K)) = (uint16_t)h;
+        }
+    }
+    if (tid < K) reinterpret_cast<int *>(out + kPlanes * kPlaneB)[tid] = (int)cmax[tid];
+}
+
+// ------------------------------------------------------------------ apply
+__global__ void __launch_bounds__(kT64Threads, 1)
+    k_fused_c128(double *__restrict__ st, const unsigned char *__restrict__ bblk, Apply64 a, uint64_t ntiles,
+                 int *__restrict__ status)
+{
+    constexpr int D = kD64, K = kK64, TB = kTB64, TAMP = kTAmp64;
+    constexpr uint32_t TBYTES = (uint32_t)TAMP * 16u;
+    constexpr uint32_t NCOLS = 512, ACC = 256;          // accumulator b at column 256 b (7 x 32 used)
+    constexpr uint32_t SBO = (K / 8) * 128;             // 8-row group stride of a 16-bit K-major operand
+
+    extern __shared__ __align__(1024) unsigned char smem[];
+    double2 *stage = reinterpret_cast<double2 *>(smem);                          // 2 x TAMP amplitudes
+    unsigned char *abuf = smem + 2 * (size_t)TBYTES;                              // 2 x 7 planes x 128 x 32 halves
+    unsigned char *wsm = abuf + 2 * (size_t)kPlanes * kAPlaneB;                   // 7 planes x 32 x 32 halves
+    __shared__ uint64_t bar_full[2], bar_empty[2], bar_a[2], bar_d[2], bar_e[2], bar_sf[kSe64], bar_se[kSe64];
+    __shared__ uint32_t rowexp[kSe64][kRows64];
+    __shared__ int colexp[K];
+    __shared__ uint32_t tslot;
+    __shared__ int tpos[TB];
+    __shared__ uint64_t pmask;
+    __shared__ int lrun;
+    __shared__ uint32_t uc[D];
+    __shared__ uint64_t gc[D];
+    __shared__ int failed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        failed = *reinterpret_cast<volatile int *>(status);
+        uint64_t pm = 0;
+        for (int i = 0; i < kQ64; ++i) pm |= 1ull << a.pos[i];
+        uint64_t tm = pm;
+        for (int b = 0, cnt = 0; cnt < 7; ++b)
+            if (!((pm >> b) & 1)) { tm |= 1ull << b; ++cnt; }
+        for (int b = 0, j = 0; j < TB; ++b)
+            if ((tm >> b) & 1) tpos[j++] = b;
+        int L = 0;
+        while (L < TB && tpos[L] == L) ++L;
+        lrun = L;
+        pmask = pm;
+    }
+    __syncthreads();
+    if (failed) return;
+    if (warp == 0) tmem_alloc(&tslot, NCOLS);
+    if (tid == 0) {
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&bar_full[b], 1);
+            mbar_init(&bar_empty[b], kRows64);
+            mbar_init(&bar_a[b], kRows64);
+            mbar_init(&bar_d[b], 1);
+            mbar_init(&bar_e[b], kRows64);
+        }
+        for (int q = 0; q < kSe64; ++q) {
+            mbar_init(&bar_sf[q], kRows64);
+            mbar_init(&bar_se[q], kRows64);
+        }
+    }
+    for (int c = tid; c < D; c += kT64Threads) {
+        uint32_t u = 0;
+        uint64_t g = 0;
+        for (int i = 0; i < kQ64; ++i)
+            if ((c >> i) & 1) {
+                g |= 1ull << a.pos[i];
+                for (int j = 0; j < TB; ++j)
+                    if (tpos[j] == a.pos[i]) u |= 1u << j;
+            }
+        uc[c] = u;
+        gc[c] = g;
+    }
+    {
+        const uint4 *src = reinterpret_cast<const uint4 *>(bblk);
+        uint4 *dst = reinterpret_cast<uint4 *>(wsm);
+        for (int e = tid; e < (int)(kPlanes * kPlaneB / 16); e += kT64Threads) dst[e] = __ldg(src + e);
+        if (tid < K) colexp[tid] = reinterpret_cast<const int *>(bblk + kPlanes * kPlaneB)[tid];
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = tslot;
+    volatile int *vfailed = &failed;
+    const uint64_t step = gridDim.x;
+    const int iters = ((uint64_t)blockIdx.x < ntiles) ? (int)((ntiles - 1 - blockIdx.x) / step + 1) : 0;
+
+    auto tile_base = [&](uint64_t t) {
+        uint64_t b = t;
+#pragma unroll
+        for (int j = 0; j < TB; ++j) {
+            const int p = tpos[j];
+            b = ((b >> p) << (p + 1)) | (b & ((1ull << p) - 1ull));
+        }
+        return b;
+    };
+    auto row_offsets = [&](int r, uint32_t &u, uint64_t &g) {
+        u = 0;
+        g = 0;
+        const uint64_t pm = pmask;
+        for (int j = 0, i = 0; j < TB; ++j) {
+            const int p = tpos[j];
+            if ((pm >> p) & 1) continue;
+            if ((r >> i) & 1) {
+                u |= 1u << j;
+                g |= 1ull << p;
+            }
+            ++i;
+        }
+    };
+
+    if (warp == 9) {
+        // loader: lane j copies run j of every tile (T holds qubits 0..6, so
+        // runs are >= 128 amplitudes and a tile has at most 16 of them)
+        const int L = lrun;
+        const int nrun = 1 << (TB - L);
+        const uint32_t rbytes = 16u << L;
+        int issued = 0;
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int s = i & 1;
+            if (i >= 2 && !mbar_wait_bounded(&bar_empty[s], (uint32_t)(((i - 2) >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step);
+            if (lane == 0) mbar_arrive_expect_tx(&bar_full[s], TBYTES);
+            __syncwarp();
+            for (int rr = lane; rr < nrun; rr += 32) {
+                uint64_t go = 0;
+                for (int b = 0; b < TB - L; ++b)
+                    if ((rr >> b) & 1) go |= 1ull << tpos[L + b];
+                bulk_load(stage + (size_t)s * TAMP + ((size_t)rr << L), st + 2 * (base | go), rbytes, &bar_full[s]);
+            }
+            issued = i + 1;
+        }
+        if (lane == 0)
+            for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
+                mbar_wait_bounded(&bar_full[i & 1], (uint32_t)((i >> 1) & 1));
+    } else if (warp < 4) {
+        // converters: thread r = row r
+        uint32_t ur;
+        uint64_t gr;
+        row_offsets(tid, ur, gr);
+        const uint32_t arow = (((uint32_t)tid >> 3) * (K >> 3) << 7) + (((uint32_t)tid & 7) << 4);
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int s = i & 1, b = i & 1;
+            if (!mbar_wait_bounded(&bar_full[s], (uint32_t)((i >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            const double2 *sg = stage + (size_t)s * TAMP;
+            double2 v[D];
+#pragma unroll
+            for (int c = 0; c < D; ++c) v[c] = sg[ur | uc[c]];
+            mbar_arrive(&bar_empty[s]);
+            uint32_t emax = 0;
+#pragma unroll
+            for (int c = 0; c < D; ++c) emax = max(emax, max(bexp(v[c].x), bexp(v[c].y)));
+            // the row's exponent: slot i mod 4, once the consumer of tile i - 4 has read it
+            const int q = i % kSe64;
+            if (i >= kSe64 && !mbar_wait_bounded(&bar_se[q], (uint32_t)(((i - kSe64) / kSe64) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            rowexp[q][tid] = emax;
+            mbar_arrive(&bar_sf[q]);
+            // A buffer b: the MMAs of tile i - 2 must be done reading it
+            if (i >= 2 && !mbar_wait_bounded(&bar_d[b], (uint32_t)(((i - 2) >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            tc_fence_after();
+            unsigned char *ab = abuf + (size_t)b * kPlanes * kAPlaneB + arow;
+#pragma unroll
+            for (int g4 = 0; g4 < D / 4; ++g4) {
+                // complex columns 4 g4 .. 4 g4 + 3 = K-elements 8 g4 .. 8 g4 + 7: one 16-byte core-matrix row per plane
+                uint32_t w[kPlanes][4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const double2 x = v[4 * g4 + j];
+                    const uint64_t tr = fixed49(x.x, emax), ti = fixed49(x.y, emax);
+                    const uint32_t rh = (uint32_t)(tr >> 28), rl = (uint32_t)tr & 0xFFFFFFFu;
+                    const uint32_t ih = (uint32_t)(ti >> 28), il = (uint32_t)ti & 0xFFFFFFFu;
+                    const uint32_t sr = (uint32_t)((uint64_t)__double_as_longlong(x.x) >> 63);
+                    const uint32_t si = (uint32_t)((uint64_t)__double_as_longlong(x.y) >> 63);
+#pragma unroll
+                    for (int p = 0; p < kPlanes; ++p)
+                        w[p][j] = digits_h2(digit2(rh, rl, p), digit2(ih, il, p), sr, si);
+                }
+#pragma unroll
+                for (int p = 0; p < kPlanes; ++p)
+                    *reinterpret_cast<uint4 *>(ab + (size_t)p * kAPlaneB + ((uint32_t)g4 << 7)) =
+                        make_uint4(w[p][0], w[p][1], w[p][2], w[p][3]);
+            }
+            fence_async_smem();
+            tc_fence_before();
+            mbar_arrive(&bar_a[b]);
+        }
+    } else if (warp < 8) {
+        // consumers: warp w reads TMEM lanes 32 (w - 4) .. + 31 = rows of the tile
+        const int r = tid - 128;
+        uint32_t ur;
+        uint64_t gr;
+        row_offsets(r, ur, gr);
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int b = i & 1;
+            const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
+            if (!mbar_wait_bounded(&bar_d[b], (uint32_t)((i >> 1) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            const int q = i % kSe64;
+            if (!mbar_wait_bounded(&bar_sf[q], (uint32_t)((i / kSe64) & 1))) {
+                *vfailed = 1;
+                break;
+            }
+            const int er = (int)rowexp[q][r];
+            mbar_arrive(&bar_se[q]);
+            tc_fence_after();
+            const uint32_t lb = taddr + ACC * (uint32_t)b + ((uint32_t)((warp - 4) * 32) << 16);
+            // one chunk of 8 columns at a time (not unrolled: the consumer's
+            // code stays small next to the converters')
+#pragma unroll 1
+            for (int n0 = 0; n0 < K; n0 += 8) {
+                uint32_t d[kPlanes][8];
+#pragma unroll
+                for (int l = 0; l < kPlanes; ++l) tmem_ld8_nowait(lb + 32u * (uint32_t)l + (uint32_t)n0, d[l]);
+                tmem_wait_ld();
+                double o[8];
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    // exact integers below 2^22: the FP32 bits of D + 1.5 2^23 carry D in the mantissa
+                    int di[kPlanes];
+#pragma unroll
+                    for (int l = 0; l < kPlanes; ++l)
+                        di[l] = __float_as_int(__uint_as_float(d[l][e]) + 12582912.0f) - 0x4B400000;
+                    // sum_l D_l 128^(6 - l) in 64 bits, through exact 32-bit pairs
+                    const int64_t a01 = (int64_t)(di[0] * 128 + di[1]);
+                    const int64_t a23 = (int64_t)(di[2] * 128 + di[3]);
+                    const int64_t a45 = (int64_t)(di[4] * 128 + di[5]);
+                    const int64_t T = a01 * (1ll << 35) + a23 * (1ll << 21) + a45 * 128 + (int64_t)di[6];
+                    // T 2^(E_r + F_n - 56), E = biased exponent - 1022, rounded down to 53 bits
+                    const uint64_t mag = (uint64_t)(T < 0 ? -T : T);
+                    uint64_t bits = 0;
+                    if (mag != 0) {
+                        const int lz = __clzll((long long)mag);
+                        const int be = 1023 + (63 - lz) + er + colexp[n0 + e] - 2044 - 56;
+                        const uint64_t mant = ((mag << lz) >> 11) & 0xFFFFFFFFFFFFFull;
+                        if (be > 0) bits = ((uint64_t)be << 52) | mant;
+                        bits |= (uint64_t)(T < 0) << 63;
+                    }
+                    o[e] = __longlong_as_double((long long)bits);
+                }
+                // columns n0 .. n0 + 7 = complex columns n0 / 2 .. + 3
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    *reinterpret_cast<double2 *>(st + 2 * (base | gc[n0 / 2 + c])) = make_double2(o[2 * c], o[2 * c + 1]);
+            }
+            tc_fence_before();
+            mbar_arrive(&bar_e[b]);
+        }
+    } else if (warp == 8 && lane == 0) {
+        // issuer: digit plane p of A against W planes 0 .. 6 - p, into levels p .. 6
+        const uint32_t sw = smem_u32(wsm);
+        const uint32_t sa = smem_u32(abuf);
+        int nd = 0;
+        for (int i = 0; i < iters && !*vfailed; ++i) {
+            const int b = i & 1;
+            if (!mbar_wait_bounded(&bar_a[b], (uint32_t)((i >> 1) & 1))) { *vfailed = 1; break; }
+            if (i >= 2 && !mbar_wait_bounded(&bar_e[b], (uint32_t)(((i - 2) >> 1) & 1))) { *vfailed = 1; break; }
+            tc_fence_after();
+            const uint32_t d0 = taddr + ACC * (uint32_t)b;
+            const uint32_t a0 = sa + (uint32_t)b * kPlanes * kAPlaneB;
+#pragma unroll 1
+            for (int p = 0; p < kPlanes; ++p) {
+                const uint32_t idesc = make_idesc_f16(kRows64, (kPlanes - p) * K);
+#pragma unroll
+                for (int ks = 0; ks < K / 16; ++ks)
+                    mma_f16_ss(d0 + 32u * (uint32_t)p, make_desc(a0 + (uint32_t)p * kAPlaneB + 256u * ks, 128, SBO),
+                               make_desc(sw + 256u * ks, 128, SBO), idesc, (p | ks) != 0);
+            }
+            mma_commit(&bar_d[b]);
+            nd = i + 1;
+        }
+        if (*vfailed && nd > 0) mbar_wait_bounded(&bar_d[(nd - 1) & 1], (uint32_t)(((nd - 1) >> 1) & 1));
+    }
+    __syncthreads();
+    if (tid == 0 && *vfailed) atomicExch(status, SIM_ETIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(taddr, NCOLS);
+}
+
+constexpr size_t c128_smem_bytes()
+{
+    return 2 * (size_t)kTAmp64 * 16 + 2 * (size_t)kPlanes * kAPlaneB + (size_t)kPlanes * kPlaneB;
+}
+
+}  // namespace
+
+size_t fused_c128_slot_bytes() { return kSlot64; }
+
+int fused_c128_prepare(qsim_state *s, int *grid)
+{
+    const size_t smem = c128_smem_bytes();
+    if (cudaFuncSetAttribute((const void *)k_fused_c128, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute((const void *)k_fused_c128, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "complex128 fused kernel attributes");
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)k_fused_c128, kT64Threads, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        return fail(SIM_ECUDA, "fused apply: the complex128 kernel does not fit on an SM");
+    const uint64_t tiles = (1ull << s->n) / kTAmp64;
+    *grid = (int)std::min<uint64_t>(tiles, (uint64_t)s->num_sms);
+    return SIM_OK;
+}
+
+int launch_fuse_build_c128(qsim_state *s, const void *gates, const int *goff, int nb, void *out)
+{
+    static_assert(sizeof(FGate64) == 72, "block gate layout");
+    launch_begin(s, KC_FUSE_BUILD, (double)nb * kSlot64);
+    k_fuse_build64<<<(unsigned)nb, 256, 0, s->stream>>>((const FGate64 *)gates, goff, (unsigned char *)out);
+    return launch_end(s, "complex128 fused build");
+}
+
+int launch_fused_c128(qsim_state *s, const void *block, const int *pos, int grid)
+{
+    Apply64 a{};
+    for (int i = 0; i < kQ64; ++i) a.pos[i] = pos[i];
+    const uint64_t tiles = (1ull << s->n) / kTAmp64;
+    // tensor-core work: 14 MMAs of 128 x 16 x (7 - p) 32 per tile
+    const double flops = (double)tiles * 2.0 * kRows64 * 16.0 * 32.0 * 2.0 * (7 + 6 + 5 + 4 + 3 + 2 + 1);
+    launch_begin(s, KC_FUSED_C128, 2.0 * (double)s->bytes, flops);
+    k_fused_c128<<<(unsigned)grid, kT64Threads, c128_smem_bytes(), s->stream>>>((double *)s->amps,
+                                                                                 (const unsigned char *)block, a,
+                                                                                 tiles, s->dev_status);
+    return launch_end(s, "complex128 fused apply");
+}
+
+}  // namespace qsim

@@ -45,6 +45,7 @@ enum KernelClass {
     KC_MLP,          // cost-model forward / backward / Adam
     KC_FUSED_MULTI,  // several fused blocks applied per pass over the state
     KC_FUSED_F16,    // fused 6-qubit unitary apply on FP16-split operands
+    KC_FUSED_C128,   // fused 4-qubit unitary apply to complex128 states on integer digit planes
     KC_COUNT
 };
 const char *kernel_class_name(int k);
@@ -137,6 +138,15 @@ int launch_init_basis(qsim_state *s, uint64_t j);
 int reduce_sums(qsim_state *s, int mode, int qubit, double out[2]);
 // sum_j |a_j|^2 into s->red_out[0] on the device, no host sync (stream-ordered)
 int reduce_norm_device(qsim_state *s);
+
+// complex128 fused blocks of 4 qubits (fused64.cu): bytes of one block's
+// slot (W digit planes + column exponents), kernel set-up (grid), the build
+// of nb blocks' slots from their gate lists (block-local gates, 72 bytes
+// each, offsets goff[0..nb]), and one block's apply
+size_t fused_c128_slot_bytes();
+int fused_c128_prepare(qsim_state *s, int *grid);
+int launch_fuse_build_c128(qsim_state *s, const void *gates, const int *goff, int nb, void *out);
+int launch_fused_c128(qsim_state *s, const void *block, const int *pos, int grid);
 int launch_probabilities(qsim_state *s, void *dev_out, int out_real);
 int launch_collapse(qsim_state *s, int qubit, int outcome, double scale);
 int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);

@@ -344,7 +344,14 @@ class State:
 
 
 # ---------------------------------------------------------------- batches
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("tile_qubits", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+
+
 _sig("sim_batch_create", [_i32, P, P, P, P, ctypes.POINTER(P)])
+_sig("sim_batch_create_opts", [_i32, P, P, P, ctypes.POINTER(BatchOpts), P, ctypes.POINTER(P)])
+_sig("sim_batch_config", [P, ctypes.POINTER(BatchOpts), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_double)])
 _sig("sim_batch_run", [P, P, _i32])
 _sig("sim_batch_info", [P, P, P, P, P, P])
 _sig("sim_batch_destroy", [P])
@@ -352,17 +359,28 @@ _sig("sim_batch_destroy", [P])
 
 class Batch:
     """Many independent circuits, each from |0...0>, returning <sum_i Z_i>
-    per circuit (one persistent launch replayed from a CUDA graph)."""
+    per circuit (one persistent launch replayed from a CUDA graph).
+    tile_qubits (11..13, 0 = 13) and ctas_per_sm (0 = as many as fit) set the
+    launch configuration (sim_batch_create_opts)."""
 
-    def __init__(self, n_qubits, offsets, gates, stream: int = 0):
+    def __init__(self, n_qubits, offsets, gates, stream: int = 0, tile_qubits: int = 0, ctas_per_sm: int = 0):
         self.n = np.ascontiguousarray(n_qubits, dtype=np.int32)
         self.offsets = np.ascontiguousarray(offsets, dtype=np.int64)
         sg = np.ascontiguousarray(to_sim_gates(gates) if gates.dtype != SIM_GATE_DTYPE else gates,
                                   dtype=SIM_GATE_DTYPE)
         h = P()
-        check(_lib.sim_batch_create(len(self.n), self.n.ctypes.data_as(P), self.offsets.ctypes.data_as(P),
-                                    sg.ctypes.data_as(P), P(stream or CUDA_STREAM_LEGACY), ctypes.byref(h)))
+        o = BatchOpts(int(tile_qubits), int(ctas_per_sm))
+        check(_lib.sim_batch_create_opts(len(self.n), self.n.ctypes.data_as(P), self.offsets.ctypes.data_as(P),
+                                         sg.ctypes.data_as(P), ctypes.byref(o), P(stream or CUDA_STREAM_LEGACY),
+                                         ctypes.byref(h)))
         self.h = h.value
+
+    def config(self):
+        o = BatchOpts()
+        fl, sb = ctypes.c_double(), ctypes.c_double()
+        check(_lib.sim_batch_config(P(self.h), ctypes.byref(o), ctypes.byref(fl), ctypes.byref(sb)))
+        return {"tile_qubits": o.tile_qubits, "ctas_per_sm": o.ctas_per_sm, "alg_flops": fl.value,
+                "alg_scratch_bytes": sb.value}
 
     def run(self) -> np.ndarray:
         out = np.zeros(len(self.n), dtype=np.float64)

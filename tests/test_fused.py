@@ -158,10 +158,12 @@ def test_fused_haar_cz_20q(gsim, orc, k):
 
 
 @pytest.mark.gpu
-def test_fused_rejects_c128_and_small(gsim):
+def test_fused_rejects_c128_k5_and_small(gsim):
+    """complex128 runs 4-qubit blocks only (tests/test_fused_c128.py); a
+    register below k + 7 qubits has no full tile."""
     st = gsim.State(12, "c128")
     with pytest.raises(gsim.SimError) as e:
-        st.apply(C.qft(12), plan="fused", fuse_k=4)
+        st.apply(C.qft(12), plan="fused", fuse_k=5)
     assert e.value.status == gsim.SIM_EUNSUPPORTED
     st.close()
     st = gsim.State(9, "c64")
