@@ -580,6 +580,18 @@ def run_variants(args, sim, C, gates, sg, dev, st_c64, peaks):
     out["per_gate_c128"] = {"ms": t128, "gates_per_s": len(gates) / (t128 / 1e3), "infidelity": 0.0,
                             "note": ("reference state for the complex64 infidelities (equal to the FP64 oracle's "
                                      "state within 1e-12 infidelity at 30 qubits: tests/test_fullsize.py)")}
+    # complex128 through the tensor cores: 4-qubit fused blocks of exact
+    # integer digit products (what the learned plan runs for complex128)
+    st128 = sim.State(args.qubits, "c128", device=dev)
+    try:
+        t = timed(st128, sim.plan_opts("fused", fuse_k=4), 2)
+        out["fused:4_c128"] = {"ms": t, "gates_per_s": len(gates) / (t / 1e3),
+                               "infidelity": infidelity_torch(st128.tensor, ref.tensor),
+                               "max_abs_diff": float((st128.tensor - ref.tensor).abs().max().item()),
+                               "speedup_vs_per_gate_c128": t128 / t}
+    except sim.SimError as e:
+        out["fused:4_c128"] = {"error": str(e)}
+    st128.close()
     for spec in args.variant_plans:
         plan, _, num = spec.partition(":")
         try:
@@ -624,8 +636,10 @@ def run_extras(args, sim, C, dev, model):
     for dt in ("c64", "c128"):
         st = sim.State(n, dt, device=dev)
         res = {}
-        for plan in ("per_gate", "staged"):
-            o = sim.plan_opts(plan)
+        plans = [("per_gate", sim.plan_opts("per_gate")), ("staged", sim.plan_opts("staged"))]
+        if dt == "c128":
+            plans.append(("fused:4", sim.plan_opts("fused", fuse_k=4)))
+        for plan, o in plans:
 
             def run():
                 sim.sim_set_basis_state(st.h, j)

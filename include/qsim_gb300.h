@@ -88,13 +88,20 @@ typedef enum {
 
 typedef struct sim_plan_opts {
     int32_t plan;            /* sim_plan_kind */
-    int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block, 3..6 (0 = 5); k <= 5 runs
-                                3xTF32, k = 6 an FP16 hi / lo split (same 22 significant bits) of
-                                operands scaled by powers of two: the state by one chosen from its
-                                norm (one extra pass over the state per call), each block's matrix
-                                by one chosen from the product of its gates' spectral norms, so
-                                states of any magnitude are applied at the same precision relative
-                                to their norm; SIM_EUNSUPPORTED if that product exceeds 2^114 */
+    int32_t fuse_k;          /* SIM_PLAN_FUSED: qubits per fused block.  complex64: 3..6 (0 = 5);
+                                k <= 5 runs 3xTF32, k = 6 an FP16 hi / lo split (same 22
+                                significant bits) of operands scaled by powers of two: the state by
+                                one chosen from its norm (one extra pass over the state per call),
+                                each block's matrix by one chosen from the product of its gates'
+                                spectral norms, so states of any magnitude are applied at the same
+                                precision relative to their norm; SIM_EUNSUPPORTED if that product
+                                exceeds 2^114.  complex128: 4 only (0 = 4): rows and columns are
+                                written in 49-bit fixed point relative to their largest entry, cut
+                                into seven 7-bit integer digits, and the digit products are summed
+                                exactly on the FP16 tensor cores (error-free splitting of Ozaki,
+                                Ogita, Oishi and Rump 2012); each result is within about 2^-49 of
+                                its row's and column's largest entries.  Every fused plan needs
+                                n >= k + 7 (SIM_EINVAL otherwise). */
     int32_t tile_qubits;     /* SIM_PLAN_STAGED: tile size log2 (0 = default) */
     int32_t flags;           /* SIM_FLAG_* bits, 0 = defaults */
 } sim_plan_opts;
@@ -240,9 +247,10 @@ int sim_batch_destroy(sim_batch_t b);
  *   eps 1e-8, learning rate lr); *final_loss (may be NULL) after the last.
  * sim_set_cost_model: SIM_PLAN_LEARNED on this handle consults model m (NULL
  *   = no model: the greedy fixed-k plan is used).  The model must outlive the
- *   handle's use of it.  A complex128 handle runs SIM_PLAN_LEARNED as the
- *   per-gate plan without consulting the model (every complex128 plan is
- *   bound by the FP64 pipe, where per-gate kernels do the least work). */
+ *   handle's use of it.  A complex128 handle runs SIM_PLAN_LEARNED without
+ *   consulting the model (trained on complex64 timings): as the fused plan
+ *   with k = 4 when n >= 11 (tensor-core digit products; the per-gate and
+ *   register-tile kernels are bound by the FP64 pipe), else per gate. */
 typedef struct qsim_mlp *sim_mlp_t;
 int sim_mlp_param_count(int d_in, int hidden);
 int sim_mlp_create(int d_in, int hidden, void *stream, sim_mlp_t *out);

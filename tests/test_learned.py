@@ -76,18 +76,21 @@ def test_learned_plan_gain_over_fixed_variants(trained):
 
 
 @pytest.mark.gpu
-def test_learned_plan_complex128_runs_per_gate(trained, orc):
-    """complex128 is FP64-bound in every plan: the learned plan runs the
-    per-gate kernels without consulting the model, at complex128 accuracy."""
+@pytest.mark.parametrize("n,variant", [(10, 0), (14, 4)])
+def test_learned_plan_complex128(trained, orc, n, variant):
+    """complex128: the learned plan runs 4-qubit fused blocks (tensor-core
+    digit products) wherever their tile fits (n >= 11) and the per-gate
+    kernels below that, without consulting the model; the state matches the
+    oracle at complex128 accuracy either way."""
     sim = trained[0]
-    n = 14
     g = C.random_gates(n, 200, seed=12)
     st = sim.State(n, "c128")
     sim.sim_set_cost_model(st.h, trained[2])
     psi = C.random_state(n, seed=2)
     st.load(psi)
     st.apply(g, plan="learned")
-    assert list(sim.sim_last_plan(st.h)) == [0]
+    assert list(sim.sim_last_plan(st.h)) == [variant]
     ref = orc.apply_circuit(psi, g)
     assert np.max(np.abs(st.state() - ref)) <= 1e-11 * np.max(np.abs(ref))
+    assert orc.infidelity(ref, st.state()) <= 1e-12
     st.close()
