@@ -5,7 +5,8 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
 shares no code with the CUDA library: the arithmetic lives in
 ``qsim_oracle.c`` (plain C, FP64), compiled here with gcc; ``mlp.py`` holds
 the numpy FP64 oracle of the cost model's network (forward, backward,
-Adam).
+Adam); ``density.py`` the numpy FP64 density-matrix oracle (gates, noise
+channels, measurement and sampling of mixed states, dense matrices).
 
 States are numpy complex128 arrays of 2^n amplitudes (amplitude j <-> |j>,
 qubit t = bit t of j).  Gate lists are structured arrays with the fields of
@@ -71,6 +72,8 @@ def _load():
             lib.orc_measure.restype = i32
             lib.orc_sample.argtypes = [i32, P, u64, u64, P]
             lib.orc_sample.restype = i32
+            lib.orc_sample_weights.argtypes = [u64, P, u64, u64, P]
+            lib.orc_sample_weights.restype = i32
             lib.orc_expect_z_sum.argtypes = [i32, P]
             lib.orc_expect_z_sum.restype = f64
             lib.orc_infidelity.argtypes = [i32, P, P]
@@ -186,6 +189,15 @@ def sample(psi: np.ndarray, shots: int, seed: int) -> np.ndarray:
     out = np.zeros(shots, dtype=np.uint64)
     if _load().orc_sample(_nqubits(psi), _ptr(psi), shots, seed, _ptr(out)) != 0:
         raise MemoryError("oracle sample")
+    return out
+
+
+def sample_weights(p: np.ndarray, shots: int, seed: int) -> np.ndarray:
+    """Inverse-CDF shots over non-negative weights p (the rule of sample())."""
+    p = np.ascontiguousarray(p, dtype=np.float64)
+    out = np.zeros(shots, dtype=np.uint64)
+    if _load().orc_sample_weights(p.size, _ptr(p), shots, seed, _ptr(out)) != 0:
+        raise MemoryError("oracle sample_weights")
     return out
 
 

@@ -370,6 +370,37 @@ int orc_sample(int n, const double *psi, uint64_t shots, uint64_t seed, uint64_t
     return 0;
 }
 
+/* ------------------------------------------------------------------------
+ * The same inverse-CDF rule on given weights p_0 .. p_{N-1} >= 0 (a density
+ * matrix's diagonal, §1.3.3 with M_j = |j><j|): compensated inclusive prefix
+ * C_i, shot s -> smallest i with C_i > u_s C_{N-1}, else the last i with
+ * p_i > 0.
+ * ---------------------------------------------------------------------- */
+int orc_sample_weights(uint64_t N, const double *p, uint64_t shots, uint64_t seed, uint64_t *out)
+{
+    double *C = (double *)malloc(sizeof(double) * (N ? N : 1));
+    if (!C) return -1;
+    nsum acc = {0, 0};
+    uint64_t last_nz = 0;
+    for (uint64_t i = 0; i < N; ++i) {
+        if (p[i] > 0) last_nz = i;
+        nsum_add(&acc, p[i]);
+        C[i] = nsum_get(&acc);
+    }
+    double total = N ? C[N - 1] : 0.0;
+    for (uint64_t s = 0; s < shots; ++s) {
+        double target = orc_uniform(seed, s) * total;
+        uint64_t lo = 0, hi = N;
+        while (lo < hi) {
+            uint64_t mid = lo + (hi - lo) / 2;
+            if (C[mid] > target) hi = mid; else lo = mid + 1;
+        }
+        out[s] = (lo < N) ? lo : last_nz;
+    }
+    free(C);
+    return 0;
+}
+
 /* <sum_i Z_i> = sum_x p_x (n - 2 popcount(x)): Z_i has eigenvalue +1 on
  * bit i = 0 and -1 on bit i = 1 (the gate table of §1.3.2). */
 double orc_expect_z_sum(int n, const double *psi)
