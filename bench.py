@@ -742,6 +742,41 @@ def run_extras(args, sim, C, dev, model):
                                                 "achieved_GBps": cfg["alg_scratch_bytes"] / tb / 1e9,
                                                 "frac": cfg["alg_scratch_bytes"] / tb / 1e9 / peaks["hbm_gbs"]}},
                            "note": "wall time of sim_batch_run (graph launch + readback of 4096 <sum Z> values)"}
+    # density matrix of 15 qubits (a 30-qubit register, 8 GiB complex64): the 30-qubit workload's
+    # gate distribution at depth 20, each layer followed by depolarizing (1e-3) and amplitude
+    # damping (2e-3) on every qubit; gates as G rho G^dagger on the register, one pass per channel
+    nd = 15
+    gd = C.noisy_haar_cz(nd, 20, seed=SEED)
+    is_ch = np.isin(gd["name"], C.CHANNEL_NAMES)
+    rho = sim.DensityMatrix(nd, "c64", device=dev)
+    sgd = sim.to_sim_gates(gd)
+    res = {"gates": int(np.count_nonzero(~is_ch)), "channels": int(np.count_nonzero(is_ch))}
+    for name, o in (("per_gate", sim.plan_opts("per_gate")), ("fused:6", sim.plan_opts("fused", fuse_k=6)),
+                    ("learned", sim.plan_opts("learned"))):
+        if name == "learned":
+            sim.sim_set_cost_model(rho.h, model)
+
+        def run():
+            rho.set_basis(0)
+            sim.sim_dm_apply_circuit(rho.h, sgd, o)
+        run()
+        sim.sim_profile_enable(rho.h, True)
+        ms = _timed(run, rho.stream, 1)
+        prof = sim.sim_profile_read(rho.h)
+        sim.sim_profile_enable(rho.h, False)
+        r = {"ms": ms, "ops_per_s": len(gd) / (ms / 1e3)}
+        if "channel" in prof:
+            cl, cms, cb, _ = prof["channel"]
+            r["channel_passes"] = cl
+            r["channel_ms"] = cms
+            r["channel_alg_GBps"] = cb / (cms / 1e3) / 1e9
+            r["channel_frac_of_copy_peak"] = r["channel_alg_GBps"] / peaks["hbm_gbs"]
+        res[name] = r
+    res["trace"] = rho.trace()
+    res["purity"] = rho.purity()
+    res["note"] = "15-qubit density matrix, complex64; ops = gates + channels; best of 1 after a warm run"
+    out["noisy_haar_cz_15q_density"] = res
+    rho.close()
     # 33 qubits, depth 24 (64 GiB complex64): learned plan vs the greedy tile planner, then 10^6 shots
     if args.c5:
         n5 = 33

@@ -62,7 +62,11 @@ typedef enum {
     SIM_GATE_U = 0, SIM_GATE_X = 1, SIM_GATE_Y = 2, SIM_GATE_Z = 3, SIM_GATE_H = 4,
     SIM_GATE_S = 5, SIM_GATE_SDG = 6, SIM_GATE_T = 7, SIM_GATE_TDG = 8,
     SIM_GATE_RX = 9, SIM_GATE_RY = 10, SIM_GATE_RZ = 11, SIM_GATE_P = 12, SIM_GATE_U3 = 13,
-    SIM_GATE_SWAP = 14
+    SIM_GATE_SWAP = 14,
+    /* noise channels, for sim_dm_apply_circuit only: on qubit target, no
+     * controls, parameter params[0] in [0, 1] (see sim_channel_kind) */
+    SIM_GATE_CH_DEPOLARIZING = 16, SIM_GATE_CH_AMPLITUDE_DAMPING = 17, SIM_GATE_CH_PHASE_DAMPING = 18,
+    SIM_GATE_CH_BIT_FLIP = 19, SIM_GATE_CH_PHASE_FLIP = 20
 } sim_gate_kind;
 
 /* One gate of a circuit (112 bytes, no padding). */
@@ -179,6 +183,78 @@ int sim_norm(sim_t s, double *out);
 int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob);
 int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
 int sim_expect_z_sum(sim_t s, double *out);
+
+/* ---- density matrices and noise ---------------------------------------------
+ * The paper names density matrices among a simulator's outputs (§1) without
+ * a method; these calls give them the operations the paper defines for a
+ * state (§1.3.3, §2.3, §2.4).  A density-matrix handle holds rho of n qubits
+ * (n in [1, 17]) as a register of 2n qubits: rho[r][c] is amplitude
+ * (r << n) | c (4^n amplitudes of the handle's dtype; sim_copy_state /
+ * sim_load_state move them in that order, sim_state_info reports 2n).  The
+ * state-vector calls that would read it as a state (sim_apply_gate,
+ * sim_apply_circuit, sim_set_basis_state, sim_probabilities, sim_norm,
+ * sim_measure, sim_sample, sim_expect_z_sum) return SIM_EINVAL on it, and the
+ * sim_dm_* calls SIM_EINVAL on a state-vector handle.
+ *
+ * Channels (Nielsen & Chuang §8.3), p in [0, 1]:
+ *   DEPOLARIZING      rho -> (1 - p) rho + p I / 2 (Kraus sqrt(1 - 3p/4) I,
+ *                     sqrt(p/4) X, Y, Z)
+ *   AMPLITUDE_DAMPING diag(1, sqrt(1 - p)), sqrt(p) |0><1|
+ *   PHASE_DAMPING     diag(1, sqrt(1 - p)), sqrt(p) |1><1|
+ *   BIT_FLIP          sqrt(1 - p) I, sqrt(p) X
+ *   PHASE_FLIP        sqrt(1 - p) I, sqrt(p) Z
+ *
+ * sim_dm_create / sim_dm_create_from_buffer: as sim_create /
+ *   sim_create_from_buffer for the 2n-qubit register (sim_dm_create starts in
+ *   |0...0><0...0|; a wrapped buffer keeps its contents).
+ * sim_dm_info: *n = the number of qubits of rho.
+ * sim_dm_set_basis_state: rho = |j><j|.
+ * sim_dm_set_pure: rho = |psi><psi| from state-vector handle psi (n qubits,
+ *   same dtype; ordered after psi's pending work).
+ * sim_dm_apply_circuit: for each gate G on qubit t, rho -> G rho G^dagger
+ *   (G on register qubit t + n, conj(G) on register qubit t, controls
+ *   likewise), scheduled by opts like sim_apply_circuit on the register; a
+ *   channel kind (SIM_GATE_CH_*) applies that channel where it stands (one
+ *   pass over the register).
+ * sim_channel_kraus: the Kraus operators of SIM_CHANNEL_* kind with
+ *   parameter p into kraus (host, up to 4 x 8 doubles, each a 2x2 matrix laid
+ *   out as sim_apply_gate's U); *n_kraus gets their count.
+ * sim_dm_apply_kraus: rho -> sum_m K_m rho K_m^dagger on qubit target,
+ *   n_kraus in [1, 16] matrices of 8 doubles (host); the map need not be
+ *   trace preserving.  sim_dm_apply_channel: the same for a named channel.
+ * sim_dm_probabilities: p_j = Re rho[j][j] into a device array of 2^n floats
+ *   (out_real = SIM_F32) or doubles.
+ * sim_dm_trace: sum_j Re rho[j][j] in FP64.  sim_dm_purity: sum |rho_rc|^2
+ *   (= tr rho^2 for Hermitian rho), accumulated as sim_norm.
+ * sim_dm_expect_z_sum: sum_j Re rho[j][j] (n - 2 popcount j), FP64.
+ * sim_dm_measure: measure qubit q as sim_measure does on a state: p0, p1
+ *   from the diagonal, the outcome from the same draw, then
+ *   rho -> P rho P / p(outcome), P the projector on bit q = outcome.
+ * sim_dm_sample: shots from p_j as sim_sample draws them from |a_j|^2 (rho
+ *   unchanged).
+ * Trace, <sum Z>, measurement and sampling read p_j through FP64 square roots
+ *   sqrt(max(p_j, 0)) whose squares they sum (within an FP64 rounding of p_j);
+ *   a diagonal entry below zero, which only rounding produces for a physical
+ *   rho, counts as zero there. */
+typedef enum {
+    SIM_CHANNEL_DEPOLARIZING = 0, SIM_CHANNEL_AMPLITUDE_DAMPING = 1, SIM_CHANNEL_PHASE_DAMPING = 2,
+    SIM_CHANNEL_BIT_FLIP = 3, SIM_CHANNEL_PHASE_FLIP = 4
+} sim_channel_kind;
+int sim_dm_create(int n, int dtype, void *stream, sim_t *out);
+int sim_dm_create_from_buffer(int n, int dtype, void *dev_ptr, size_t bytes, void *stream, sim_t *out);
+int sim_dm_info(sim_t s, int *n);
+int sim_dm_set_basis_state(sim_t s, uint64_t j);
+int sim_dm_set_pure(sim_t s, sim_t psi);
+int sim_dm_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts);
+int sim_channel_kraus(int kind, double p, double *kraus, int *n_kraus);
+int sim_dm_apply_kraus(sim_t s, int target, const double *kraus, int n_kraus);
+int sim_dm_apply_channel(sim_t s, int kind, double p, int target);
+int sim_dm_probabilities(sim_t s, void *dev_out, int out_real);
+int sim_dm_trace(sim_t s, double *out);
+int sim_dm_purity(sim_t s, double *out);
+int sim_dm_expect_z_sum(sim_t s, double *out);
+int sim_dm_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob);
+int sim_dm_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
 
 /* ---- batches of small circuits ---------------------------------------------
  * Many independent registers, each started in |0...0> (§2.1), each with its

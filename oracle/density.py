@@ -104,11 +104,21 @@ def basis(n: int, j: int = 0) -> np.ndarray:
     return rho
 
 
+# record names of noise channels (the input format's channel records) -> kind
+CHANNELS = {"dep": "depolarizing", "adamp": "amplitude_damping", "pdamp": "phase_damping",
+            "bflip": "bit_flip", "pflip": "phase_flip"}
+
+
 def apply_circuit(rho: np.ndarray, gates) -> np.ndarray:
-    """rho -> G_m ... G_1 rho G_1^dagger ... G_m^dagger."""
+    """rho -> G rho G^dagger for each gate record in order; a channel record
+    (name in CHANNELS, parameter params[0]) applies its Kraus map there."""
     n = _nq(rho)
     out = np.array(rho, dtype=np.complex128)
     for g in gates:
+        name = str(g["name"])
+        if name in CHANNELS:
+            out = apply_kraus(out, kraus(CHANNELS[name], float(g["params"][0])), int(g["target"]))
+            continue
         G = gate_operator(n, g)
         out = G @ out @ G.conj().T
     return out
@@ -139,18 +149,6 @@ def apply_kraus(rho: np.ndarray, ks, target: int) -> np.ndarray:
     for K in ks:
         E = kron_register(n, {target: np.asarray(K, dtype=np.complex128)})
         out += E @ rho @ E.conj().T
-    return out
-
-
-def apply_noisy(rho: np.ndarray, ops) -> np.ndarray:
-    """A noisy circuit: ops is a list of ("gates", gate array) and
-    ("channel", kind, p, target) items, applied in order."""
-    out = np.array(rho, dtype=np.complex128)
-    for op in ops:
-        if op[0] == "gates":
-            out = apply_circuit(out, op[1])
-        else:
-            out = apply_kraus(out, kraus(op[1], op[2]), op[3])
     return out
 
 

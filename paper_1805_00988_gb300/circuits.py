@@ -18,6 +18,11 @@ Gate records use ``GATE_DTYPE``:
     params   angles (theta, phi, lambda) for rx/ry/rz/p/u3
     mat      explicit 2x2 matrix [[A, B], [C, D]] as (re, im) pairs, name 'u'
 
+Noise channels (density matrices only) use the same records: name one of
+``CHANNEL_NAMES`` (dep = depolarizing, adamp = amplitude damping, pdamp =
+phase damping, bflip = bit flip, pflip = phase flip), the qubit in target and
+the channel's parameter in params[0].
+
 Workloads (sizes and distributions of the paper's QFT benchmark, App. A, and
 of the dense random / variational circuits the simulator is measured on):
 
@@ -26,9 +31,12 @@ of the dense random / variational circuits the simulator is measured on):
     qft_paper        the App. A benchmark ordering (no final swaps)
     haar_cz          layers of Haar-random 1q unitaries + CZ on a random matching
     phase_polynomial diagonal gates only (controlled phases, RZ, P, T, S, Z)
+    reversible       permutation gates only (X, CNOT, Toffoli, SWAP)
     segments         consecutive stretches of the above (mixed circuits)
     variational      batched RY/RZ layers + CZ ring, uneven qubit counts
     bernstein_vazirani   the App. C worked example
+    noisy            layers of a circuit, each followed by channels on every qubit
+    random_noisy     random gates with random channels in between (parity sweeps)
 """
 from __future__ import annotations
 
@@ -48,6 +56,7 @@ GATE_DTYPE = np.dtype([
 
 GATE_NAMES = ("u", "x", "y", "z", "h", "s", "sdg", "t", "tdg",
               "rx", "ry", "rz", "p", "u3", "swap")
+CHANNEL_NAMES = ("dep", "adamp", "pdamp", "bflip", "pflip")
 
 # inverse of each named gate, with the map on its angles
 _INVERSE = {"x": "x", "y": "y", "z": "z", "h": "h", "s": "sdg", "sdg": "s",
@@ -199,12 +208,36 @@ def phase_polynomial(n: int, m: int, seed: int) -> np.ndarray:
     return g
 
 
+def reversible(n: int, m: int, seed: int) -> np.ndarray:
+    """m permutation gates (the reversible-logic part of arithmetic and
+    oracle circuits): X, CNOT, Toffoli (two controls) and SWAP in equal
+    shares, on random distinct qubits."""
+    rng = np.random.default_rng(seed)
+    g = empty(m)
+    for k in range(m):
+        qs = rng.permutation(n)
+        kind = int(rng.integers(0, 4 if n >= 3 else 2))
+        if kind == 3 and n >= 2:
+            g["name"][k] = "swap"
+            g["target"][k] = qs[0]
+            g["target2"][k] = qs[1]
+            continue
+        g["name"][k] = "x"
+        g["target"][k] = qs[0]
+        nc = min(kind, n - 1) if kind < 3 else 0
+        g["nctrl"][k] = nc
+        for c in range(nc):
+            g["ctrl"][k, c] = qs[1 + c]
+    return g
+
+
 def segments(n: int, kinds, seg_gates: int, seed: int) -> np.ndarray:
     """A circuit made of consecutive segments of about seg_gates gates each,
     of the given kinds: "haar" (layers of haar_cz), "phase"
     (phase_polynomial), "qft" (the textbook QFT, whatever its length),
-    "ladder" (layers of u3_cnot_ladder).  Circuits whose best plan differs
-    from one stretch of gates to the next."""
+    "ladder" (layers of u3_cnot_ladder), "rev" (reversible: X / CNOT /
+    Toffoli / SWAP).  Circuits whose best plan differs from one stretch of
+    gates to the next."""
     parts = []
     for i, kind in enumerate(kinds):
         sd = seed * 101 + i
@@ -216,6 +249,8 @@ def segments(n: int, kinds, seg_gates: int, seed: int) -> np.ndarray:
             parts.append(qft(n))
         elif kind == "ladder":
             parts.append(u3_cnot_ladder(n, max(1, round(seg_gates / (2 * n - 1))), seed=sd))
+        elif kind == "rev":
+            parts.append(reversible(n, seg_gates, seed=sd))
         else:
             raise ValueError(kind)
     return concat(parts)
@@ -344,3 +379,47 @@ def random_state(n: int, seed: int, dtype=np.complex128) -> np.ndarray:
     v = rng.standard_normal(2 ** n) + 1j * rng.standard_normal(2 ** n)
     v /= np.sqrt(np.vdot(v, v).real)
     return v.astype(dtype)
+
+
+def channel(name: str, target: int, p: float) -> np.ndarray:
+    """One noise-channel record (density matrices only)."""
+    if name not in CHANNEL_NAMES:
+        raise ValueError(name)
+    g = empty(1)
+    g["name"][0] = name
+    g["target"][0] = target
+    g["params"][0, 0] = p
+    return g
+
+
+def noisy(gates: np.ndarray, n: int, per_layer: int, channels=(("dep", 1e-3),)) -> np.ndarray:
+    """`gates` cut into layers of per_layer gates, each layer followed by every
+    (name, p) channel of `channels` on every qubit 0..n-1."""
+    parts = []
+    for f in range(0, len(gates), per_layer):
+        parts.append(gates[f:f + per_layer])
+        for name, p in channels:
+            for q in range(n):
+                parts.append(channel(name, q, p))
+    return concat(parts)
+
+
+def noisy_haar_cz(n: int, depth: int, seed: int, channels=(("dep", 1e-3), ("adamp", 2e-3))) -> np.ndarray:
+    """haar_cz(n, depth) with the given channels on every qubit after each
+    layer (a layer = n Haar gates + the matching's n // 2 CZ)."""
+    return noisy(haar_cz(n, depth, seed=seed), n, n + n // 2, channels)
+
+
+def random_noisy(n: int, m: int, seed: int, p_channel: float = 0.3) -> np.ndarray:
+    """m records: random gates (random_gates), each followed with probability
+    p_channel by a random channel on a random qubit, parameter uniform in
+    [0, 0.5)."""
+    rng = np.random.default_rng(seed)
+    g = random_gates(n, m, seed=seed + 1)
+    parts = []
+    for k in range(m):
+        parts.append(g[k:k + 1])
+        if rng.random() < p_channel:
+            parts.append(channel(CHANNEL_NAMES[int(rng.integers(0, len(CHANNEL_NAMES)))],
+                                 int(rng.integers(0, n)), float(rng.uniform(0.0, 0.5))))
+    return concat(parts)

@@ -36,7 +36,7 @@ const char *kernel_class_name(int k)
 {
     static const char *names[KC_COUNT] = {"init", "dense", "diag", "perm", "swap", "staged", "fused",
                                           "fuse_build", "prob", "reduce", "collapse", "sample", "batch", "mlp",
-                                          "fused_multi", "fused_f16", "fused_c128"};
+                                          "fused_multi", "fused_f16", "fused_c128", "channel"};
     return (k >= 0 && k < KC_COUNT) ? names[k] : "?";
 }
 
@@ -153,6 +153,33 @@ static int check_handle(sim_t s)
     return SIM_OK;
 }
 
+// entry points whose meaning is that of a state vector
+static int check_state(sim_t s, const char *who)
+{
+    if (!s) return fail(SIM_EINVAL, std::string(who) + ": null handle");
+    if (s->density)
+        return fail(SIM_EINVAL, std::string(who) + ": density-matrix handle (use the sim_dm_* entry points)");
+    return SIM_OK;
+}
+
+int apply_plan(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
+{
+    switch (o.plan) {
+    case SIM_PLAN_PER_GATE:
+        for (size_t k = 0; k < n_gates; ++k)
+            if (int rc = launch_pair_gate(s, make_pair_gate(gates[k]))) return rc;
+        return SIM_OK;
+    case SIM_PLAN_STAGED:
+        return apply_circuit_staged(s, gates, n_gates, o);
+    case SIM_PLAN_FUSED:
+        return apply_circuit_fused(s, gates, n_gates, o);
+    case SIM_PLAN_LEARNED:
+        return apply_circuit_learned(s, gates, n_gates, o);
+    default:
+        return fail(SIM_EINVAL, "sim_apply_circuit: unknown plan");
+    }
+}
+
 }  // namespace qsim
 
 using namespace qsim;
@@ -251,7 +278,7 @@ int sim_synchronize(sim_t s)
 
 int sim_set_basis_state(sim_t s, uint64_t j)
 {
-    if (int rc = check_handle(s)) return rc;
+    if (int rc = check_state(s, "sim_set_basis_state")) return rc;
     if (j >> s->n) return fail(SIM_EINVAL, "sim_set_basis_state: j >= 2^n");
     return launch_init_basis(s, j);
 }
@@ -278,7 +305,7 @@ int sim_copy_state(sim_t s, void *dst, int dst_is_host)
 
 int sim_apply_gate(sim_t s, const double U[8], int target, const int *controls, int n_controls)
 {
-    if (int rc = check_handle(s)) return rc;
+    if (int rc = check_state(s, "sim_apply_gate")) return rc;
     if (!U) return fail(SIM_EINVAL, "sim_apply_gate: U is NULL");
     if (n_controls < 0 || n_controls > 2 || (n_controls > 0 && !controls))
         return fail(SIM_EINVAL, "sim_apply_gate: n_controls must be 0..2 with a controls array");
@@ -298,7 +325,7 @@ int sim_apply_gate(sim_t s, const double U[8], int target, const int *controls, 
 
 int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts)
 {
-    if (int rc = check_handle(s)) return rc;
+    if (int rc = check_state(s, "sim_apply_circuit")) return rc;
     if (n_gates == 0) return SIM_OK;
     if (!gates) return fail(SIM_EINVAL, "sim_apply_circuit: gates is NULL");
     for (size_t k = 0; k < n_gates; ++k) {
@@ -312,25 +339,12 @@ int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_
     sim_plan_opts o{};
     o.plan = SIM_PLAN_PER_GATE;
     if (opts) o = *opts;
-    switch (o.plan) {
-    case SIM_PLAN_PER_GATE:
-        for (size_t k = 0; k < n_gates; ++k)
-            if (int rc = launch_pair_gate(s, make_pair_gate(gates[k]))) return rc;
-        return SIM_OK;
-    case SIM_PLAN_STAGED:
-        return apply_circuit_staged(s, gates, n_gates, o);
-    case SIM_PLAN_FUSED:
-        return apply_circuit_fused(s, gates, n_gates, o);
-    case SIM_PLAN_LEARNED:
-        return apply_circuit_learned(s, gates, n_gates, o);
-    default:
-        return fail(SIM_EINVAL, "sim_apply_circuit: unknown plan");
-    }
+    return apply_plan(s, gates, n_gates, o);
 }
 
 int sim_probabilities(sim_t s, void *dev_out, int out_real)
 {
-    if (int rc = check_handle(s)) return rc;
+    if (int rc = check_state(s, "sim_probabilities")) return rc;
     if (!dev_out) return fail(SIM_EINVAL, "sim_probabilities: dev_out is NULL");
     if (out_real != SIM_F32 && out_real != SIM_F64) return fail(SIM_EINVAL, "sim_probabilities: out_real");
     return launch_probabilities(s, dev_out, out_real);
@@ -338,7 +352,7 @@ int sim_probabilities(sim_t s, void *dev_out, int out_real)
 
 int sim_norm(sim_t s, double *out)
 {
-    if (int rc = check_handle(s)) return rc;
+    if (int rc = check_state(s, "sim_norm")) return rc;
     if (!out) return fail(SIM_EINVAL, "sim_norm: out is NULL");
     double r[2];
     if (int rc = reduce_sums(s, RED_NORM, 0, r)) return rc;
@@ -348,7 +362,7 @@ int sim_norm(sim_t s, double *out)
 
 int sim_expect_z_sum(sim_t s, double *out)
 {
-    if (int rc = check_handle(s)) return rc;
+    if (int rc = check_state(s, "sim_expect_z_sum")) return rc;
     if (!out) return fail(SIM_EINVAL, "sim_expect_z_sum: out is NULL");
     double r[2];
     if (int rc = reduce_sums(s, RED_EXPZ, 0, r)) return rc;
@@ -358,7 +372,7 @@ int sim_expect_z_sum(sim_t s, double *out)
 
 int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob)
 {
-    if (int rc = check_handle(s)) return rc;
+    if (int rc = check_state(s, "sim_measure")) return rc;
     if (qubit < 0 || qubit >= s->n) return fail(SIM_EINVAL, "sim_measure: qubit out of range");
     double r[2];
     if (int rc = reduce_sums(s, RED_BIT, qubit, r)) return rc;
@@ -375,7 +389,7 @@ int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, 
 
 int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device)
 {
-    if (int rc = check_handle(s)) return rc;
+    if (int rc = check_state(s, "sim_sample")) return rc;
     if (shots > 0 && !out) return fail(SIM_EINVAL, "sim_sample: out is NULL");
     return run_sample(s, shots, seed, out, out_on_device);
 }

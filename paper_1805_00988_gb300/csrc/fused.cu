@@ -49,6 +49,11 @@ struct FGate {                          // one gate of a block, in block-local q
     uint32_t ctrl;
     double m[8];
 };
+// A 4 x 4 matrix S on local qubits la < lb (a density matrix's channel) takes
+// four consecutive records: the first has target kSuperHead and ctrl =
+// la | lb << 8, then kSuperRow; record l holds row l of S (l = 2 (bit lb) +
+// (bit la)) as four (re, im) pairs.
+constexpr int32_t kSuperHead = -1, kSuperRow = -2;
 
 
 // x rounded to TF32 (10 explicit mantissa bits), nearest with ties away from
@@ -100,6 +105,35 @@ __global__ void __launch_bounds__(256) k_fuse_build(const FGate *__restrict__ ga
     for (int g = goff[blk]; g < goff[blk + 1]; ++g) {
         const int t = gates[g].target;
         const uint32_t cm = gates[g].ctrl;
+        if (t == kSuperHead) {
+            // 4 x 4 on local qubits (la, lb): y_l = sum_k S[l][k] x_k over the
+            // four rows that differ only in those bits
+            const int la = (int)(cm & 0xFFu), lb = (int)((cm >> 8) & 0xFFu);
+            for (int e = threadIdx.x; e < DC * (D / 4); e += 256) {
+                const int c = e / (D / 4);
+                int i0 = e % (D / 4);
+                i0 = ((i0 >> la) << (la + 1)) | (i0 & ((1 << la) - 1));
+                i0 = ((i0 >> lb) << (lb + 1)) | (i0 & ((1 << lb) - 1));
+                const int idx[4] = {i0, i0 | (1 << la), i0 | (1 << lb), i0 | (1 << la) | (1 << lb)};
+                double2 x[4];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) x[l] = U[idx[l] * DC + c];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const double *r = gates[g + l].m;
+                    double yr = 0.0, yi = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        yr += r[2 * k] * x[k].x - r[2 * k + 1] * x[k].y;
+                        yi += r[2 * k] * x[k].y + r[2 * k + 1] * x[k].x;
+                    }
+                    U[idx[l] * DC + c] = make_double2(yr, yi);
+                }
+            }
+            __syncthreads();
+            g += 3;
+            continue;
+        }
         const double ar = gates[g].m[0], ai = gates[g].m[1], br = gates[g].m[2], bi = gates[g].m[3];
         const double cr = gates[g].m[4], ci = gates[g].m[5], dr = gates[g].m[6], di = gates[g].m[7];
         for (int e = threadIdx.x; e < DC * (D / 2); e += 256) {
@@ -1356,10 +1390,34 @@ static double sgate_norm_bound(const SGate &g)
 // 2^14 (1 + 1e-6), far below the FP16 maximum; a unitary block gets 14.  we
 // lies in [kF16WExpMin, kF16WExpMax]; returns false when the bound is too
 // large (above 2^114) or not finite.
-static bool block_wexp(const std::vector<SGate> &g, const std::vector<int> &members, int *we, double *bound_out)
+// a bound on the spectral norm of a 4 x 4 matrix S (32 doubles, row-major
+// (re, im)): sqrt(||S||_1 ||S||_inf) (Hoelder), exactly 1 for the
+// depolarizing, phase-damping and flip channels
+static double super_norm_bound(const double *S)
+{
+    double c1 = 0.0, ci = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        double row = 0.0, col = 0.0;
+        for (int j = 0; j < 4; ++j) {
+            row += std::hypot(S[2 * (4 * i + j)], S[2 * (4 * i + j) + 1]);
+            col += std::hypot(S[2 * (4 * j + i)], S[2 * (4 * j + i) + 1]);
+        }
+        ci = std::max(ci, row);
+        c1 = std::max(c1, col);
+    }
+    return std::sqrt(c1 * ci);
+}
+
+static double member_norm_bound(const SGate &g, const double *sup)
+{
+    return g.op == OP_SUPER ? super_norm_bound(sup + 32 * (size_t)g.orig) : sgate_norm_bound(g);
+}
+
+static bool block_wexp(const std::vector<SGate> &g, const std::vector<int> &members, int *we, double *bound_out,
+                       const double *sup)
 {
     double bound = 1.0;
-    for (int m : members) bound *= sgate_norm_bound(g[m]);
+    for (int m : members) bound *= member_norm_bound(g[m], sup);
     *bound_out = bound;
     if (!std::isfinite(bound)) return false;
     int eb = 0;
@@ -1382,13 +1440,15 @@ static bool block_wexp(const std::vector<SGate> &g, const std::vector<int> &memb
 // reuse within a call); the W matrices use two device slots, reused in
 // stream order.
 template <int KQ>
-int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_multi)
+int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_multi, const double *sup = nullptr)
 {
     constexpr int K = 2 << KQ;
     constexpr size_t kGroup = kGroupBlocks;
     constexpr size_t kFirst = kFirstGroup;
     const int n = s->n;
-    const size_t ng = g.size();
+    size_t ng = g.size();
+    for (const SGate &x : g)
+        if (x.op == OP_SUPER) ng += 3;             // a 4 x 4 takes four block-gate records
     // complex128 (k = 4 only): the integer digit-plane kernels of fused64.cu
     const bool c128 = s->dtype == SIM_C128;
     const size_t blk_bytes = c128 ? fused_c128_slot_bytes() : 2 * (size_t)K * K * sizeof(float);
@@ -1505,7 +1565,7 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
             ho[go_used++] = 0;
             for (size_t bi = 0; bi < blocks.size() && rc == SIM_OK; ++bi) {
                 int we = kF16WExp;
-                if (KQ == 6 && !block_wexp(g, blocks[bi].members, &we, &bnd[bi]))
+                if (KQ == 6 && !block_wexp(g, blocks[bi].members, &we, &bnd[bi], sup))
                     rc = fail(SIM_EUNSUPPORTED, "fused apply, k = 6: the product of a block's gate norms is above "
                                                 "2^114 or not finite (beyond the range of its FP16 scale)");
                 he[be_used++] = we;
@@ -1522,6 +1582,17 @@ int run_fused(qsim_state *s, const std::vector<SGate> &g, int depth, bool allow_
                         return -1;
                     };
                     for (int m : blocks[bi].members) {
+                        if (g[m].op == OP_SUPER) {
+                            const double *S = sup + 32 * (size_t)g[m].orig;
+                            for (int l = 0; l < 4; ++l) {
+                                FGate f;
+                                f.target = l == 0 ? kSuperHead : kSuperRow;
+                                f.ctrl = l == 0 ? ((uint32_t)loc(g[m].target) | ((uint32_t)loc(g[m].target2) << 8)) : 0u;
+                                memcpy(f.m, S + 8 * l, sizeof f.m);
+                                hg[fg_used++] = f;
+                            }
+                            continue;
+                        }
                         FGate f;
                         f.target = loc(g[m].target);
                         f.ctrl = 0;
@@ -1647,6 +1718,21 @@ int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t 
 }
 
 int fused_feature_depth() { return kFeatureDepth; }
+
+int apply_sgates_fused(qsim_state *s, const std::vector<SGate> &g, const double *sup, int k)
+{
+    if (k < 3 || k > 6) return fail(SIM_EINVAL, "fused plan: fuse_k must be in 3..6");
+    if (s->dtype == SIM_C128 && k != 4)
+        return fail(SIM_EUNSUPPORTED, "fused plan: complex128 states run 4-qubit blocks (fuse_k 4 or 0)");
+    if (s->n < k + 7) return fail(SIM_EINVAL, "fused plan: needs n >= fuse_k + 7 (one CTA covers 128 rows)");
+    if (g.empty()) return SIM_OK;
+    switch (k) {
+    case 3: return run_fused<3>(s, g, kRunDepth, false, sup);
+    case 4: return run_fused<4>(s, g, kRunDepth, false, sup);
+    case 5: return run_fused<5>(s, g, kRunDepth, false, sup);
+    default: return run_fused<6>(s, g, kRunDepth, false, sup);
+    }
+}
 
 int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
 {

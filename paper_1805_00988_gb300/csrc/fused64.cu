@@ -146,6 +146,35 @@ __global__ void __launch_bounds__(256) k_fuse_build64(const FGate64 *__restrict_
     for (int g = goff[blk]; g < goff[blk + 1]; ++g) {
         const int t = gates[g].target;
         const uint32_t cm = gates[g].ctrl;
+        if (t == -1) {
+            // a 4 x 4 matrix on local qubits la < lb in four records (rows of S,
+            // l = 2 (bit lb) + (bit la); the block-gate layout of fused.cu)
+            const int la = (int)(cm & 0xFFu), lb = (int)((cm >> 8) & 0xFFu);
+            for (int e = tid; e < D * (D / 4); e += 256) {
+                const int c = e / (D / 4);
+                int i0 = e % (D / 4);
+                i0 = ((i0 >> la) << (la + 1)) | (i0 & ((1 << la) - 1));
+                i0 = ((i0 >> lb) << (lb + 1)) | (i0 & ((1 << lb) - 1));
+                const int idx[4] = {i0, i0 | (1 << la), i0 | (1 << lb), i0 | (1 << la) | (1 << lb)};
+                double2 x[4];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) x[l] = U[idx[l]][c];
+#pragma unroll
+                for (int l = 0; l < 4; ++l) {
+                    const double *r = gates[g + l].m;
+                    double yr = 0.0, yi = 0.0;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        yr += r[2 * k] * x[k].x - r[2 * k + 1] * x[k].y;
+                        yi += r[2 * k] * x[k].y + r[2 * k + 1] * x[k].x;
+                    }
+                    U[idx[l]][c] = make_double2(yr, yi);
+                }
+            }
+            __syncthreads();
+            g += 3;
+            continue;
+        }
         const double ar = gates[g].m[0], ai = gates[g].m[1], br = gates[g].m[2], bi = gates[g].m[3];
         const double cr = gates[g].m[4], ci = gates[g].m[5], dr = gates[g].m[6], di = gates[g].m[7];
         for (int e = tid; e < D * (D / 2); e += 256) {

@@ -82,6 +82,8 @@ int classify_matrix(const double m[8])
 int validate_gate(int n, const sim_gate &g, std::string *why)
 {
     auto bad = [&](const char *m) { if (why) *why = m; return -1; };
+    if (g.kind >= SIM_GATE_CH_DEPOLARIZING && g.kind <= SIM_GATE_CH_PHASE_FLIP)
+        return bad("noise channels apply to density-matrix handles only (sim_dm_apply_circuit)");
     if (g.kind < SIM_GATE_U || g.kind > SIM_GATE_SWAP) return bad("unknown gate kind");
     if (g.target < 0 || g.target >= n) return bad("target qubit out of range");
     if (g.n_controls < 0 || g.n_controls > 2) return bad("n_controls must be 0, 1 or 2");

@@ -46,6 +46,7 @@ enum KernelClass {
     KC_FUSED_MULTI,  // several fused blocks applied per pass over the state
     KC_FUSED_F16,    // fused 6-qubit unitary apply on FP16-split operands
     KC_FUSED_C128,   // fused 4-qubit unitary apply to complex128 states on integer digit planes
+    KC_CHANNEL,      // density matrices: single-qubit channel (4 x 4 superoperator) pass
     KC_COUNT
 };
 const char *kernel_class_name(int k);
@@ -68,6 +69,8 @@ struct qsim_state {
     double *red_out = nullptr;       // 4 doubles
     double *host_red = nullptr;      // pinned, 4 doubles
     int *dev_status = nullptr;       // device status word of bounded waits (0 = ok)
+    bool density = false;            // a density matrix of n_sys qubits held as an n = 2 n_sys register
+    int n_sys = 0;
     void *cost_model = nullptr;      // qsim_mlp used by SIM_PLAN_LEARNED (not owned)
     std::vector<int> last_plan;      // variant chosen per window by the last learned plan
     // circuit upload buffers (device), grown on demand
@@ -105,7 +108,9 @@ int launch_end(qsim_state *s, const char *what);
 
 // ---------------------------------------------------------------- per-gate kernels
 // Classified gate, ready for a per-gate launch.
-enum GateOp { OP_DENSE = 0, OP_DIAG, OP_DIAG_HI, OP_ANTIDIAG, OP_XPERM, OP_SWAP, OP_IDENTITY };
+enum GateOp { OP_DENSE = 0, OP_DIAG, OP_DIAG_HI, OP_ANTIDIAG, OP_XPERM, OP_SWAP, OP_IDENTITY,
+              OP_SUPER   // a 4 x 4 matrix on two qubits (a density matrix's channel), fused plans only
+};
 
 struct PairGate {
     int op;
@@ -130,6 +135,16 @@ int validate_gate(int n, const sim_gate &g, std::string *why);
 PairGate make_pair_gate(const sim_gate &g);
 
 int launch_pair_gate(qsim_state *s, const PairGate &g);
+
+// a validated gate list on the handle's register under plan o (the dispatch
+// of sim_apply_circuit, without the handle-kind check)
+int apply_plan(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
+
+// density matrices (density.cu): Kraus operators of a named channel
+// (SIM_CHANNEL_*; returns their count, 0 for an unknown kind) and one channel
+// pass on system qubit t of a density handle
+int channel_kraus(int kind, double p, double out[32]);
+int launch_superop(qsim_state *s, int t, const double *kraus, int n_kraus);
 
 // ---------------------------------------------------------------- reductions
 // mode for masked FP64 sums of |a|^2
@@ -160,8 +175,13 @@ struct SGate {
     int target;
     uint64_t ctrl;       // control qubits
     double m[8];
-    int orig;            // index of the circuit gate it comes from
-    uint64_t xq() const { return (op == OP_DENSE || op == OP_ANTIDIAG || op == OP_XPERM) ? (1ull << target) : 0ull; }
+    int orig;            // index of the circuit gate it comes from (OP_SUPER: index of its 4 x 4 matrix)
+    int target2 = -1;    // OP_SUPER: the second qubit (above target)
+    uint64_t xq() const
+    {
+        if (op == OP_SUPER) return (1ull << target) | (1ull << target2);
+        return (op == OP_DENSE || op == OP_ANTIDIAG || op == OP_XPERM) ? (1ull << target) : 0ull;
+    }
     uint64_t dq() const { return ctrl | ((op == OP_DIAG || op == OP_DIAG_HI) ? (1ull << target) : 0ull); }
 };
 
@@ -175,8 +195,15 @@ int launch_sgate(qsim_state *s, const SGate &g);
 // ---------------------------------------------------------------- staged / fused plans
 int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
 int apply_circuit_fused(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
+// fused blocks of k qubits over lowered gates that may hold OP_SUPER entries
+// (a density matrix's channels; sup = their 4 x 4 matrices, 32 doubles each,
+// row-major (re, im), indexed by SGate::orig)
+int apply_sgates_fused(qsim_state *s, const std::vector<SGate> &g, const double *sup, int k);
 int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o);
 int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v, float *out);
+// the learned plan's variant per window for a complex64 register with a cost
+// model (also stored as the handle's last plan)
+int learned_choose(qsim_state *s, const sim_gate *gates, size_t n_gates, std::vector<int> *best);
 // blocks of the fused plan (depth 0 = the depth the plan runs with) and, when
 // passes_out is given, the passes over the state (multi-block passes pair
 // blocks when multi is set)

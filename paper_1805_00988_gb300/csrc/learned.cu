@@ -6,9 +6,9 @@
 // runs: each window with its own cheapest variant, or the whole circuit with
 // one variant (one variant over many windows lets the block and pass planners
 // work across window boundaries, which per-window predictions cannot see).
-// Without a model the greedy fixed-k tile planner (the staged plan) is used:
-// it is both the fallback and the judge the learned plans are measured
-// against.
+// Without a model the greedy fixed-k plan runs (fused blocks of the largest k
+// whose tile fits): it is both the fallback and the judge the learned plans
+// are measured against.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -89,39 +89,11 @@ int plan_features(int n, int dtype, const sim_gate *gates, size_t n_gates, int v
     return SIM_OK;
 }
 
-int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
+// The learned plan's choice for a complex64 register with a cost model: one
+// variant per window of max(64, 8n) gates (into *best, also kept as the
+// handle's last plan).
+int learned_choose(qsim_state *s, const sim_gate *gates, size_t n_gates, std::vector<int> *best_out)
 {
-    if (!s->cost_model) {
-        sim_plan_opts st{};
-        st.plan = SIM_PLAN_STAGED;
-        st.tile_qubits = o.tile_qubits;
-        return apply_circuit_staged(s, gates, n_gates, st);
-    }
-    if (n_gates == 0) {
-        s->last_plan.clear();
-        return SIM_OK;
-    }
-    if (s->dtype == SIM_C128) {
-        // complex128: the per-gate and register-tile kernels are bound by this
-        // GPU's narrow FP64 pipe, while 4-qubit fused blocks run on the FP16
-        // tensor cores as exact integer digit-plane products (fused64.cu).
-        // Measured at 30 qubits (Haar layers + CZ, depth 20): fused 1276 ms
-        // against 12837 ms per gate; 28-qubit QFT: 253 against 351 ms.  So the
-        // fused plan runs wherever a 4-qubit block's tile fits (n >= 11), the
-        // per-gate plan below that; the model (trained on complex64 timings)
-        // is not consulted.
-        if (s->n >= 11) {
-            s->last_plan.assign(1, 4);
-            sim_plan_opts fo{};
-            fo.plan = SIM_PLAN_FUSED;
-            fo.fuse_k = 4;
-            return apply_circuit_fused(s, gates, n_gates, fo);
-        }
-        s->last_plan.assign(1, 0);
-        for (size_t k = 0; k < n_gates; ++k)
-            if (int rc = launch_pair_gate(s, make_pair_gate(gates[k]))) return rc;
-        return SIM_OK;
-    }
     // windows of about eight layers of single-qubit gates
     const size_t W = (size_t)std::max(64, 8 * s->n);
     std::vector<Window> win;
@@ -153,7 +125,8 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
         }
     std::vector<float> pred(who.size());
     if (int rc = sim_mlp_forward((qsim_mlp *)s->cost_model, rows.data(), (int64_t)who.size(), pred.data(), 0)) return rc;
-    std::vector<int> best(nw, -1);
+    std::vector<int> &best = *best_out;
+    best.assign(nw, -1);
     std::vector<float> bestp(nw, 0.f);
     int whole_v = -1;
     float whole_p = 0.f;
@@ -177,6 +150,58 @@ int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, 
         if (!all || std::exp((double)whole_p) <= mix) std::fill(best.begin(), best.end(), whole_v);
     }
     s->last_plan.assign(best.begin(), best.end());
+    return SIM_OK;
+}
+
+int apply_circuit_learned(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
+{
+    if (!s->cost_model) {
+        // the greedy fixed-k plan: the largest block size whose tile fits
+        // (k = 6 from 13 qubits; complex128 k = 4 from 11), per gate below
+        const int kmax = s->dtype == SIM_C128 ? 4 : 6;
+        const int k = std::min(kmax, s->n - 7);
+        if (k >= (s->dtype == SIM_C128 ? 4 : 3)) {
+            s->last_plan.assign(1, k);
+            sim_plan_opts fo{};
+            fo.plan = SIM_PLAN_FUSED;
+            fo.fuse_k = k;
+            return apply_circuit_fused(s, gates, n_gates, fo);
+        }
+        s->last_plan.assign(1, 0);
+        for (size_t i = 0; i < n_gates; ++i)
+            if (int rc = launch_pair_gate(s, make_pair_gate(gates[i]))) return rc;
+        return SIM_OK;
+    }
+    if (n_gates == 0) {
+        s->last_plan.clear();
+        return SIM_OK;
+    }
+    if (s->dtype == SIM_C128) {
+        // complex128: the per-gate and register-tile kernels are bound by this
+        // GPU's narrow FP64 pipe, while 4-qubit fused blocks run on the FP16
+        // tensor cores as exact integer digit-plane products (fused64.cu).
+        // Measured at 30 qubits (Haar layers + CZ, depth 20): fused 1276 ms
+        // against 12837 ms per gate; 28-qubit QFT: 253 against 351 ms.  So the
+        // fused plan runs wherever a 4-qubit block's tile fits (n >= 11), the
+        // per-gate plan below that; the model (trained on complex64 timings)
+        // is not consulted.
+        if (s->n >= 11) {
+            s->last_plan.assign(1, 4);
+            sim_plan_opts fo{};
+            fo.plan = SIM_PLAN_FUSED;
+            fo.fuse_k = 4;
+            return apply_circuit_fused(s, gates, n_gates, fo);
+        }
+        s->last_plan.assign(1, 0);
+        for (size_t k = 0; k < n_gates; ++k)
+            if (int rc = launch_pair_gate(s, make_pair_gate(gates[k]))) return rc;
+        return SIM_OK;
+    }
+    std::vector<int> best;
+    if (int rc = learned_choose(s, gates, n_gates, &best)) return rc;
+    const size_t W = (size_t)std::max(64, 8 * s->n);
+    std::vector<Window> win;
+    for (size_t f = 0; f < n_gates; f += W) win.push_back(Window{f, std::min(W, n_gates - f)});
     // consecutive windows with the same variant run as one call, so the tile
     // and block planners see the whole run of gates
     for (size_t w = 0; w < win.size();) {

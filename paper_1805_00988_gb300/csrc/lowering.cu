@@ -48,6 +48,7 @@ double sgate_flops(const SGate &g, int n)
     case OP_DIAG: return 6.0 * amps;
     case OP_DIAG_HI:                                   // only the |1> half; a sign flip is a move
         return (g.m[6] == -1.0 && g.m[7] == 0.0) ? 0.0 : 3.0 * amps;
+    case OP_SUPER: return 32.0 * amps;                 // four complex MACs per amplitude
     default: return 0.0;                               // exchanges
     }
 }

@@ -33,7 +33,10 @@ PLANS = {"per_gate": 0, "staged": 1, "fused": 2, "learned": 3}
 CUDA_STREAM_LEGACY = 1      # cudaStreamLegacy
 
 GATE_KINDS = {"u": 0, "x": 1, "y": 2, "z": 3, "h": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8,
-              "rx": 9, "ry": 10, "rz": 11, "p": 12, "u3": 13, "swap": 14}
+              "rx": 9, "ry": 10, "rz": 11, "p": 12, "u3": 13, "swap": 14,
+              # noise channels (density-matrix handles only), parameter in params[0]
+              "dep": 16, "adamp": 17, "pdamp": 18, "bflip": 19, "pflip": 20}
+SIM_CHANNELS = {"depolarizing": 0, "amplitude_damping": 1, "phase_damping": 2, "bit_flip": 3, "phase_flip": 4}
 
 # struct sim_gate (112 bytes)
 SIM_GATE_DTYPE = np.dtype([
@@ -338,6 +341,146 @@ class State:
 
     def sample(self, shots: int, seed: int) -> np.ndarray:
         return sim_sample(self.h, shots, seed)
+
+    def synchronize(self):
+        sim_synchronize(self.h)
+
+
+# ---------------------------------------------------------------- density matrices
+_sig("sim_dm_create", [_i32, _i32, P, ctypes.POINTER(P)])
+_sig("sim_dm_create_from_buffer", [_i32, _i32, P, _sz, P, ctypes.POINTER(P)])
+_sig("sim_dm_info", [P, P])
+_sig("sim_dm_set_basis_state", [P, _u64])
+_sig("sim_dm_set_pure", [P, P])
+_sig("sim_dm_apply_circuit", [P, P, _sz, P])
+_sig("sim_channel_kraus", [_i32, ctypes.c_double, P, P])
+_sig("sim_dm_apply_kraus", [P, _i32, P, _i32])
+_sig("sim_dm_apply_channel", [P, _i32, ctypes.c_double, _i32])
+_sig("sim_dm_probabilities", [P, P, _i32])
+_sig("sim_dm_trace", [P, P])
+_sig("sim_dm_purity", [P, P])
+_sig("sim_dm_expect_z_sum", [P, P])
+_sig("sim_dm_measure", [P, _i32, _u64, _u64, P, P])
+_sig("sim_dm_sample", [P, _u64, _u64, P, _i32])
+
+
+def _mat8(K) -> np.ndarray:
+    m = np.asarray(K, dtype=np.complex128).reshape(2, 2).reshape(-1)
+    out = np.zeros(8, dtype=np.float64)
+    out[0::2] = m.real
+    out[1::2] = m.imag
+    return out
+
+
+def sim_channel_kraus(kind: str, p: float):
+    """The library's Kraus operators of a named channel, as 2x2 complex arrays."""
+    buf = np.zeros(32, dtype=np.float64)
+    cnt = ctypes.c_int()
+    check(_lib.sim_channel_kraus(SIM_CHANNELS[kind], float(p), buf.ctypes.data_as(P), ctypes.byref(cnt)))
+    return [(buf[8 * m:8 * m + 8:2] + 1j * buf[8 * m + 1:8 * m + 8:2]).reshape(2, 2) for m in range(cnt.value)]
+
+
+def sim_dm_apply_circuit(h: int, sim_gates: np.ndarray, opts: sim_plan_opts = None):
+    g = np.ascontiguousarray(sim_gates, dtype=SIM_GATE_DTYPE)
+    check(_lib.sim_dm_apply_circuit(P(h), g.ctypes.data_as(P), len(g),
+                                    ctypes.byref(opts) if opts is not None else None))
+
+
+def _dm_scalar(fn, h):
+    r = ctypes.c_double()
+    check(fn(P(h), ctypes.byref(r)))
+    return r.value
+
+
+class DensityMatrix:
+    """A density matrix of n qubits (a 2n-qubit register whose amplitude
+    (r << n) | c is rho[r][c]) in a PyTorch CUDA tensor.  Starts in
+    |0...0><0...0|."""
+
+    def __init__(self, n: int, dtype: str = "c64", device=None):
+        import torch
+        self.n = n
+        self.dtype = SIM_C128 if dtype in ("c128", SIM_C128, np.complex128) else SIM_C64
+        self._torch = torch
+        dev = torch.device(device or "cuda")
+        self.stream = torch.cuda.current_stream(dev)
+        self.stream_handle = self.stream.cuda_stream or CUDA_STREAM_LEGACY
+        tdt = torch.complex128 if self.dtype == SIM_C128 else torch.complex64
+        self.tensor = torch.empty(4 ** n, dtype=tdt, device=dev)
+        h = P()
+        check(_lib.sim_dm_create_from_buffer(n, self.dtype, P(self.tensor.data_ptr()),
+                                             self.tensor.numel() * self.tensor.element_size(),
+                                             P(self.stream_handle), ctypes.byref(h)))
+        self.h = h.value
+        self.set_basis(0)
+
+    def close(self):
+        if getattr(self, "h", None):
+            sim_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def np_dtype(self):
+        return np.complex128 if self.dtype == SIM_C128 else np.complex64
+
+    def set_basis(self, j: int = 0):
+        check(_lib.sim_dm_set_basis_state(P(self.h), j))
+
+    def set_pure(self, psi_state: "State"):
+        check(_lib.sim_dm_set_pure(P(self.h), P(psi_state.h)))
+
+    def load(self, rho: np.ndarray):
+        a = np.ascontiguousarray(np.asarray(rho).reshape(-1), dtype=self.np_dtype)
+        assert a.size == 4 ** self.n
+        sim_load_state(self.h, a.ctypes.data, True)
+
+    def matrix(self) -> np.ndarray:
+        out = np.empty(4 ** self.n, dtype=self.np_dtype)
+        sim_copy_state(self.h, out.ctypes.data, True)
+        return out.reshape(2 ** self.n, 2 ** self.n)
+
+    def apply(self, gates: np.ndarray, plan="per_gate", **kw):
+        sim_dm_apply_circuit(self.h, to_sim_gates(gates), plan_opts(plan, **kw))
+
+    def apply_kraus(self, kraus_ops, target: int):
+        k = np.concatenate([_mat8(K) for K in kraus_ops])
+        check(_lib.sim_dm_apply_kraus(P(self.h), target, k.ctypes.data_as(P), len(kraus_ops)))
+
+    def apply_channel(self, kind: str, p: float, target: int):
+        check(_lib.sim_dm_apply_channel(P(self.h), SIM_CHANNELS[kind], float(p), target))
+
+    def probabilities(self, f64: bool = True):
+        t = self._torch.empty(2 ** self.n, dtype=self._torch.float64 if f64 else self._torch.float32,
+                              device=self.tensor.device)
+        check(_lib.sim_dm_probabilities(P(self.h), P(t.data_ptr()), SIM_F64 if f64 else SIM_F32))
+        sim_synchronize(self.h)
+        return t.cpu().numpy()
+
+    def trace(self) -> float:
+        return _dm_scalar(_lib.sim_dm_trace, self.h)
+
+    def purity(self) -> float:
+        return _dm_scalar(_lib.sim_dm_purity, self.h)
+
+    def expect_z_sum(self) -> float:
+        return _dm_scalar(_lib.sim_dm_expect_z_sum, self.h)
+
+    def measure(self, qubit: int, seed: int, draw: int = 0):
+        m = ctypes.c_int()
+        p = ctypes.c_double()
+        check(_lib.sim_dm_measure(P(self.h), qubit, seed, draw, ctypes.byref(m), ctypes.byref(p)))
+        return m.value, p.value
+
+    def sample(self, shots: int, seed: int) -> np.ndarray:
+        arr = np.empty(shots, dtype=np.uint64)
+        check(_lib.sim_dm_sample(P(self.h), shots, seed, arr.ctypes.data_as(P), 0))
+        return arr
 
     def synchronize(self):
         sim_synchronize(self.h)

@@ -81,4 +81,39 @@ def test_gate_kind_codes_match_header():
     from paper_1805_00988_gb300 import sim
     src = open(os.path.join(ROOT, "include", "qsim_gb300.h")).read()
     codes = dict((k.lower(), int(v)) for k, v in re.findall(r"SIM_GATE_(\w+)\s*=\s*(\d+)", src))
-    assert codes == sim.GATE_KINDS
+    # channel records carry short names in the binding
+    short = {"ch_depolarizing": "dep", "ch_amplitude_damping": "adamp", "ch_phase_damping": "pdamp",
+             "ch_bit_flip": "bflip", "ch_phase_flip": "pflip"}
+    assert {short.get(k, k): v for k, v in codes.items()} == sim.GATE_KINDS
+    chan = dict((k.lower(), int(v)) for k, v in re.findall(r"SIM_CHANNEL_(\w+)\s*=\s*(\d+)", src))
+    assert chan == sim.SIM_CHANNELS
+    for k, v in sim.SIM_CHANNELS.items():
+        assert codes["ch_" + k] == 16 + v
+
+
+def test_channel_kraus_matches_oracle_without_gpu(lib, orc):
+    """sim_channel_kraus is host code: its Kraus operators equal the oracle's
+    (Nielsen & Chuang §8.3) for every named channel, and bad arguments are
+    rejected."""
+    from oracle import density
+    P = ctypes.c_void_p
+    lib.sim_channel_kraus.argtypes = [ctypes.c_int, ctypes.c_double, P, P]
+    names = ["depolarizing", "amplitude_damping", "phase_damping", "bit_flip", "phase_flip"]
+    for kind, name in enumerate(names):
+        for p in (0.0, 0.17, 1.0):
+            buf = np.zeros(32)
+            cnt = ctypes.c_int()
+            assert lib.sim_channel_kraus(kind, p, buf.ctypes.data_as(P), ctypes.byref(cnt)) == 0
+            got = [(buf[8 * m:8 * m + 8:2] + 1j * buf[8 * m + 1:8 * m + 8:2]).reshape(2, 2) for m in range(cnt.value)]
+            want = density.kraus(name, p)
+            assert len(got) == len(want)
+            for a, b in zip(got, want):
+                assert np.max(np.abs(a - b)) < 1e-15, (name, p)
+    buf = np.zeros(32)
+    cnt = ctypes.c_int()
+    assert lib.sim_channel_kraus(9, 0.1, buf.ctypes.data_as(P), ctypes.byref(cnt)) == 1
+    assert lib.sim_channel_kraus(0, 1.5, buf.ctypes.data_as(P), ctypes.byref(cnt)) == 1
+    lib.sim_dm_create.argtypes = [ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)]
+    h = P()
+    assert lib.sim_dm_create(18, 0, None, ctypes.byref(h)) == 1
+    assert lib.sim_dm_create(0, 0, None, ctypes.byref(h)) == 1
