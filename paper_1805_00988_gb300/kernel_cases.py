@@ -4,6 +4,7 @@
     python -m paper_1805_00988_gb300.kernel_cases pergate   # CNOT / CZ / SWAP, low qubit 3, 8, 17, 25; 27 qubits
     python -m paper_1805_00988_gb300.kernel_cases batch     # 512 variational circuits, one persistent launch
     python -m paper_1805_00988_gb300.kernel_cases c128      # complex128 fused 4-qubit blocks, 27 qubits (2 GiB)
+    python -m paper_1805_00988_gb300.kernel_cases channel   # density-matrix channel passes, 13-qubit rho (26-qubit register)
 
 Each case holds a few GB on the device at most (a 27-qubit complex64 state
 is 1 GiB, 8x the L2), so a full ncu capture of one launch ends in a minute
@@ -34,6 +35,13 @@ def main(argv=None):
     elif mode == "c128":
         st = sim.State(27, "c128")
         st.apply(C.haar_cz(27, 3, seed=1234), plan="fused", fuse_k=4)
+    elif mode == "channel":
+        rho = sim.DensityMatrix(13, "c64")
+        rho.apply(C.haar_cz(13, 1, seed=1234), plan="per_gate")
+        for t in (0, 5, 12):
+            rho.apply_channel("depolarizing", 0.01, t)
+            rho.apply_channel("amplitude_damping", 0.02, t)
+        rho.close()
     elif mode == "batch":
         ns, offs, bg = C.variational(512, 8, 20, 4, 12, seed=1234)
         b = sim.Batch(ns, offs, bg)
@@ -41,7 +49,7 @@ def main(argv=None):
         b.run()
         b.close()
     else:
-        raise SystemExit("unknown case %r (k6, pergate, batch, c128)" % mode)
+        raise SystemExit("unknown case %r (k6, pergate, batch, c128, channel)" % mode)
     torch.cuda.synchronize()
     print("ok", mode)
 
