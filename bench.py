@@ -742,6 +742,31 @@ def run_extras(args, sim, C, dev, model):
                                                 "achieved_GBps": cfg["alg_scratch_bytes"] / tb / 1e9,
                                                 "frac": cfg["alg_scratch_bytes"] / tb / 1e9 / peaks["hbm_gbs"]}},
                            "note": "wall time of sim_batch_run (graph launch + readback of 4096 <sum Z> values)"}
+    # the learned plan on held-out mixed circuits (stretches of different circuit families) at
+    # register sizes where the best plan changes, against every fixed variant
+    from paper_1805_00988_gb300 import costmodel
+    mixes = (("haar", "graph", "haar", "graph"), ("graph", "qft", "haar"), ("rev", "phase", "ladder", "graph"))
+    rows = []
+    for n in (18, 22, 26, 28):
+        st = sim.State(n, "c64", device=dev)
+        sim.sim_set_cost_model(st.h, model)
+        W = costmodel.window_size(n)
+        for i, kinds in enumerate(mixes):
+            sgm = sim.to_sim_gates(C.segments(n, kinds, 2 * W, seed=900 + i))
+            r = {"n": n, "circuit": "+".join(kinds), "gates": len(sgm),
+                 "learned": costmodel.time_window(st, sgm, sim.plan_opts("learned"), 3),
+                 "learned_plan": [sim.VARIANTS[int(v)] for v in sim.sim_last_plan(st.h)]}
+            for v in range(sim.N_VARIANTS):
+                r[sim.VARIANTS[v]] = costmodel.time_window(st, sgm, sim.variant_opts(v), 3)
+            rows.append(r)
+        st.close()
+    names = list(sim.VARIANTS)
+    out["learned_vs_fixed_heldout"] = {
+        "unit": "ms (median of 3, CUDA events)", "rows": rows,
+        "geomean_learned_over_fixed": {v: float(np.exp(np.mean([np.log(r["learned"] / r[v]) for r in rows])))
+                                       for v in names},
+        "geomean_learned_over_best_fixed": float(np.exp(np.mean([np.log(r["learned"] / min(r[v] for v in names))
+                                                                 for r in rows])))}
     # density matrix of 15 qubits (a 30-qubit register, 8 GiB complex64): the 30-qubit workload's
     # gate distribution at depth 20, each layer followed by depolarizing (1e-3) and amplitude
     # damping (2e-3) on every qubit; gates as G rho G^dagger on the register, one pass per channel

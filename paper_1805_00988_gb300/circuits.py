@@ -32,6 +32,7 @@ of the dense random / variational circuits the simulator is measured on):
     haar_cz          layers of Haar-random 1q unitaries + CZ on a random matching
     phase_polynomial diagonal gates only (controlled phases, RZ, P, T, S, Z)
     reversible       permutation gates only (X, CNOT, Toffoli, SWAP)
+    graph_state      H on every qubit, then CZ on random edges (cluster states)
     segments         consecutive stretches of the above (mixed circuits)
     variational      batched RY/RZ layers + CZ ring, uneven qubit counts
     bernstein_vazirani   the App. C worked example
@@ -231,12 +232,35 @@ def reversible(n: int, m: int, seed: int) -> np.ndarray:
     return g
 
 
+def graph_state(n: int, m: int, seed: int) -> np.ndarray:
+    """m gates of graph-state (cluster-state) preparation, the entangling
+    stage of measurement-based and IQP-type circuits: H on every qubit, then
+    CZ on random edges, with a Z or S on a random qubit every eighth gate."""
+    rng = np.random.default_rng(seed)
+    g = empty(m)
+    for k in range(m):
+        if k < min(n, m):
+            g["name"][k] = "h"
+            g["target"][k] = k
+            continue
+        qs = rng.permutation(n)
+        if k % 8 == 0 or n < 2:
+            g["name"][k] = "z" if rng.random() < 0.5 else "s"
+            g["target"][k] = qs[0]
+            continue
+        g["name"][k] = "z"
+        g["target"][k] = qs[0]
+        g["nctrl"][k] = 1
+        g["ctrl"][k, 0] = qs[1]
+    return g
+
+
 def segments(n: int, kinds, seg_gates: int, seed: int) -> np.ndarray:
     """A circuit made of consecutive segments of about seg_gates gates each,
     of the given kinds: "haar" (layers of haar_cz), "phase"
     (phase_polynomial), "qft" (the textbook QFT, whatever its length),
     "ladder" (layers of u3_cnot_ladder), "rev" (reversible: X / CNOT /
-    Toffoli / SWAP).  Circuits whose best plan differs from one stretch of
+    Toffoli / SWAP), "graph" (graph-state preparation: H, then CZ edges).  Circuits whose best plan differs from one stretch of
     gates to the next."""
     parts = []
     for i, kind in enumerate(kinds):
@@ -251,6 +275,8 @@ def segments(n: int, kinds, seg_gates: int, seed: int) -> np.ndarray:
             parts.append(u3_cnot_ladder(n, max(1, round(seg_gates / (2 * n - 1))), seed=sd))
         elif kind == "rev":
             parts.append(reversible(n, seg_gates, seed=sd))
+        elif kind == "graph":
+            parts.append(graph_state(n, seg_gates, seed=sd))
         else:
             raise ValueError(kind)
     return concat(parts)

@@ -38,6 +38,8 @@ def families(n: int, seed: int):
     yield "variational", C.variational_layered(n, 8, rng)
     yield "random", C.random_gates(n, 12 * n, seed=seed)
     yield "phase", C.phase_polynomial(n, 12 * n, seed=seed)
+    yield "reversible", C.reversible(n, 12 * n, seed=seed)
+    yield "graph", C.graph_state(n, 12 * n, seed=seed)
 
 
 def time_window(st, sg, opts, reps: int) -> float:

@@ -98,56 +98,72 @@ int learned_choose(qsim_state *s, const sim_gate *gates, size_t n_gates, std::ve
     const size_t W = (size_t)std::max(64, 8 * s->n);
     std::vector<Window> win;
     for (size_t f = 0; f < n_gates; f += W) win.push_back(Window{f, std::min(W, n_gates - f)});
-    // candidate segments: every window, and the whole circuit (segment nw)
     const size_t nw = win.size();
-    std::vector<Window> seg(win);
-    if (nw > 1) seg.push_back(Window{0, n_gates});
-    std::vector<std::pair<size_t, int>> cand;
-    for (size_t w = 0; w < seg.size(); ++w)
-        for (int v = 0; v < SIM_VARIANTS; ++v)
-            if (feasible(s->n, s->dtype, v)) cand.push_back({w, v});
-    std::vector<float> feat(cand.size() * SIM_FEATURES);
-    std::vector<char> ok(cand.size(), 0);
-    // rows in reverse: the whole-circuit segment (the longest rows, its block
-    // planner runs over every gate) starts first instead of after the windows
-    parallel_for(cand.size(), [&](size_t i) {
-        const size_t r = cand.size() - 1 - i;
-        const Window &w = seg[cand[r].first];
-        ok[r] = plan_features(s->n, s->dtype, gates + w.first, w.count, cand[r].second,
-                              feat.data() + r * SIM_FEATURES) == SIM_OK;
-    });
-    std::vector<float> rows;
-    std::vector<std::pair<size_t, int>> who;
-    for (size_t r = 0; r < cand.size(); ++r)
-        if (ok[r]) {
-            rows.insert(rows.end(), feat.begin() + r * SIM_FEATURES, feat.begin() + (r + 1) * SIM_FEATURES);
-            who.push_back(cand[r]);
-        }
-    std::vector<float> pred(who.size());
-    if (int rc = sim_mlp_forward((qsim_mlp *)s->cost_model, rows.data(), (int64_t)who.size(), pred.data(), 0)) return rc;
+    // predicted log times of the feasible variants of some segments, the
+    // feature rows in parallel on the host threads, one batched forward pass
+    struct Pred { size_t seg; int v; float p; };
+    auto predict = [&](const std::vector<Window> &segs, std::vector<Pred> *out) -> int {
+        std::vector<std::pair<size_t, int>> cand;
+        for (size_t w = 0; w < segs.size(); ++w)
+            for (int v = 0; v < SIM_VARIANTS; ++v)
+                if (feasible(s->n, s->dtype, v)) cand.push_back({w, v});
+        std::vector<float> feat(cand.size() * SIM_FEATURES);
+        std::vector<char> ok(cand.size(), 0);
+        parallel_for(cand.size(), [&](size_t r) {
+            const Window &w = segs[cand[r].first];
+            ok[r] = plan_features(s->n, s->dtype, gates + w.first, w.count, cand[r].second,
+                                  feat.data() + r * SIM_FEATURES) == SIM_OK;
+        });
+        std::vector<float> rows;
+        out->clear();
+        for (size_t r = 0; r < cand.size(); ++r)
+            if (ok[r]) {
+                rows.insert(rows.end(), feat.begin() + r * SIM_FEATURES, feat.begin() + (r + 1) * SIM_FEATURES);
+                out->push_back(Pred{cand[r].first, cand[r].second, 0.f});
+            }
+        std::vector<float> pred(out->size());
+        if (!out->empty())
+            if (int rc = sim_mlp_forward((qsim_mlp *)s->cost_model, rows.data(), (int64_t)out->size(), pred.data(), 0))
+                return rc;
+        for (size_t r = 0; r < out->size(); ++r) (*out)[r].p = pred[r];
+        return SIM_OK;
+    };
+    std::vector<Pred> pw;
+    if (int rc = predict(win, &pw)) return rc;
     std::vector<int> &best = *best_out;
     best.assign(nw, -1);
     std::vector<float> bestp(nw, 0.f);
-    int whole_v = -1;
-    float whole_p = 0.f;
-    for (size_t r = 0; r < who.size(); ++r) {
-        const size_t w = who[r].first;
-        if (w < nw) {
-            if (best[w] < 0 || pred[r] < bestp[w]) { best[w] = who[r].second; bestp[w] = pred[r]; }
-        } else if (whole_v < 0 || pred[r] < whole_p) {
-            whole_v = who[r].second;
-            whole_p = pred[r];
-        }
-    }
-    // predicted times: the model's target is a log time, so windows add in exp
-    if (whole_v >= 0) {
+    for (const Pred &x : pw)
+        if (best[x.seg] < 0 || x.p < bestp[x.seg]) { best[x.seg] = x.v; bestp[x.seg] = x.p; }
+    bool agree = true;
+    for (size_t w = 0; w < nw; ++w) agree = agree && best[w] >= 0 && best[w] == best[0];
+    // when the windows disagree, compare their mix with one variant over the
+    // whole circuit (its block and pass planners work across window
+    // boundaries, which per-window predictions cannot see); when they agree,
+    // the windows run as one call of that variant anyway, and the costly
+    // whole-circuit rows are skipped
+    if (!agree && nw > 1) {
+        std::vector<Pred> pwhole;
+        if (int rc = predict(std::vector<Window>{Window{0, n_gates}}, &pwhole)) return rc;
+        int whole_v = -1;
+        float whole_p = 0.f;
+        for (const Pred &x : pwhole)
+            if (x.v != 0 && (whole_v < 0 || x.p < whole_p)) { whole_v = x.v; whole_p = x.p; }
+        // predicted times: the model's target is a log time, so windows add in
+        // exp.  A mix must win by a margin: each prediction is off by about
+        // the model's log-time RMSE (0.06-0.08 on its training timings), and a
+        // mix also loses the blocks and passes that would span its window
+        // boundaries; so the mix runs only if it is predicted faster than the
+        // whole-circuit variant by twice that error, exp(-2 x 0.084).
+        constexpr double kMixMargin = 0.845;
         double mix = 0;
         bool all = true;
         for (size_t w = 0; w < nw; ++w) {
             if (best[w] < 0) all = false;
             else mix += std::exp((double)bestp[w]);
         }
-        if (!all || std::exp((double)whole_p) <= mix) std::fill(best.begin(), best.end(), whole_v);
+        if (whole_v >= 0 && (!all || mix > kMixMargin * std::exp((double)whole_p)))
+            std::fill(best.begin(), best.end(), whole_v);
     }
     s->last_plan.assign(best.begin(), best.end());
     return SIM_OK;
