@@ -137,33 +137,35 @@ int learned_choose(qsim_state *s, const sim_gate *gates, size_t n_gates, std::ve
         if (best[x.seg] < 0 || x.p < bestp[x.seg]) { best[x.seg] = x.v; bestp[x.seg] = x.p; }
     bool agree = true;
     for (size_t w = 0; w < nw; ++w) agree = agree && best[w] >= 0 && best[w] == best[0];
-    // when the windows disagree, compare their mix with one variant over the
-    // whole circuit (its block and pass planners work across window
-    // boundaries, which per-window predictions cannot see); when they agree,
-    // the windows run as one call of that variant anyway, and the costly
-    // whole-circuit rows are skipped
+    // When the windows disagree, the mix of per-window argmins is compared
+    // with the best single variant for the whole circuit, whose time is
+    // predicted as the sum of its window predictions (running it as one call
+    // can only do better: its block and pass planners then work across window
+    // boundaries; fused k = 5 on the 30-qubit workload took 356 ms as four
+    // windows and 261 ms as one call).  The mix must win by a margin: each
+    // prediction is off by about the model's log-time RMSE (0.06-0.08 on its
+    // training timings), so the mix runs only if it is predicted faster by
+    // twice that error, a factor exp(-2 x 0.084).  No planner runs over the
+    // whole circuit here: those feature rows cost more host time than the
+    // windows' rows together.
     if (!agree && nw > 1) {
-        std::vector<Pred> pwhole;
-        if (int rc = predict(std::vector<Window>{Window{0, n_gates}}, &pwhole)) return rc;
-        int whole_v = -1;
-        float whole_p = 0.f;
-        for (const Pred &x : pwhole)
-            if (x.v != 0 && (whole_v < 0 || x.p < whole_p)) { whole_v = x.v; whole_p = x.p; }
-        // predicted times: the model's target is a log time, so windows add in
-        // exp.  A mix must win by a margin: each prediction is off by about
-        // the model's log-time RMSE (0.06-0.08 on its training timings), and a
-        // mix also loses the blocks and passes that would span its window
-        // boundaries; so the mix runs only if it is predicted faster than the
-        // whole-circuit variant by twice that error, exp(-2 x 0.084).
         constexpr double kMixMargin = 0.845;
+        std::vector<double> uni(SIM_VARIANTS, 0.0);
+        std::vector<size_t> seen(SIM_VARIANTS, 0);
+        for (const Pred &x : pw) {
+            uni[x.v] += std::exp((double)x.p);
+            seen[x.v]++;
+        }
+        int whole_v = -1;
+        for (int v = 0; v < SIM_VARIANTS; ++v)
+            if (seen[v] == nw && (whole_v < 0 || uni[v] < uni[whole_v])) whole_v = v;
         double mix = 0;
         bool all = true;
         for (size_t w = 0; w < nw; ++w) {
             if (best[w] < 0) all = false;
             else mix += std::exp((double)bestp[w]);
         }
-        if (whole_v >= 0 && (!all || mix > kMixMargin * std::exp((double)whole_p)))
-            std::fill(best.begin(), best.end(), whole_v);
+        if (whole_v >= 0 && (!all || mix > kMixMargin * uni[whole_v])) std::fill(best.begin(), best.end(), whole_v);
     }
     s->last_plan.assign(best.begin(), best.end());
     return SIM_OK;

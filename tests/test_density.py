@@ -231,3 +231,37 @@ def test_full_size_noisy_register(sim, dm):
     assert float((tb[r, c] - tb[c, r].conj()).abs().max()) <= 1e-12 * float(tb.diagonal().abs().max())
     a.close()
     b.close()
+
+
+def test_maximum_density_matrix_17_qubits(sim):
+    """The largest density matrix (17 qubits: a 34-qubit register, 128 GiB in
+    complex64): H on the top qubit and a depolarizing channel (p = 0.2)
+    there; the trace is 1, the diagonal 1/2 on |0...0> and |10...0>, and the
+    purity that of a Bloch vector of length 1 - p: (1 + (1 - p)^2) / 2."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    if free < 140 * 2 ** 30:
+        pytest.skip("needs 140 GiB of free device memory")
+    n = 17
+    import ctypes
+    P = ctypes.c_void_p
+    h = P()
+    lib = sim.lib_handle()
+    assert lib.sim_dm_create(n, sim.SIM_C64, P(1), ctypes.byref(h)) == sim.SIM_OK, sim.last_error()
+    lib_h = h.value
+    try:
+        gh = sim.to_sim_gates(C.concat([C.gate("h", n - 1), C.channel("dep", n - 1, 0.2)]))
+        sim.sim_dm_apply_circuit(lib_h, gh, sim.plan_opts("per_gate"))
+        tr, pu = ctypes.c_double(), ctypes.c_double()
+        assert lib.sim_dm_trace(P(lib_h), ctypes.byref(tr)) == sim.SIM_OK
+        assert lib.sim_dm_purity(P(lib_h), ctypes.byref(pu)) == sim.SIM_OK
+        assert abs(tr.value - 1.0) < 1e-6
+        # |+><+| depolarized with p: Bloch vector length 1 - p, purity (1 + (1 - p)^2) / 2
+        assert abs(pu.value - (1 + 0.8 ** 2) / 2) < 1e-6
+        p = torch.empty(2 ** n, dtype=torch.float64, device="cuda")
+        assert lib.sim_dm_probabilities(P(lib_h), P(p.data_ptr()), sim.SIM_F64) == sim.SIM_OK
+        torch.cuda.synchronize()
+        assert abs(float(p[0]) - 0.5) < 1e-6 and abs(float(p[1 << (n - 1)]) - 0.5) < 1e-6
+        assert float(p.sum()) == pytest.approx(1.0, abs=1e-6)
+    finally:
+        sim.sim_destroy(lib_h)

@@ -58,7 +58,6 @@ def test_learned_plan_matches_oracle(trained, orc, fam):
 # above.
 HELDOUT_SIZES = (18, 20, 22, 24, 26, 28)
 HELDOUT_MIXES = (("haar", "graph", "haar", "graph"), ("graph", "qft", "haar"), ("rev", "phase", "ladder", "graph"))
-GREEDY_K = ("fused:3", "fused:4", "fused:5", "fused:6")
 
 
 @pytest.fixture(scope="module")
@@ -91,18 +90,20 @@ def geomean(xs):
 
 
 @pytest.mark.gpu
-def test_learned_plan_beats_the_greedy_fixed_k_plans(heldout_times):
+def test_learned_plan_beats_every_fixed_plan(heldout_times):
     """What the trained network gains over the method without it: on the
-    held-out set, the learned plan beats the greedy fixed-k fallback (fused
-    blocks of the largest k) and every other fixed block size k in geometric
-    mean over the circuits, without slack; measured geometric means of
-    t_learned / t_fixed were 0.56-0.70.  (Register tiles, not a fixed-k plan,
-    beat it below 24 qubits, where the model's feature rows cost the learned
-    plan 1.5-2 ms of host time against 1-4 ms circuits.)"""
+    held-out set the learned plan beats, in geometric mean of t_learned /
+    t_fixed over the circuits and without slack, the greedy fixed-k fallback
+    (fused blocks of the largest k), every other block size k, the register
+    tiles of either size and the per-gate plan.  Measured: 0.51 against fused
+    k = 6, 0.41-0.47 against k = 3..5, 0.92 / 0.96 against 13- / 12-qubit
+    register tiles, 0.27 against per gate; no single fixed plan is best over
+    the whole size range, and the model switches at about 24 qubits."""
+    from paper_1805_00988_gb300 import sim
     rows = heldout_times
-    for k in GREEDY_K:
-        ratio = geomean([r["learned"] / r[k] for r in rows])
-        assert ratio < 1.0, (k, ratio, rows)
+    for v in sim.VARIANTS:
+        ratio = geomean([r["learned"] / r[v] for r in rows])
+        assert ratio < 1.0, (v, ratio, rows)
 
 
 @pytest.mark.gpu
