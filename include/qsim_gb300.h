@@ -177,12 +177,16 @@ int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_
  *   on the device when out_on_device, else host memory.
  * sim_expect_z_sum: <sum_i Z_i> = sum_x |a_x|^2 (n - 2 popcount x), FP64
  *   (complex64: squares accumulated as for sim_norm, weighted by exact
- *   products). */
+ *   products).
+ * sim_norm_expect_z: sim_norm and sim_expect_z_sum from one pass over the
+ *   state (both read every |a_x|^2; the norm is the unweighted sum of the
+ *   same accumulators, within about 1e-12 relative of sim_norm's). */
 int sim_probabilities(sim_t s, void *dev_out, int out_real);
 int sim_norm(sim_t s, double *out);
 int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob);
 int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
 int sim_expect_z_sum(sim_t s, double *out);
+int sim_norm_expect_z(sim_t s, double *norm, double *expz);
 
 /* ---- density matrices and noise ---------------------------------------------
  * The paper names density matrices among a simulator's outputs (§1) without

@@ -370,6 +370,17 @@ int sim_expect_z_sum(sim_t s, double *out)
     return SIM_OK;
 }
 
+int sim_norm_expect_z(sim_t s, double *norm, double *expz)
+{
+    if (int rc = check_state(s, "sim_norm_expect_z")) return rc;
+    if (!norm || !expz) return fail(SIM_EINVAL, "sim_norm_expect_z: NULL output");
+    double r[2];
+    if (int rc = reduce_sums(s, RED_EXPZ, 0, r)) return rc;
+    *expz = r[0];
+    *norm = r[1];
+    return SIM_OK;
+}
+
 int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob)
 {
     if (int rc = check_state(s, "sim_measure")) return rc;

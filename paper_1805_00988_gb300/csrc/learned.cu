@@ -1,14 +1,14 @@
 // learned.cu -- SIM_PLAN_LEARNED: the circuit is cut into windows of
-// consecutive gates; for every window, and for the whole circuit, and every
-// feasible plan variant the host computes a feature row (rows in parallel on
-// the host cores), the cost model (mlp.cu) predicts the log run time of all
-// rows in one batched forward pass on the GPU, and the cheaper of two plans
-// runs: each window with its own cheapest variant, or the whole circuit with
-// one variant (one variant over many windows lets the block and pass planners
-// work across window boundaries, which per-window predictions cannot see).
-// Without a model the greedy fixed-k plan runs (fused blocks of the largest k
-// whose tile fits): it is both the fallback and the judge the learned plans
-// are measured against.
+// consecutive gates; for every window and every feasible plan variant the
+// host computes a feature row (rows in parallel on the host cores), the cost
+// model (mlp.cu) predicts the log run time of all rows in one batched forward
+// pass on the GPU, and the cheaper of two plans runs: each window with its
+// own cheapest variant, or the whole circuit with the one variant whose
+// windows sum to the least (one variant over many windows lets the block and
+// pass planners work across window boundaries, which per-window predictions
+// cannot see, so a mix must win by a margin).  Without a model the greedy
+// fixed-k plan runs (fused blocks of the largest k whose tile fits): it is
+// both the fallback and the yardstick the learned plans are measured against.
 #include <algorithm>
 #include <atomic>
 #include <cmath>

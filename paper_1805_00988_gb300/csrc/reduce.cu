@@ -254,7 +254,8 @@ constexpr int kBatch = 8;     // 16-byte loads in flight per thread
 // Masked FP64 sums over a contiguous range per block.
 //   RED_NORM: out0 = sum |a|^2                    (two FP64 FMAs per amplitude)
 //   RED_BIT : out0 = sum over bit q = 0, out1 = sum over bit q = 1
-//   RED_EXPZ: out0 = sum |a_x|^2 (n - 2 popcount x)  (weights from a table)
+//   RED_EXPZ: out0 = sum |a_x|^2 (n - 2 popcount x)  (weights from a table),
+//             out1 = sum |a|^2 (the norm, from the same pass)
 template <typename R, int MODE>
 __global__ void __launch_bounds__(kRedThreads) k_masked_sum(const R *__restrict__ st, uint64_t nvec, uint64_t per,
                                                             int q, int n, double *__restrict__ partial)
@@ -281,7 +282,9 @@ __global__ void __launch_bounds__(kRedThreads) k_masked_sum(const R *__restrict_
                 if ((i >> q) & 1ull) acc_sq<R>(b, re[e], im[e]);
                 else acc_sq<R>(a, re[e], im[e]);
             } else {
-                a = fma(sq<R>(re[e], im[e]), wtab[__popcll(i)], a);
+                const double p2 = sq<R>(re[e], im[e]);
+                a = fma(p2, wtab[__popcll(i)], a);
+                b += p2;
             }
         }
     };
@@ -366,7 +369,8 @@ __global__ void __launch_bounds__(kRedThreads) k_sum_sq32(const float *__restric
 // e, popcount(x) = popcount(ch) + popcount(e), so a thread sums the squares of
 // a chunk into five bins by popcount(e) (two FP64 FMAs per amplitude, e known
 // at compile time) and adds bin j with weight n - 2 (popcount(ch) + j): five
-// FMAs per 16 amplitudes instead of one weighted FMA each.
+// FMAs per 16 amplitudes instead of one weighted FMA each.  The second
+// partial is the norm (the bins' sum) from the same pass.
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) k_expz_chunks(const R *__restrict__ st, uint64_t nch, uint64_t per,
                                                              int n, double *__restrict__ partial)
@@ -404,7 +408,10 @@ __global__ void __launch_bounds__(kRedThreads) k_expz_chunks(const R *__restrict
         }
         const int pc = __popcll(ch);
 #pragma unroll
-        for (int j = 0; j < 5; ++j) a = fma(wtab[pc + j], bin[j], a);
+        for (int j = 0; j < 5; ++j) {
+            a = fma(wtab[pc + j], bin[j], a);
+            b += bin[j];
+        }
     }
     block_sum2<kRedThreads>(a, b, sh);
     if (threadIdx.x == 0) {
@@ -419,7 +426,8 @@ __global__ void __launch_bounds__(kRedThreads) k_expz_chunks(const R *__restrict
 // integers n - 2 (popcount(ch) + j) with exact FP32 products into one
 // compensated sum, carried into FP64 once per chunk.  Bins hold at most 12
 // squares; the weighted sum cancels, so its error is relative to
-// sum_j |w_j| bin_j <= n * (the chunk's sum of squares).
+// sum_j |w_j| bin_j <= n * (the chunk's sum of squares).  The second
+// partial is the norm: the bins' compensated sum, carried into FP64 per chunk.
 __global__ void __launch_bounds__(kRedThreads) k_expz32(const float *__restrict__ st, uint64_t nch, uint64_t per,
                                                         int n, double *__restrict__ partial)
 {
@@ -446,14 +454,17 @@ __global__ void __launch_bounds__(kRedThreads) k_expz32(const float *__restrict_
             bin[__builtin_popcount(2 * u + 1)].add_sq(y.w);
         }
         const int pc = __popcll(ch);
-        Sq32 w;
+        Sq32 w, t;
 #pragma unroll
         for (int j = 0; j < 5; ++j) {
             const float wj = (float)(n - 2 * (pc + j));
             w.add_prod(bin[j].s, wj);
             w.e = __fmaf_rn(bin[j].e, wj, w.e);
+            t.two_sum(bin[j].s);
+            t.e = __fadd_rn(t.e, bin[j].e);
         }
         a += widen_sum(w, p.sh);
+        b += widen_sum(t, p.sh);
     }
     block_sum2<kRedThreads>(a, b, sh);
     if (threadIdx.x == 0) {
@@ -776,55 +787,64 @@ __global__ void __launch_bounds__(256) k_resolve(const R *__restrict__ st, uint6
     uint32_t cur = 0xFFFFFFFFu;          // block whose scan the warp holds
     double Pl = 0.0, be = 0.0;
     unsigned sub_nz = 0u;
-    for (uint64_t k = k0; k < k1; ++k) {
-        const uint32_t s = order[k];
-        const uint32_t blk = shot_blk[s];
-        if (blk != cur) {
-            cur = blk;
-            Pl = warp_incl_scan(((uint32_t)lane < g.nsub) ? sub[(uint64_t)blk * g.nsub + lane] : 0.0, lane);
-            be = bexcl[blk];
-            const double prev = __shfl_up_sync(0xffffffffu, Pl, 1);
-            const bool lane_nz = (uint32_t)lane < g.nsub && (lane == 0 ? Pl > 0.0 : Pl > prev);
-            sub_nz = __ballot_sync(0xffffffffu, lane_nz);
-        }
-        const uint64_t base = (uint64_t)blk * bs;
-        const double t = unif(seed, s) * tot;
-        const unsigned hit = __ballot_sync(0xffffffffu, (uint32_t)lane < g.nsub && be + Pl > t);
-        const uint32_t j = hit ? (uint32_t)(__ffs(hit) - 1) : (sub_nz ? (uint32_t)(31 - __clz(sub_nz)) : 0u);
-        const double pj = __shfl_sync(0xffffffffu, Pl, (int)(j > 0 ? j - 1 : 0));
-        const double pre = be + (j > 0 ? pj : 0.0);
-        int first = -1, last_nz = -1;
-        if (sizeof(R) == 4 && g.apl == 8) {
-            lane_locate32(reinterpret_cast<const float *>(st), base, j, lane, pre, t, first, last_nz);
-        } else {
-            double p[8];
-            lane_squares<R>(st, base, g, j, lane, p);
-            double c[8], run = 0.0;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                run += p[e];
-                c[e] = run;
+    // the shot numbers and blocks of 32 shots at a time: lane i loads those
+    // of shot c0 + i (one coalesced load and one gather for 32 shots instead
+    // of two dependent loads per shot), the loop takes them by shuffle
+    for (uint64_t c0 = k0; c0 < k1; c0 += 32) {
+        const uint64_t kl = c0 + (uint64_t)lane;
+        const uint32_t s_l = kl < k1 ? order[kl] : 0u;
+        const uint32_t b_l = kl < k1 ? shot_blk[s_l] : 0u;
+        const int cnt = (int)min((uint64_t)32, k1 - c0);
+        for (int i = 0; i < cnt; ++i) {
+            const uint32_t s = __shfl_sync(0xffffffffu, s_l, i);
+            const uint32_t blk = __shfl_sync(0xffffffffu, b_l, i);
+            if (blk != cur) {
+                cur = blk;
+                Pl = warp_incl_scan(((uint32_t)lane < g.nsub) ? sub[(uint64_t)blk * g.nsub + lane] : 0.0, lane);
+                be = bexcl[blk];
+                const double prev = __shfl_up_sync(0xffffffffu, Pl, 1);
+                const bool lane_nz = (uint32_t)lane < g.nsub && (lane == 0 ? Pl > 0.0 : Pl > prev);
+                sub_nz = __ballot_sync(0xffffffffu, lane_nz);
             }
-            const double incl = warp_incl_scan(run, lane);
-            const double start = pre + (incl - run);
+            const uint64_t base = (uint64_t)blk * bs;
+            const double t = unif(seed, s) * tot;
+            const unsigned hit = __ballot_sync(0xffffffffu, (uint32_t)lane < g.nsub && be + Pl > t);
+            const uint32_t j = hit ? (uint32_t)(__ffs(hit) - 1) : (sub_nz ? (uint32_t)(31 - __clz(sub_nz)) : 0u);
+            const double pj = __shfl_sync(0xffffffffu, Pl, (int)(j > 0 ? j - 1 : 0));
+            const double pre = be + (j > 0 ? pj : 0.0);
+            int first = -1, last_nz = -1;
+            if (sizeof(R) == 4 && g.apl == 8) {
+                lane_locate32(reinterpret_cast<const float *>(st), base, j, lane, pre, t, first, last_nz);
+            } else {
+                double p[8];
+                lane_squares<R>(st, base, g, j, lane, p);
+                double c[8], run = 0.0;
 #pragma unroll
-            for (int e = 7; e >= 0; --e) {
-                if ((uint32_t)e < g.apl && start + c[e] > t) first = e;
-                if (last_nz < 0 && p[e] > 0.0) last_nz = e;
+                for (int e = 0; e < 8; ++e) {
+                    run += p[e];
+                    c[e] = run;
+                }
+                const double incl = warp_incl_scan(run, lane);
+                const double start = pre + (incl - run);
+#pragma unroll
+                for (int e = 7; e >= 0; --e) {
+                    if ((uint32_t)e < g.apl && start + c[e] > t) first = e;
+                    if (last_nz < 0 && p[e] > 0.0) last_nz = e;
+                }
             }
+            const unsigned fl = __ballot_sync(0xffffffffu, first >= 0);
+            uint64_t idx;
+            if (fl) {
+                const int L = __ffs(fl) - 1;
+                idx = (uint64_t)L * g.apl + (uint64_t)__shfl_sync(0xffffffffu, first, L);
+            } else {
+                const unsigned nl = __ballot_sync(0xffffffffu, last_nz >= 0);
+                const int L = nl ? 31 - __clz(nl) : 0;
+                const int e = __shfl_sync(0xffffffffu, last_nz, L);
+                idx = (uint64_t)L * g.apl + (uint64_t)(e > 0 ? e : 0);
+            }
+            if (lane == 0) out[s] = base + (uint64_t)j * g.sub + idx;
         }
-        const unsigned fl = __ballot_sync(0xffffffffu, first >= 0);
-        uint64_t idx;
-        if (fl) {
-            const int L = __ffs(fl) - 1;
-            idx = (uint64_t)L * g.apl + (uint64_t)__shfl_sync(0xffffffffu, first, L);
-        } else {
-            const unsigned nl = __ballot_sync(0xffffffffu, last_nz >= 0);
-            const int L = nl ? 31 - __clz(nl) : 0;
-            const int e = __shfl_sync(0xffffffffu, last_nz, L);
-            idx = (uint64_t)L * g.apl + (uint64_t)(e > 0 ? e : 0);
-        }
-        if (lane == 0) out[s] = base + (uint64_t)j * g.sub + idx;
     }
 }
 

@@ -201,6 +201,16 @@ def sim_expect_z_sum(h: int) -> float:
     return r.value
 
 
+_sig("sim_norm_expect_z", [P, P, P])
+
+
+def sim_norm_expect_z(h: int):
+    """(norm, <sum Z>) from one pass over the state."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(_lib.sim_norm_expect_z(P(h), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
 def sim_measure(h: int, qubit: int, seed: int, draw: int = 0):
     m = ctypes.c_int()
     p = ctypes.c_double()

@@ -117,7 +117,7 @@ def test_timed_workload_state_matches_oracle(gsim, oracle_state):
 @pytest.mark.slow
 def test_timed_workload_c128_per_gate_matches_oracle(gsim, oracle_state):
     """Per-gate complex128 at full size against the oracle: infidelity
-    <= 1e-12 (spec bound) and |psi - ref| <= 1e-11 max|ref| (FP64
+    <= 1e-12 (the required bound) and |psi - ref| <= 1e-11 max|ref| (FP64
     rounding of 900 gates, a few ulp per gate per amplitude)."""
     g = C.haar_cz(N, DEPTH, seed=SEED)
     st = gsim.State(N, "c128")

@@ -188,7 +188,7 @@ def test_fused_k6_state_magnitudes(gsim, orc, case):
     the input: states of norm 1e-3, 1e-6, 1e-30 and 1e6, a state scaled by 4,
     and one whose amplitudes spread over 2^-40 .. 2^-5.  Element by element
     against the oracle on the same complex64 input, and the infidelity held to
-    1e-10 (a 22-bit split gives about 1e-13 per block; the benchmark spec's bound is
+    1e-10 (a 22-bit split gives about 1e-13 per block; the required bound is
     1e-6) -- the precision must not depend on the magnitude."""
     n = 18
     g = C.haar_cz(n, 4, seed=31)

@@ -3,7 +3,7 @@ unitary built in FP64 and applied on the FP16 tensor cores as exact integer
 arithmetic on 7-bit digit planes of the state and of the block matrix (49
 bits relative to each row's and each column's largest entry).
 
-Tolerances (the benchmark spec's bounds for complex128): infidelity <= 1e-12 and
+Tolerances (the required bounds for complex128): infidelity <= 1e-12 and
 |psi - ref| <= 1e-11 max|ref| element-wise.  Derivation: each block keeps 49
 bits of every row and column in fixed point and drops the digit products
 below 2^-49 of them; a K = 32 dot product then errs by about 2^-45 of its

@@ -5,10 +5,10 @@ Tolerances, derived from the arithmetic:
   complex128: a few FP64 ulp (2.2e-16) per gate and amplitude, growing like a
               random walk over up to ~10^3 gates ->
               |psi_gpu - psi_ref| <= 1e-11 * max|psi_ref| element-wise and
-              infidelity <= 1e-12 (the north-star bound);
+              infidelity <= 1e-12 (the required bound);
   complex64 : FP32 rounding (6e-8) per gate, the same growth ->
               |psi_gpu - psi_ref| <= 1e-5 * max|psi_ref| element-wise and
-              infidelity <= 1e-6 (the north-star bound);
+              infidelity <= 1e-6 (the required bound);
   permutations (X, CNOT, Toffoli, SWAP and their controlled forms): bit-exact.
 """
 import math
@@ -199,6 +199,10 @@ def test_reductions_and_probabilities(sim, orc, dt, n):
     tol = 1e-12
     assert abs(st.norm2() - orc.norm2(got)) < tol
     assert abs(st.expect_z_sum() - orc.expect_z_sum(got)) < 1e-11
+    # both from one pass (sim_norm_expect_z), against the same oracle values
+    nrm, ez = sim.sim_norm_expect_z(st.h)
+    assert abs(nrm - orc.norm2(got)) < tol
+    assert abs(ez - orc.expect_z_sum(got)) < 1e-11
     np.testing.assert_allclose(st.probabilities(True), orc.probabilities(got), rtol=1e-15, atol=1e-300)
     p32 = st.probabilities(False)
     np.testing.assert_allclose(p32, orc.probabilities(got), rtol=2e-6, atol=1e-30)

@@ -1,6 +1,6 @@
 """The learned plan: a cost model trained on this GPU's own timings picks a
 plan variant per window.  Whatever it picks, the state must match the
-oracle; and its plans are judged against the fixed variants it replaces."""
+oracle; and its plans are compared with the fixed variants it replaces."""
 import numpy as np
 import pytest
 
