@@ -357,10 +357,10 @@ def run_reference(args, rank, world):
 def load_cost_model(sim):
     """The plan cost model trained on this machine's GB300 (parameters shipped
     with the package); None when absent (the learned plan then falls back to
-    the greedy tile planner)."""
+    the greedy fixed-k plan)."""
     from paper_1805_00988_gb300 import costmodel
     if not os.path.exists(costmodel.DEFAULT_PATH):
-        return None, {"cost_model": "absent: greedy tile planner used"}
+        return None, {"cost_model": "absent: greedy fixed-k plan used"}
     m, info = costmodel.load()
     return m, {"cost_model": info}
 
@@ -801,7 +801,7 @@ def run_extras(args, sim, C, dev, model):
     res["note"] = "15-qubit density matrix, complex64; ops = gates + channels; best of 1 after a warm run"
     out["noisy_haar_cz_15q_density"] = res
     rho.close()
-    # 33 qubits, depth 24 (64 GiB complex64): learned plan vs the greedy tile planner, then 10^6 shots
+    # 33 qubits, depth 24 (64 GiB complex64): learned plan vs greedy register tiles and greedy fixed-k fused blocks, then 10^6 shots
     if args.c5:
         n5 = 33
         g5 = sim.to_sim_gates(C.haar_cz(n5, 24, seed=SEED))
