@@ -669,6 +669,62 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_exclusive(const T *__rest
     }
 }
 
+// Exclusive scan over many CTAs (the sampler's block sums are FP64, and one
+// CTA adding 2^17 of them ran into the narrow FP64 pipe of a single SM):
+// chunks of kScanChunk values, four contiguous values per thread.  Pass 1
+// writes each chunk's total, the one-CTA scan above turns the totals into
+// chunk offsets (and the grand total), pass 2 repeats the chunk's local scan
+// (the same operations, so the same bits) and adds the chunk's offset.
+constexpr int kScanChunk = 1024;
+
+template <typename T>
+__device__ __forceinline__ T chunk_local_scan(const T *__restrict__ in, uint64_t nb, T *sh, T &total, T v[4],
+                                              uint64_t &lo)
+{
+    lo = (uint64_t)blockIdx.x * kScanChunk + 4u * threadIdx.x;
+    T loc = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        v[e] = (lo + e < nb) ? in[lo + e] : (T)0;
+        loc += v[e];
+    }
+    sh[threadIdx.x] = loc;
+    __syncthreads();
+    for (int off = 1; off < 256; off <<= 1) {
+        const T y = (threadIdx.x >= (unsigned)off) ? sh[threadIdx.x - off] : (T)0;
+        __syncthreads();
+        sh[threadIdx.x] += y;
+        __syncthreads();
+    }
+    total = sh[255];
+    return (threadIdx.x > 0) ? sh[threadIdx.x - 1] : (T)0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_scan_chunk_sums(const T *__restrict__ in, uint64_t nb, T *__restrict__ csum)
+{
+    __shared__ T sh[256];
+    T v[4], total;
+    uint64_t lo;
+    chunk_local_scan<T>(in, nb, sh, total, v, lo);
+    if (threadIdx.x == 0) csum[blockIdx.x] = total;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_scan_chunk_out(const T *__restrict__ in, uint64_t nb,
+                                                        const T *__restrict__ cexcl, T *__restrict__ out)
+{
+    __shared__ T sh[256];
+    T v[4], total;
+    uint64_t lo;
+    T run = chunk_local_scan<T>(in, nb, sh, total, v, lo) + cexcl[blockIdx.x];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        if (lo + e < nb) out[lo + e] = run;
+        run += v[e];
+    }
+}
+
 // shot s -> block: smallest b with bexcl[b] + bsum[b] > u_s * total; none ->
 // the last block with a non-zero sum.
 __global__ void k_locate(uint64_t shots, uint64_t seed, const double *__restrict__ bexcl,
@@ -710,15 +766,36 @@ __global__ void k_scatter(uint64_t shots, const uint32_t *__restrict__ shot_blk,
     }
 }
 
+// a power of two 2^d as a float for d <= 127; 0 below -126 (a lane that
+// small against the largest one contributes nothing measurable)
+__device__ __forceinline__ float pow2f(int d)
+{
+    return d < -126 ? 0.f : __uint_as_float((uint32_t)(127 + min(d, 127)) << 23);
+}
+
+// s + t as an unevaluated pair (hi, lo) (Knuth's TwoSum) added to (hi, lo)
+__device__ __forceinline__ void df_add(float &hi, float &lo, float th, float tl)
+{
+    const float u = __fadd_rn(hi, th);
+    const float z = __fsub_rn(u, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(u, z)), __fsub_rn(th, z));
+    hi = u;
+    lo = __fadd_rn(__fadd_rn(lo, tl), err);
+}
+
 // complex64, full sub-blocks (8 amplitudes per lane): lane `lane`'s part of
 // the in-sub-block search.  The lane's prefix is kept as compensated FP32
-// partial sums of its rescaled squares; its total (FP64) feeds the warp scan
-// that gives the lane's start; the target relative to that start, rescaled by
-// the same power of two and clamped far outside the lane's range, is split
-// into a float pair th + tl that each partial sum is compared with.  An
-// amplitude that is exactly zero leaves the prefix unchanged and is never the
-// first crossing.  first = the first crossing in the lane (-1: none), last_nz =
-// the last amplitude with non-zero probability (-1: none).  All 32 lanes call it.
+// partial sums of its squares rescaled by a power of two (2^-sh, from the
+// lane's largest component).  The lanes' totals are brought to one scale (the
+// warp's largest sh) by exact powers of two and scanned across the warp as
+// FP32 pairs (TwoSum), so the only FP64 work per shot is the target t - pre
+// in that scale: this GPU's FP64 pipe runs at a small fraction of its FP32
+// rate, and an FP64 warp scan per shot made the search FP64-bound.  The
+// target relative to the lane's start, rescaled back to the lane's units, is
+// compared with each partial sum as a float pair.  An amplitude that is
+// exactly zero leaves the prefix unchanged and is never the first crossing.
+// first = the first crossing in the lane (-1: none), last_nz = the last
+// amplitude with non-zero probability (-1: none).  All 32 lanes call it.
 __device__ __forceinline__ void lane_locate32(const float *st, uint64_t base, uint32_t j, int lane, double pre,
                                               double t, int &first, int &last_nz)
 {
@@ -744,18 +821,37 @@ __device__ __forceinline__ void lane_locate32(const float *st, uint64_t base, ui
         cs[2 * u + 1] = A.s; ce[2 * u + 1] = A.e;
         nz[2 * u + 1] = x[u].z != 0.f || x[u].w != 0.f;
     }
-    const double run = widen_sum(A, pw.sh);
-    const double incl = warp_incl_scan(run, lane);
-    const double start = pre + (incl - run);
-    double T = (t - start) * __longlong_as_double((long long)((uint64_t)(1023 - pw.sh) << 52));
-    T = fmin(fmax(T, -0x1p100), 0x1p100);
-    const float th = __double2float_rn(T);
-    const float tl = __double2float_rn(T - (double)th);
+    // the lane's total in the warp's common units 2^shm (shm >= pw.sh)
+    const int shm = __reduce_max_sync(0xffffffffu, pw.sh);
+    const float down = pow2f(pw.sh - shm);
+    float ih = __fmul_rn(A.s, down), il = __fmul_rn(A.e, down);
+    // inclusive warp scan of the pairs, then each lane's start = the previous
+    // lane's inclusive sum
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float yh = __shfl_up_sync(0xffffffffu, ih, o);
+        const float yl = __shfl_up_sync(0xffffffffu, il, o);
+        if (lane >= o) df_add(ih, il, yh, yl);
+    }
+    float sh0 = __shfl_up_sync(0xffffffffu, ih, 1), sl0 = __shfl_up_sync(0xffffffffu, il, 1);
+    if (lane == 0) { sh0 = 0.f; sl0 = 0.f; }
+    // target relative to the sub-block start in common units (FP64, then a
+    // float pair), minus the lane's start, back in the lane's units
+    double Tc = (t - pre) * __longlong_as_double((long long)((uint64_t)(1023 - shm) << 52));
+    Tc = fmin(fmax(Tc, -0x1p100), 0x1p100);
+    const float th = __double2float_rn(Tc);
+    const float tl = __double2float_rn(Tc - (double)th);
+    float rh = th, rl = tl;
+    df_add(rh, rl, -sh0, -sl0);
+    const float up = pow2f(shm - pw.sh);
+    const bool far = shm - pw.sh > 127;            // the lane is negligible next to the largest
+    rh = far ? (rh > 0.f ? INFINITY : -INFINITY) : __fmul_rn(rh, up);
+    rl = far ? 0.f : __fmul_rn(rl, up);
     first = -1;
     last_nz = -1;
 #pragma unroll
     for (int e = 7; e >= 0; --e) {
-        if (nz[e] && __fadd_rn(__fsub_rn(cs[e], th), __fsub_rn(ce[e], tl)) > 0.f) first = e;
+        if (nz[e] && __fadd_rn(__fsub_rn(cs[e], rh), __fsub_rn(ce[e], rl)) > 0.f) first = e;
         if (last_nz < 0 && nz[e]) last_nz = e;
     }
 }
@@ -855,6 +951,23 @@ unsigned grid_for(uint64_t work, int threads, int num_sms)
     if (g > cap) g = cap;
     if (g < 1) g = 1;
     return (unsigned)g;
+}
+
+// exclusive scan of nb values into out and their total into *total, on the
+// handle's stream; cs holds 2 * ceil(nb / kScanChunk) values of scratch
+template <typename T>
+int scan_exclusive(qsim_state *s, const T *in, T *out, uint64_t nb, T *total, T *cs, const char *what)
+{
+    const uint64_t nc = (nb + kScanChunk - 1) / kScanChunk;
+    launch_begin(s, KC_SAMPLE);
+    k_scan_chunk_sums<T><<<(unsigned)nc, 256, 0, s->stream>>>(in, nb, cs);
+    if (int rc = launch_end(s, what)) return rc;
+    launch_begin(s, KC_SAMPLE);
+    k_scan_exclusive<T><<<1, kScanThreads, 0, s->stream>>>(cs, cs + nc, nc, total);
+    if (int rc = launch_end(s, what)) return rc;
+    launch_begin(s, KC_SAMPLE);
+    k_scan_chunk_out<T><<<(unsigned)nc, 256, 0, s->stream>>>(in, nb, cs + nc, out);
+    return launch_end(s, what);
 }
 
 }  // namespace
@@ -974,13 +1087,16 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
     const uint64_t nb = N / bs;
     const SubGeo sg(bs);
     // scratch: sub-sums (nb * nsub doubles), bsum, bexcl (nb doubles), counts, offs, cursor (nb u32),
-    //          total, last (8 B each), shot_blk, order (shots u32), out (shots u64 for host output)
+    //          total, last (8 B each), shot_blk, order (shots u32), out (shots u64 for host output),
+    //          chunk totals and offsets of the two scans
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~(size_t)255; return o; };
     const size_t o_sub = take(nb * sg.nsub * 8);
     const size_t o_bsum = take(nb * 8), o_bexcl = take(nb * 8), o_tot = take(8), o_last = take(8);
     const size_t o_cnt = take(nb * 4), o_offs = take(nb * 4), o_cur = take(nb * 4), o_u32tot = take(8);
     const size_t o_sblk = take(shots * 4), o_order = take(shots * 4);
+    const uint64_t nchunk = (nb + kScanChunk - 1) / kScanChunk;
+    const size_t o_cs = take(2 * nchunk * 8), o_cs32 = take(2 * nchunk * 4);
     const size_t o_out = out_on_device ? 0 : take(shots * 8);
     char *scratch = nullptr;
     QSIM_CUDA(cudaMallocAsync((void **)&scratch, off, s->stream));
@@ -992,6 +1108,8 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
     uint32_t *cur = (uint32_t *)(scratch + o_cur), *u32tot = (uint32_t *)(scratch + o_u32tot);
     uint32_t *sblk = (uint32_t *)(scratch + o_sblk), *order = (uint32_t *)(scratch + o_order);
     uint64_t *dout = out_on_device ? out : (uint64_t *)(scratch + o_out);
+    double *cs = (double *)(scratch + o_cs);
+    uint32_t *cs32 = (uint32_t *)(scratch + o_cs32);
     int rc = SIM_OK;
     const bool c128 = s->dtype == SIM_C128;
     do {
@@ -999,9 +1117,7 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
         if (c128) k_sub_sums<double><<<(unsigned)nb, 256, 0, s->stream>>>((const double *)s->amps, bs, sub, bsum);
         else k_sub_sums<float><<<(unsigned)nb, 256, 0, s->stream>>>((const float *)s->amps, bs, sub, bsum);
         if ((rc = launch_end(s, "sub-block sums"))) break;
-        launch_begin(s, KC_SAMPLE);
-        k_scan_exclusive<double><<<1, kScanThreads, 0, s->stream>>>(bsum, bexcl, nb, tot);
-        if ((rc = launch_end(s, "block scan"))) break;
+        if ((rc = scan_exclusive<double>(s, bsum, bexcl, nb, tot, cs, "block scan"))) break;
         launch_begin(s, KC_SAMPLE);
         k_last_nonzero<<<1, 32, 0, s->stream>>>(bsum, nb, last);
         if ((rc = launch_end(s, "last nonzero"))) break;
@@ -1021,9 +1137,7 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
         k_locate<<<grid_for(shots, 256, s->num_sms), 256, 0, s->stream>>>(shots, seed, bexcl, bsum, nb, tot, sblk,
                                                                            cnt, hlast);
         if ((rc = launch_end(s, "locate shots"))) break;
-        launch_begin(s, KC_SAMPLE);
-        k_scan_exclusive<uint32_t><<<1, kScanThreads, 0, s->stream>>>(cnt, offs, nb, u32tot);
-        if ((rc = launch_end(s, "bucket scan"))) break;
+        if ((rc = scan_exclusive<uint32_t>(s, cnt, offs, nb, u32tot, cs32, "bucket scan"))) break;
         if (cudaMemcpyAsync(cur, offs, nb * 4, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "cursor copy");
             break;
