@@ -339,9 +339,9 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
         for (int b = 0; b < TB - L; ++b)
             if ((lane >> b) & 1) go |= 1ull << tpos[L + b];
         int issued = 0;
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int s = i % S;
-            if (i >= S && !mbar_wait_bounded(&bar_empty[s], (uint32_t)((i / S - 1) & 1))) {
+            if (i >= S && !mbar_wait_warp(&bar_empty[s], (uint32_t)((i / S - 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -370,9 +370,9 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
         for (int j = 0; j < 4; ++j) zc += (int)((pmask >> tpos[j]) & 1);
         const int x = (tid >> (4 - zc)) & ((1 << zc) - 1);
         const uint32_t ux = uc[x];
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int s = i % S;
-            if (!mbar_wait_bounded(&bar_full[s], (uint32_t)((i / S) & 1))) {
+            if (!mbar_wait_warp(&bar_full[s], (uint32_t)((i / S) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
             for (int j = 0; j < D; ++j) v[j] = sg[(ur | uc[j]) ^ ux];
             mbar_arrive(&bar_empty[s]);
             // A buffer i % AB: the MMAs of tile i - AB must be done reading it
-            if (i >= AB && !mbar_wait_bounded(&bar_d[(i - AB) & 1], (uint32_t)(((i - AB) >> 1) & 1))) {
+            if (i >= AB && !mbar_wait_warp(&bar_d[(i - AB) & 1], (uint32_t)(((i - AB) >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -410,10 +410,10 @@ __global__ void __launch_bounds__(kStreamThreads, StreamCfg<KQ>::MINB)
         uint64_t gr;
         row_offsets(r, ur, gr);
         const bool q0_in_block = (pmask & 1ull) != 0;
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int sb = i & 1;
             const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
-            if (!mbar_wait_bounded(&bar_d[sb], (uint32_t)((i >> 1) & 1))) {
+            if (!mbar_wait_warp(&bar_d[sb], (uint32_t)((i >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -649,9 +649,9 @@ __global__ void __launch_bounds__(kT6Threads, 1)
         const int nrun = 1 << (TB - L);
         const uint32_t rbytes = 8u << L;
         int issued = 0;
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int s = i & 1;
-            if (i >= 2 && !mbar_wait_bounded(&bar_empty[s], (uint32_t)(((i - 2) >> 1) & 1))) {
+            if (i >= 2 && !mbar_wait_warp(&bar_empty[s], (uint32_t)(((i - 2) >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -683,14 +683,14 @@ __global__ void __launch_bounds__(kT6Threads, 1)
         const uint32_t ux = uc[x];
         const uint32_t tl = taddr + ((uint32_t)(warp * 32) << 16);
         const float xs = __uint_as_float((uint32_t)(sexp + 127) << 23);   // 2^se
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int s = i & 1, b = i & 1;
-            if (!mbar_wait_bounded(&bar_full[s], (uint32_t)((i >> 1) & 1))) {
+            if (!mbar_wait_warp(&bar_full[s], (uint32_t)((i >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
             // A buffer b: the MMAs of tile i - 2 must be done reading it
-            if (i >= 2 && !mbar_wait_bounded(&bar_d[b], (uint32_t)(((i - 2) >> 1) & 1))) {
+            if (i >= 2 && !mbar_wait_warp(&bar_d[b], (uint32_t)(((i - 2) >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -750,10 +750,10 @@ __global__ void __launch_bounds__(kT6Threads, 1)
         const float f1 = __uint_as_float((uint32_t)(127 - t1) << 23);
         const float f2 = __uint_as_float((uint32_t)(127 - (t - t1)) << 23);
         const bool two_step = t1 != t;
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int b = i & 1;
             const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
-            if (!mbar_wait_bounded(&bar_d[b], (uint32_t)((i >> 1) & 1))) {
+            if (!mbar_wait_warp(&bar_d[b], (uint32_t)((i >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -987,9 +987,9 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
     if (warp >= 9) {
         // loaders: thread lt copies 16-byte pairs of amplitudes u = 2 (lt + 64 k)
         const int lt = tid - 9 * 32;
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int sg = i & 1;
-            if (i >= 2 && !mbar_wait_bounded(&bar_empty[sg], (uint32_t)(((i >> 1) - 1) & 1))) {
+            if (i >= 2 && !mbar_wait_warp(&bar_empty[sg], (uint32_t)(((i >> 1) - 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -1005,14 +1005,14 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         }
         cp_async_wait_all();
     } else if (warp < 4) {
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int sg = i & 1;
             const float2 *X = stage + (size_t)sg * TAMP;
-            for (int j = 0; j < m && !*vfailed; ++j) {
+            for (int j = 0; j < m && !warp_flag(vfailed); ++j) {
                 const int s = i * m + j;
                 bool ok;
-                if (j == 0) ok = mbar_wait_bounded(&bar_full[sg], (uint32_t)((i >> 1) & 1));
-                else ok = mbar_wait_bounded(&bar_w, (uint32_t)((i * (m - 1) + j - 1) & 1));
+                if (j == 0) ok = mbar_wait_warp(&bar_full[sg], (uint32_t)((i >> 1) & 1));
+                else ok = mbar_wait_warp(&bar_w, (uint32_t)((i * (m - 1) + j - 1) & 1));
                 if (!ok) { *vfailed = 1; break; }
                 const int zc = xs[j];
                 const int x = (tid >> (4 - zc)) & ((1 << zc) - 1);
@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
 #pragma unroll
                 for (int c = 0; c < D; ++c) v[c] = X[(ur | uc[j][c]) ^ ux];
                 if (j == m - 1) mbar_arrive(&bar_empty[sg]);
-                if (s >= 1 && !mbar_wait_bounded(&bar_d[(s - 1) & 1], (uint32_t)(((s - 1) >> 1) & 1))) {
+                if (s >= 1 && !mbar_wait_warp(&bar_d[(s - 1) & 1], (uint32_t)(((s - 1) >> 1) & 1))) {
                     *vfailed = 1;
                     break;
                 }
@@ -1045,14 +1045,14 @@ __global__ void __launch_bounds__(kMultiThreads, 1)
         const int r = tid - 128;
         const uint64_t gr = gr_last[r];
         const bool q0_last = a.pos[m - 1][0] == 0;
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int sg = i & 1;
             float2 *X = stage + (size_t)sg * TAMP;
             const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
-            for (int j = 0; j < m && !*vfailed; ++j) {
+            for (int j = 0; j < m && !warp_flag(vfailed); ++j) {
                 const int s = i * m + j;
                 const int sb = s & 1;
-                if (!mbar_wait_bounded(&bar_d[sb], (uint32_t)((s >> 1) & 1))) { *vfailed = 1; break; }
+                if (!mbar_wait_warp(&bar_d[sb], (uint32_t)((s >> 1) & 1))) { *vfailed = 1; break; }
                 tc_fence_after();
                 const uint32_t lane_base = taddr + (uint32_t)(sb * NC) + ((uint32_t)((warp - 4) * 32) << 16);
                 const bool last = j == m - 1;

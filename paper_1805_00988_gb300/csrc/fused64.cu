@@ -29,14 +29,18 @@
 //
 // k = 4 (K = N = 32 per level): two accumulators of 7 x 32 columns fit in
 // tensor memory, the seven digit planes of A in shared memory.
-//   warp 9: loads tile i (128 rows x 16 amplitudes, runs of >= 2 KB) into
+//   warp 17: loads tile i (128 rows x 16 amplitudes, runs of >= 2 KB) into
 //       stage i mod 2 with bulk copies;
-//   warps 0-3: thread r turns row r into its exponent and digit planes (A
-//       buffer i mod 2, K-major FP16), once the MMAs of tile i - 2 are done;
-//   warp 8 (one thread): the 14 MMAs of tile i once A is written and
+//   warps 0-7: threads 2 r and 2 r + 1 turn row r into its exponent and digit
+//       planes (A buffer i mod 2, K-major FP16), half of its columns each,
+//       once the MMAs of tile i - 2 are done;
+//   warp 16 (one thread): the 14 MMAs of tile i once A is written and
 //       accumulator i mod 2 has been drained (tile i - 2);
-//   warps 4-7: thread r reads row r's levels, forms the FP64 results and
-//       stores them to HBM.
+//   warps 8-15: a thread per row and half of the columns reads the row's
+//       levels, forms the FP64 results and stores them to HBM.
+// The integer digit work sets this kernel's pace, so it is spread over 512
+// threads (at most 112 registers each) rather than 256: more warps to issue
+// from while others wait on shared memory or tensor memory.
 // Row exponents pass from converter to consumer through four shared-memory
 // slots with their own full / empty barriers.  Every wait is bounded; on a
 // timeout the kernel records SIM_ETIMEOUT, lets work in flight land (bounded
@@ -59,7 +63,8 @@ constexpr int kPlanes = 7;                    // base-128 digits per operand
 constexpr int kRows64 = 128;                  // MMA M, rows per tile
 constexpr int kTB64 = kQ64 + 7;               // tile bits
 constexpr int kTAmp64 = 1 << kTB64;           // amplitudes per tile
-constexpr int kT64Threads = 320;
+constexpr int kT64Threads = 576;            // 8 converter + 8 consumer warps, issuer, loader
+constexpr int kHalf64 = 2 * kRows64;         // converter (and consumer) threads: two per row
 constexpr uint32_t kPlaneB = (uint32_t)kK64 * kK64 * 2;            // one W plane: 32 x 32 halves
 constexpr uint32_t kAPlaneB = (uint32_t)kRows64 * kK64 * 2;         // one A plane: 128 x 32 halves
 constexpr uint32_t kSlot64 = kPlanes * kPlaneB + kK64 * sizeof(int); // per block: W planes + column exponents
@@ -256,14 +261,14 @@ __global__ void __launch_bounds__(kT64Threads, 1)
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
             mbar_init(&bar_full[b], 1);
-            mbar_init(&bar_empty[b], kRows64);
-            mbar_init(&bar_a[b], kRows64);
+            mbar_init(&bar_empty[b], kHalf64);
+            mbar_init(&bar_a[b], kHalf64);
             mbar_init(&bar_d[b], 1);
-            mbar_init(&bar_e[b], kRows64);
+            mbar_init(&bar_e[b], kHalf64);
         }
         for (int q = 0; q < kSe64; ++q) {
-            mbar_init(&bar_sf[q], kRows64);
-            mbar_init(&bar_se[q], kRows64);
+            mbar_init(&bar_sf[q], kHalf64);
+            mbar_init(&bar_se[q], kHalf64);
         }
     }
     for (int c = tid; c < D; c += kT64Threads) {
@@ -317,16 +322,16 @@ __global__ void __launch_bounds__(kT64Threads, 1)
         }
     };
 
-    if (warp == 9) {
+    if (warp == 17) {
         // loader: lane j copies run j of every tile (T holds qubits 0..6, so
         // runs are >= 128 amplitudes and a tile has at most 16 of them)
         const int L = lrun;
         const int nrun = 1 << (TB - L);
         const uint32_t rbytes = 16u << L;
         int issued = 0;
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int s = i & 1;
-            if (i >= 2 && !mbar_wait_bounded(&bar_empty[s], (uint32_t)(((i - 2) >> 1) & 1))) {
+            if (i >= 2 && !mbar_wait_warp(&bar_empty[s], (uint32_t)(((i - 2) >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -344,48 +349,53 @@ __global__ void __launch_bounds__(kT64Threads, 1)
         if (lane == 0)
             for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
                 mbar_wait_bounded(&bar_full[i & 1], (uint32_t)((i >> 1) & 1));
-    } else if (warp < 4) {
-        // converters: thread r = row r
+    } else if (warp < 8) {
+        // converters: threads 2 r and 2 r + 1 share row r, each taking half of
+        // its complex columns (one shuffle gives both the row's exponent)
+        const int r = tid >> 1, h = tid & 1;
         uint32_t ur;
         uint64_t gr;
-        row_offsets(tid, ur, gr);
-        const uint32_t arow = (((uint32_t)tid >> 3) * (K >> 3) << 7) + (((uint32_t)tid & 7) << 4);
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        row_offsets(r, ur, gr);
+        const uint32_t arow = (((uint32_t)r >> 3) * (K >> 3) << 7) + (((uint32_t)r & 7) << 4);
+        constexpr int DH = D / 2;
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int s = i & 1, b = i & 1;
-            if (!mbar_wait_bounded(&bar_full[s], (uint32_t)((i >> 1) & 1))) {
+            if (!mbar_wait_warp(&bar_full[s], (uint32_t)((i >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
             const double2 *sg = stage + (size_t)s * TAMP;
-            double2 v[D];
+            double2 v[DH];
 #pragma unroll
-            for (int c = 0; c < D; ++c) v[c] = sg[ur | uc[c]];
+            for (int c = 0; c < DH; ++c) v[c] = sg[ur | uc[DH * h + c]];
             mbar_arrive(&bar_empty[s]);
             uint32_t emax = 0;
 #pragma unroll
-            for (int c = 0; c < D; ++c) emax = max(emax, max(bexp(v[c].x), bexp(v[c].y)));
-            // the row's exponent: slot i mod 4, once the consumer of tile i - 4 has read it
+            for (int c = 0; c < DH; ++c) emax = max(emax, max(bexp(v[c].x), bexp(v[c].y)));
+            emax = max(emax, __shfl_xor_sync(0xFFFFFFFFu, emax, 1));
+            // the row's exponent: slot i mod 4, once the consumers of tile i - 4 have read it
             const int q = i % kSe64;
-            if (i >= kSe64 && !mbar_wait_bounded(&bar_se[q], (uint32_t)(((i - kSe64) / kSe64) & 1))) {
+            if (i >= kSe64 && !mbar_wait_warp(&bar_se[q], (uint32_t)(((i - kSe64) / kSe64) & 1))) {
                 *vfailed = 1;
                 break;
             }
-            rowexp[q][tid] = emax;
+            if (h == 0) rowexp[q][r] = emax;
             mbar_arrive(&bar_sf[q]);
             // A buffer b: the MMAs of tile i - 2 must be done reading it
-            if (i >= 2 && !mbar_wait_bounded(&bar_d[b], (uint32_t)(((i - 2) >> 1) & 1))) {
+            if (i >= 2 && !mbar_wait_warp(&bar_d[b], (uint32_t)(((i - 2) >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
             tc_fence_after();
             unsigned char *ab = abuf + (size_t)b * kPlanes * kAPlaneB + arow;
 #pragma unroll
-            for (int g4 = 0; g4 < D / 4; ++g4) {
+            for (int g = 0; g < DH / 4; ++g) {
                 // complex columns 4 g4 .. 4 g4 + 3 = K-elements 8 g4 .. 8 g4 + 7: one 16-byte core-matrix row per plane
+                const int g4 = (DH / 4) * h + g;
                 uint32_t w[kPlanes][4];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    const double2 x = v[4 * g4 + j];
+                    const double2 x = v[4 * g + j];
                     const uint64_t tr = fixed49(x.x, emax), ti = fixed49(x.y, emax);
                     const uint32_t rh = (uint32_t)(tr >> 28), rl = (uint32_t)tr & 0xFFFFFFFu;
                     const uint32_t ih = (uint32_t)(ti >> 28), il = (uint32_t)ti & 0xFFFFFFFu;
@@ -404,32 +414,34 @@ __global__ void __launch_bounds__(kT64Threads, 1)
             tc_fence_before();
             mbar_arrive(&bar_a[b]);
         }
-    } else if (warp < 8) {
-        // consumers: warp w reads TMEM lanes 32 (w - 4) .. + 31 = rows of the tile
-        const int r = tid - 128;
+    } else if (warp < 16) {
+        // consumers: warp w may read TMEM lanes 32 (w mod 4) .. + 31 (rows of the
+        // tile); warps 8-11 take columns 0..15 of every level, warps 12-15 16..31
+        const int quarter = warp & 3, half = (warp - 8) >> 2;
+        const int r = 32 * quarter + lane;
         uint32_t ur;
         uint64_t gr;
         row_offsets(r, ur, gr);
-        for (int i = 0; i < iters && !*vfailed; ++i) {
+        for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
             const int b = i & 1;
             const uint64_t base = tile_base(blockIdx.x + (uint64_t)i * step) | gr;
-            if (!mbar_wait_bounded(&bar_d[b], (uint32_t)((i >> 1) & 1))) {
+            if (!mbar_wait_warp(&bar_d[b], (uint32_t)((i >> 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
             const int q = i % kSe64;
-            if (!mbar_wait_bounded(&bar_sf[q], (uint32_t)((i / kSe64) & 1))) {
+            if (!mbar_wait_warp(&bar_sf[q], (uint32_t)((i / kSe64) & 1))) {
                 *vfailed = 1;
                 break;
             }
             const int er = (int)rowexp[q][r];
             mbar_arrive(&bar_se[q]);
             tc_fence_after();
-            const uint32_t lb = taddr + ACC * (uint32_t)b + ((uint32_t)((warp - 4) * 32) << 16);
+            const uint32_t lb = taddr + ACC * (uint32_t)b + ((uint32_t)(quarter * 32) << 16);
             // one chunk of 8 columns at a time (not unrolled: the consumer's
             // code stays small next to the converters')
 #pragma unroll 1
-            for (int n0 = 0; n0 < K; n0 += 8) {
+            for (int n0 = half * (K / 2); n0 < (half + 1) * (K / 2); n0 += 8) {
                 uint32_t d[kPlanes][8];
 #pragma unroll
                 for (int l = 0; l < kPlanes; ++l) tmem_ld8_nowait(lb + 32u * (uint32_t)l + (uint32_t)n0, d[l]);
@@ -467,7 +479,7 @@ __global__ void __launch_bounds__(kT64Threads, 1)
             tc_fence_before();
             mbar_arrive(&bar_e[b]);
         }
-    } else if (warp == 8 && lane == 0) {
+    } else if (warp == 16 && lane == 0) {
         // issuer: digit plane p of A against W planes 0 .. 6 - p, into levels p .. 6
         const uint32_t sw = smem_u32(wsm);
         const uint32_t sa = smem_u32(abuf);

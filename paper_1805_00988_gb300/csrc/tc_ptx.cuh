@@ -78,6 +78,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     }
 }
 
+// the same for a role that a whole warp runs: one vote makes the outcome the
+// warp's, so no lane leaves its loop while the others go on to a
+// warp-collective instruction (a tensor-memory load, a shuffle, a vote)
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity)
+{
+    return __all_sync(0xFFFFFFFFu, mbar_wait_bounded(bar, parity));
+}
+// a shared failure flag read once for the whole warp
+__device__ __forceinline__ bool warp_flag(volatile int *f) { return __any_sync(0xFFFFFFFFu, *f != 0); }
+
 __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accum)
 {
