@@ -21,8 +21,8 @@
 //     2^24 without rounding);
 //   - levels l = 0..6 are kept (pairs with i + j >= 7 are dropped, a relative
 //     error of about 2^-49 of the row and column maxima), and the consumer
-//     forms sum_l D_l 128^(6 - l) exactly in 64-bit integers, then the FP64
-//     result T 2^(E_r + F_n - 56).
+//     forms T = sum_l D_l 128^(6 - l) exactly in 64-bit integers, converts it
+//     to FP64 (rounded to nearest) and scales it by 2^(E_r + F_n - 56).
 // One MMA per digit plane i of X and K-step: A = plane i (128 rows x 16), B =
 // W's planes 0 .. 6 - i side by side (N = (7 - i) x 32), D = accumulator
 // columns of levels i .. 6, so levels accumulate in place: 14 MMAs per tile.
@@ -449,27 +449,28 @@ __global__ void __launch_bounds__(kT64Threads, 1)
                 double o[8];
 #pragma unroll
                 for (int e = 0; e < 8; ++e) {
-                    // exact integers below 2^22: the FP32 bits of D + 1.5 2^23 carry D in the mantissa
-                    int di[kPlanes];
+                    // exact integers below 2^22: the FP32 bits of D + 1.5 2^23 are
+                    // kMagic + D, so pairs combine on the raw bits (mod 2^32) and
+                    // one constant removes the magic: D_0 128 + D_1 = u_0 128 + u_1 - 129 kMagic
+                    constexpr uint32_t kMagic = 0x4B400000u;
+                    uint32_t u[kPlanes];
 #pragma unroll
-                    for (int l = 0; l < kPlanes; ++l)
-                        di[l] = __float_as_int(__uint_as_float(d[l][e]) + 12582912.0f) - 0x4B400000;
-                    // sum_l D_l 128^(6 - l) in 64 bits, through exact 32-bit pairs
-                    const int64_t a01 = (int64_t)(di[0] * 128 + di[1]);
-                    const int64_t a23 = (int64_t)(di[2] * 128 + di[3]);
-                    const int64_t a45 = (int64_t)(di[4] * 128 + di[5]);
-                    const int64_t T = a01 * (1ll << 35) + a23 * (1ll << 21) + a45 * 128 + (int64_t)di[6];
-                    // T 2^(E_r + F_n - 56), E = biased exponent - 1022, rounded down to 53 bits
-                    const uint64_t mag = (uint64_t)(T < 0 ? -T : T);
-                    uint64_t bits = 0;
-                    if (mag != 0) {
-                        const int lz = __clzll((long long)mag);
-                        const int be = 1023 + (63 - lz) + er + colexp[n0 + e] - 2044 - 56;
-                        const uint64_t mant = ((mag << lz) >> 11) & 0xFFFFFFFFFFFFFull;
-                        if (be > 0) bits = ((uint64_t)be << 52) | mant;
-                        bits |= (uint64_t)(T < 0) << 63;
-                    }
-                    o[e] = __longlong_as_double((long long)bits);
+                    for (int l = 0; l < kPlanes; ++l) u[l] = __float_as_uint(__uint_as_float(d[l][e]) + 12582912.0f);
+                    const int32_t a01 = (int32_t)(u[0] * 128u + u[1] - 129u * kMagic);
+                    const int32_t a23 = (int32_t)(u[2] * 128u + u[3] - 129u * kMagic);
+                    const int32_t a45 = (int32_t)(u[4] * 128u + u[5] - 129u * kMagic);
+                    const int32_t a6 = (int32_t)(u[6] - kMagic);
+                    // T = sum_l D_l 128^(6 - l), |T| < 2^62
+                    const long long T = (long long)a01 * (1ll << 35) + (long long)a23 * (1ll << 21) +
+                                        (long long)a45 * 128 + (long long)a6;
+                    // T 2^(E_r + F_n - 56), E = biased exponent - 1022: T as an FP64
+                    // value (rounded to nearest above 2^53), the scale added to its
+                    // exponent field; zero, and results below the normal range, give 0
+                    const double f = __ll2double_rn(T);
+                    const int fh = __double2hiint(f);
+                    const int ef = (fh >> 20) & 0x7FF;
+                    const int sc = er + colexp[n0 + e] - 2044 - 56;
+                    o[e] = (ef != 0 && ef + sc > 0) ? __hiloint2double(fh + sc * (1 << 20), __double2loint(f)) : 0.0;
                 }
                 // columns n0 .. n0 + 7 = complex columns n0 / 2 .. + 3
 #pragma unroll
