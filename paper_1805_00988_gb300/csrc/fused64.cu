@@ -10,31 +10,34 @@
 // Ogita and Imamura (2020):
 //   - each row r of X (the 2^k amplitudes sharing all index bits outside the
 //     block, as 2^(k+1) reals) is written in fixed point relative to its
-//     largest component: |x| < 2^E_r, t = trunc(|x| 2^(49 - E_r)) < 2^49, and t
-//     is cut into kPlanes = 7 base-128 digits (0..127) carrying the sign of x;
+//     largest component: |x| < 2^E_r, t = trunc(x 2^(47 - E_r)), |t| < 2^47,
+//     and t is cut into kPlanes = 6 balanced base-256 digits: t = sum_i d_i
+//     256^(5 - i) with d_1..d_5 in -128..127 and d_0 in -128..128 (the bytes
+//     of t + 128 (1 + 256 + ... + 256^4), each less 128);
 //   - each column n of W likewise relative to its largest entry (2^F_n);
-//   - a digit is an integer of at most 7 bits, exact in FP16, and a product
-//     of two is below 2^14; a K = 32 sum of them is below 2^19, and the
-//     products of digit i of X with digit j of W are summed per level
-//     l = i + j (at most 7 products per level, below 2^22), so every FP32
-//     accumulator holds an exact integer (the tensor core adds integers below
-//     2^24 without rounding);
-//   - levels l = 0..6 are kept (pairs with i + j >= 7 are dropped, a relative
-//     error of about 2^-49 of the row and column maxima), and the consumer
-//     forms T = sum_l D_l 128^(6 - l) exactly in 64-bit integers, converts it
-//     to FP64 (rounded to nearest) and scales it by 2^(E_r + F_n - 56).
+//   - a digit is an integer of magnitude at most 128, exact in FP16, and a
+//     product of two is at most 2^14; a K = 32 sum of them is at most 2^19,
+//     and the products of digit i of X with digit j of W are summed per
+//     level l = i + j (at most 6 products per level, below 2^22), so every
+//     FP32 accumulator holds an exact integer (the tensor core adds integers
+//     below 2^24 without rounding);
+//   - levels l = 0..5 are kept (pairs with i + j >= 6 are dropped, a relative
+//     error of about 2^-42 of the row and column maxima in the worst case),
+//     and the consumer forms T = sum_l D_l 256^(5 - l) exactly in 64-bit
+//     integers, converts it to FP64 (rounded to nearest) and scales it by
+//     2^(E_r + F_n - 54).
 // One MMA per digit plane i of X and K-step: A = plane i (128 rows x 16), B =
-// W's planes 0 .. 6 - i side by side (N = (7 - i) x 32), D = accumulator
-// columns of levels i .. 6, so levels accumulate in place: 14 MMAs per tile.
+// W's planes 0 .. 5 - i side by side (N = (6 - i) x 32), D = accumulator
+// columns of levels i .. 5, so levels accumulate in place: 12 MMAs per tile.
 //
-// k = 4 (K = N = 32 per level): two accumulators of 7 x 32 columns fit in
-// tensor memory, the seven digit planes of A in shared memory.
+// k = 4 (K = N = 32 per level): two accumulators of 6 x 32 columns fit in
+// tensor memory, the six digit planes of A in shared memory.
 //   warp 17: loads tile i (128 rows x 16 amplitudes, runs of >= 2 KB) into
-//       stage i mod 2 with bulk copies;
+//       stage i mod 3 with bulk copies (three tiles in flight);
 //   warps 0-7: threads 2 r and 2 r + 1 turn row r into its exponent and digit
 //       planes (A buffer i mod 2, K-major FP16), half of its columns each,
 //       once the MMAs of tile i - 2 are done;
-//   warp 16 (one thread): the 14 MMAs of tile i once A is written and
+//   warp 16 (one thread): the 12 MMAs of tile i once A is written and
 //       accumulator i mod 2 has been drained (tile i - 2);
 //   warps 8-15: a thread per row and half of the columns reads the row's
 //       levels, forms the FP64 results and stores them to HBM.
@@ -59,7 +62,7 @@ namespace {
 constexpr int kQ64 = 4;                       // qubits per block
 constexpr int kD64 = 1 << kQ64;               // amplitudes per row
 constexpr int kK64 = 2 * kD64;                // reals per row: MMA K, and N per level
-constexpr int kPlanes = 7;                    // base-128 digits per operand
+constexpr int kPlanes = 6;                    // balanced base-256 digits per operand
 constexpr int kRows64 = 128;                  // MMA M, rows per tile
 constexpr int kTB64 = kQ64 + 7;               // tile bits
 constexpr int kTAmp64 = 1 << kTB64;           // amplitudes per tile
@@ -69,6 +72,7 @@ constexpr uint32_t kPlaneB = (uint32_t)kK64 * kK64 * 2;            // one W plan
 constexpr uint32_t kAPlaneB = (uint32_t)kRows64 * kK64 * 2;         // one A plane: 128 x 32 halves
 constexpr uint32_t kSlot64 = kPlanes * kPlaneB + kK64 * sizeof(int); // per block: W planes + column exponents
 constexpr int kSe64 = 4;                      // row-exponent slots
+constexpr int kStage64 = 3;                   // tiles in flight from HBM
 
 struct FGate64 {                              // a gate in block-local qubits (the host's block-gate layout)
     int32_t target;
@@ -101,41 +105,29 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t *r)
 // taken as zero)
 __device__ __forceinline__ uint32_t bexp(double x) { return (uint32_t)(__double_as_longlong(x) >> 52) & 0x7FFu; }
 
-// |x| in fixed point relative to emax (|x| < 2^(emax - 1022)): trunc(|x| 2^(49 - E)), below 2^49
-__device__ __forceinline__ uint64_t fixed49(double x, uint32_t emax)
-{
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
-    if (e == 0) return 0;
-    const uint32_t sh = emax - e + 4u;        // >= 4
-    const uint64_t m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    return sh < 64 ? (m >> sh) : 0ull;
-}
+// 128 (1 + 256 + ... + 256^5): added to t, it leaves digit i + 128 in byte
+// 5 - i (digit 0: bits 40 and up, 0..256)
+constexpr uint64_t kDigitOff = 0x808080808080ull;
 
-// digit i (0 = most significant) of a 49-bit fixed-point value
-__device__ __forceinline__ uint32_t digit(uint64_t t, int i) { return (uint32_t)(t >> (42 - 7 * i)) & 127u; }
-
-// the same from the value's two 32-bit parts th = t >> 28 (digits 0..2) and
-// tl = t mod 2^28 (digits 3..6): one bit-field extract per digit
-__device__ __forceinline__ uint32_t digit2(uint32_t th, uint32_t tl, int i)
+// t + kDigitOff with t = trunc(|x| 2^(47 - E)), E = emax - 1022 the exponent
+// bound of x's row or column (|x| < 2^E, emax the largest biased exponent),
+// so 0 <= t < 2^47; x given as its two 32-bit halves.  Zero and subnormal x
+// give t = 0 (their shift is 64; PTX clamps 64-bit shifts at 64).  The
+// balanced digits of t, each times the sign of x, are those of x 2^(47 - E).
+__device__ __forceinline__ uint64_t fixed47m(uint32_t hi, uint32_t lo, uint32_t emax)
 {
-    return i < 3 ? (th >> (14 - 7 * i)) & 127u : (tl >> (21 - 7 * (i - 3))) & 127u;
-}
-
-// two digits (< 1024) as an FP16 pair with the given signs: 1024 + d is exact
-// in FP16 with mantissa d, and subtracting 1024 leaves d exactly
-__device__ __forceinline__ uint32_t digits_h2(uint32_t dlo, uint32_t dhi, uint32_t slo, uint32_t shi)
-{
-    const uint32_t w = 0x64006400u | dlo | (dhi << 16);
-    __half2 h = *reinterpret_cast<const __half2 *>(&w);
-    h = __hsub2(h, __halves2half2(__ushort_as_half(0x6400), __ushort_as_half(0x6400)));
-    return *reinterpret_cast<const uint32_t *>(&h) ^ ((slo << 15) | (shi << 31));
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    const uint32_t sh = e ? emax - e + 6u : 64u;        // >= 6
+    const uint64_t m = ((uint64_t)((hi & 0xFFFFFu) | 0x100000u) << 32) | lo;
+    uint64_t t;
+    asm("shr.b64 %0, %1, %2;" : "=l"(t) : "l"(m), "r"(sh));
+    return t + kDigitOff;
 }
 
 // ------------------------------------------------------------------ builder
 // U = G_m ... G_1 in FP64 (columns evolved from the identity), then its real
 // form W (fused.cu's convention), each column n in fixed point relative to
-// its largest entry, cut into kPlanes digit planes in the 16-bit K-major
+// its largest entry, cut into kPlanes balanced digit planes (FP16, exact) in the 16-bit K-major
 // B-operand layout ([plane][n][kk], plane j as rows 32 j .. 32 j + 31), and the
 // columns' biased exponents after the planes.  One CTA per block.
 __global__ void __launch_bounds__(256) k_fuse_build64(const FGate64 *__restrict__ gates, const int *__restrict__ goff,
@@ -205,11 +197,12 @@ __global__ void __launch_bounds__(256) k_fuse_build64(const FGate64 *__restrict_
     for (int e = tid; e < K * K; e += 256) {
         const int n = e / K, kk = e % K;
         const double w = wval(n, kk);
-        const uint64_t t = fixed49(w, cmax[n]);
-        const uint32_t sgn = (uint32_t)((uint64_t)__double_as_longlong(w) >> 63);
+        const uint64_t t = fixed47m((uint32_t)__double2hiint(w), (uint32_t)__double2loint(w), cmax[n]);
         for (int p = 0; p < kPlanes; ++p) {
-            const uint32_t h = digits_h2(digit(t, p), 0u, sgn, 0u) & 0xFFFFu;
-            *reinterpret_cast<uint16_t *>(out + kmajor16_off((uint32_t)(p * K + n), (uint32_t)kk, K)) = (uint16_t)h;
+            // digit p: byte 5 - p of t + kDigitOff (digit 0: bits 40 and up) less 128, with w's sign
+            const int dm = (int)(p == 0 ? (t >> 40) : ((t >> (40 - 8 * p)) & 255u)) - 128;
+            const int d = (w < 0.0) ? -dm : dm;
+            *reinterpret_cast<__half *>(out + kmajor16_off((uint32_t)(p * K + n), (uint32_t)kk, K)) = __int2half_rn(d);
         }
     }
     if (tid < K) reinterpret_cast<int *>(out + kPlanes * kPlaneB)[tid] = (int)cmax[tid];
@@ -222,14 +215,14 @@ __global__ void __launch_bounds__(kT64Threads, 1)
 {
     constexpr int D = kD64, K = kK64, TB = kTB64, TAMP = kTAmp64;
     constexpr uint32_t TBYTES = (uint32_t)TAMP * 16u;
-    constexpr uint32_t NCOLS = 512, ACC = 256;          // accumulator b at column 256 b (7 x 32 used)
+    constexpr uint32_t NCOLS = 512, ACC = 256;          // accumulator b at column 256 b (6 x 32 used)
     constexpr uint32_t SBO = (K / 8) * 128;             // 8-row group stride of a 16-bit K-major operand
 
     extern __shared__ __align__(1024) unsigned char smem[];
-    double2 *stage = reinterpret_cast<double2 *>(smem);                          // 2 x TAMP amplitudes
-    unsigned char *abuf = smem + 2 * (size_t)TBYTES;                              // 2 x 7 planes x 128 x 32 halves
-    unsigned char *wsm = abuf + 2 * (size_t)kPlanes * kAPlaneB;                   // 7 planes x 32 x 32 halves
-    __shared__ uint64_t bar_full[2], bar_empty[2], bar_a[2], bar_d[2], bar_e[2], bar_sf[kSe64], bar_se[kSe64];
+    double2 *stage = reinterpret_cast<double2 *>(smem);                          // kStage64 x TAMP amplitudes
+    unsigned char *abuf = smem + kStage64 * (size_t)TBYTES;                              // 2 x 6 planes x 128 x 32 halves
+    unsigned char *wsm = abuf + 2 * (size_t)kPlanes * kAPlaneB;                   // 6 planes x 32 x 32 halves
+    __shared__ uint64_t bar_full[kStage64], bar_empty[kStage64], bar_a[2], bar_d[2], bar_e[2], bar_sf[kSe64], bar_se[kSe64];
     __shared__ uint32_t rowexp[kSe64][kRows64];
     __shared__ int colexp[K];
     __shared__ uint32_t tslot;
@@ -259,9 +252,11 @@ __global__ void __launch_bounds__(kT64Threads, 1)
     if (failed) return;
     if (warp == 0) tmem_alloc(&tslot, NCOLS);
     if (tid == 0) {
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kStage64; ++b) {
             mbar_init(&bar_full[b], 1);
             mbar_init(&bar_empty[b], kHalf64);
+        }
+        for (int b = 0; b < 2; ++b) {
             mbar_init(&bar_a[b], kHalf64);
             mbar_init(&bar_d[b], 1);
             mbar_init(&bar_e[b], kHalf64);
@@ -330,8 +325,8 @@ __global__ void __launch_bounds__(kT64Threads, 1)
         const uint32_t rbytes = 16u << L;
         int issued = 0;
         for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
-            const int s = i & 1;
-            if (i >= 2 && !mbar_wait_warp(&bar_empty[s], (uint32_t)(((i - 2) >> 1) & 1))) {
+            const int s = i % kStage64;
+            if (i >= kStage64 && !mbar_wait_warp(&bar_empty[s], (uint32_t)((i / kStage64 - 1) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -347,8 +342,8 @@ __global__ void __launch_bounds__(kT64Threads, 1)
             issued = i + 1;
         }
         if (lane == 0)
-            for (int i = (issued > 2 ? issued - 2 : 0); i < issued; ++i)
-                mbar_wait_bounded(&bar_full[i & 1], (uint32_t)((i >> 1) & 1));
+            for (int i = (issued > kStage64 ? issued - kStage64 : 0); i < issued; ++i)
+                mbar_wait_bounded(&bar_full[i % kStage64], (uint32_t)((i / kStage64) & 1));
     } else if (warp < 8) {
         // converters: threads 2 r and 2 r + 1 share row r, each taking half of
         // its complex columns (one shuffle gives both the row's exponent)
@@ -359,8 +354,8 @@ __global__ void __launch_bounds__(kT64Threads, 1)
         const uint32_t arow = (((uint32_t)r >> 3) * (K >> 3) << 7) + (((uint32_t)r & 7) << 4);
         constexpr int DH = D / 2;
         for (int i = 0; i < iters && !warp_flag(vfailed); ++i) {
-            const int s = i & 1, b = i & 1;
-            if (!mbar_wait_warp(&bar_full[s], (uint32_t)((i >> 1) & 1))) {
+            const int s = i % kStage64, b = i & 1;
+            if (!mbar_wait_warp(&bar_full[s], (uint32_t)((i / kStage64) & 1))) {
                 *vfailed = 1;
                 break;
             }
@@ -388,6 +383,11 @@ __global__ void __launch_bounds__(kT64Threads, 1)
             }
             tc_fence_after();
             unsigned char *ab = abuf + (size_t)b * kPlanes * kAPlaneB + arow;
+            // an FP16 pair (1024 + b_re, 1024 + b_im) has the exponent byte 0x64 above
+            // each offset digit b = d + 128 (0..256); times the sign s of the
+            // component, plus -1152 s, it is s d exactly (one HFMA2)
+            constexpr uint32_t kE = 0x64646464u;
+            const uint32_t kOne = 0x3C003C00u, kNegBias = 0xE480E480u;   // (1, 1), (-1152, -1152)
 #pragma unroll
             for (int g = 0; g < DH / 4; ++g) {
                 // complex columns 4 g4 .. 4 g4 + 3 = K-elements 8 g4 .. 8 g4 + 7: one 16-byte core-matrix row per plane
@@ -396,14 +396,31 @@ __global__ void __launch_bounds__(kT64Threads, 1)
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const double2 x = v[4 * g + j];
-                    const uint64_t tr = fixed49(x.x, emax), ti = fixed49(x.y, emax);
-                    const uint32_t rh = (uint32_t)(tr >> 28), rl = (uint32_t)tr & 0xFFFFFFFu;
-                    const uint32_t ih = (uint32_t)(ti >> 28), il = (uint32_t)ti & 0xFFFFFFFu;
-                    const uint32_t sr = (uint32_t)((uint64_t)__double_as_longlong(x.x) >> 63);
-                    const uint32_t si = (uint32_t)((uint64_t)__double_as_longlong(x.y) >> 63);
+                    const uint32_t xrh = (uint32_t)__double2hiint(x.x), xih = (uint32_t)__double2hiint(x.y);
+                    const uint64_t tr = fixed47m(xrh, (uint32_t)__double2loint(x.x), emax);
+                    const uint64_t ti = fixed47m(xih, (uint32_t)__double2loint(x.y), emax);
+                    const uint32_t rh = (uint32_t)(tr >> 32), rl = (uint32_t)tr;
+                    const uint32_t ih = (uint32_t)(ti >> 32), il = (uint32_t)ti;
+                    // signs: bit 15 from the real part, bit 31 from the imaginary part
+                    const uint32_t sgn = __byte_perm(xrh, xih, 0x7030u) & 0x80008000u;
+                    const uint32_t sig = kOne | sgn, bia = kNegBias ^ sgn;
+                    // byte k of t + kDigitOff is digit 5 - k; pick each digit pair
+                    // (re, im) next to the exponent bytes
+                    const uint32_t p23 = __byte_perm(rl, il, 0x6723u), p45 = __byte_perm(rl, il, 0x4501u);
+                    uint32_t q[kPlanes];
+                    q[0] = 0x64006400u | (rh >> 8) | ((ih >> 8) << 16);
+                    q[1] = __byte_perm(__byte_perm(rh, ih, 0x0400u), kE, 0x4240u);
+                    q[2] = __byte_perm(p23, kE, 0x4240u);
+                    q[3] = __byte_perm(p23, kE, 0x4341u);
+                    q[4] = __byte_perm(p45, kE, 0x4240u);
+                    q[5] = __byte_perm(p45, kE, 0x4341u);
 #pragma unroll
-                    for (int p = 0; p < kPlanes; ++p)
-                        w[p][j] = digits_h2(digit2(rh, rl, p), digit2(ih, il, p), sr, si);
+                    for (int p = 0; p < kPlanes; ++p) {
+                        const __half2 hd = __hfma2(*reinterpret_cast<const __half2 *>(&q[p]),
+                                                   *reinterpret_cast<const __half2 *>(&sig),
+                                                   *reinterpret_cast<const __half2 *>(&bia));
+                        w[p][j] = *reinterpret_cast<const uint32_t *>(&hd);
+                    }
                 }
 #pragma unroll
                 for (int p = 0; p < kPlanes; ++p)
@@ -451,25 +468,23 @@ __global__ void __launch_bounds__(kT64Threads, 1)
                 for (int e = 0; e < 8; ++e) {
                     // exact integers below 2^22: the FP32 bits of D + 1.5 2^23 are
                     // kMagic + D, so pairs combine on the raw bits (mod 2^32) and
-                    // one constant removes the magic: D_0 128 + D_1 = u_0 128 + u_1 - 129 kMagic
+                    // one constant removes the magic: D_0 256 + D_1 = u_0 256 + u_1 - 257 kMagic
                     constexpr uint32_t kMagic = 0x4B400000u;
                     uint32_t u[kPlanes];
 #pragma unroll
                     for (int l = 0; l < kPlanes; ++l) u[l] = __float_as_uint(__uint_as_float(d[l][e]) + 12582912.0f);
-                    const int32_t a01 = (int32_t)(u[0] * 128u + u[1] - 129u * kMagic);
-                    const int32_t a23 = (int32_t)(u[2] * 128u + u[3] - 129u * kMagic);
-                    const int32_t a45 = (int32_t)(u[4] * 128u + u[5] - 129u * kMagic);
-                    const int32_t a6 = (int32_t)(u[6] - kMagic);
-                    // T = sum_l D_l 128^(6 - l), |T| < 2^62
-                    const long long T = (long long)a01 * (1ll << 35) + (long long)a23 * (1ll << 21) +
-                                        (long long)a45 * 128 + (long long)a6;
-                    // T 2^(E_r + F_n - 56), E = biased exponent - 1022: T as an FP64
+                    const int32_t a01 = (int32_t)(u[0] * 256u + u[1] - 257u * kMagic);
+                    const int32_t a23 = (int32_t)(u[2] * 256u + u[3] - 257u * kMagic);
+                    const int32_t a45 = (int32_t)(u[4] * 256u + u[5] - 257u * kMagic);
+                    // T = sum_l D_l 256^(5 - l), |T| < 2^63
+                    const long long T = (long long)a01 * (1ll << 32) + (long long)a23 * 65536 + (long long)a45;
+                    // T 2^(E_r + F_n - 54), E = biased exponent - 1022: T as an FP64
                     // value (rounded to nearest above 2^53), the scale added to its
                     // exponent field; zero, and results below the normal range, give 0
                     const double f = __ll2double_rn(T);
                     const int fh = __double2hiint(f);
                     const int ef = (fh >> 20) & 0x7FF;
-                    const int sc = er + colexp[n0 + e] - 2044 - 56;
+                    const int sc = er + colexp[n0 + e] - 2044 - 54;
                     o[e] = (ef != 0 && ef + sc > 0) ? __hiloint2double(fh + sc * (1 << 20), __double2loint(f)) : 0.0;
                 }
                 // columns n0 .. n0 + 7 = complex columns n0 / 2 .. + 3
@@ -481,7 +496,7 @@ __global__ void __launch_bounds__(kT64Threads, 1)
             mbar_arrive(&bar_e[b]);
         }
     } else if (warp == 16 && lane == 0) {
-        // issuer: digit plane p of A against W planes 0 .. 6 - p, into levels p .. 6
+        // issuer: digit plane p of A against W planes 0 .. 5 - p, into levels p .. 5
         const uint32_t sw = smem_u32(wsm);
         const uint32_t sa = smem_u32(abuf);
         int nd = 0;
@@ -514,7 +529,7 @@ __global__ void __launch_bounds__(kT64Threads, 1)
 
 constexpr size_t c128_smem_bytes()
 {
-    return 2 * (size_t)kTAmp64 * 16 + 2 * (size_t)kPlanes * kAPlaneB + (size_t)kPlanes * kPlaneB;
+    return kStage64 * (size_t)kTAmp64 * 16 + 2 * (size_t)kPlanes * kAPlaneB + (size_t)kPlanes * kPlaneB;
 }
 
 }  // namespace

@@ -1,14 +1,16 @@
 """The fused plan on complex128 states: blocks of 4 qubits, each block's
 unitary built in FP64 and applied on the FP16 tensor cores as exact integer
-arithmetic on 7-bit digit planes of the state and of the block matrix (49
-bits relative to each row's and each column's largest entry).
+arithmetic on balanced 8-bit digit planes of the state and of the block
+matrix (47 bits relative to each row's and each column's largest entry).
 
 Tolerances (the required bounds for complex128): infidelity <= 1e-12 and
-|psi - ref| <= 1e-11 max|ref| element-wise.  Derivation: each block keeps 49
-bits of every row and column in fixed point and drops the digit products
-below 2^-49 of them; a K = 32 dot product then errs by about 2^-45 of its
-largest term (3e-14), and over a few hundred blocks that random walk stays
-under 1e-12 of max|ref|."""
+|psi - ref| <= 1e-11 max|ref| element-wise.  Derivation: each block keeps 47
+bits of every row and column in fixed point (2^-47 = 7e-15 of its largest
+entry) and drops the digit products of levels 6 and up (at most about 2^-42
+of the row and column maxima, with random signs far less); a K = 32 dot
+product then errs by about 1e-13 of its largest term, and over a few hundred
+blocks that random walk stays under 1e-11 of max|ref|, the infidelity near
+its square."""
 import numpy as np
 import pytest
 
