@@ -101,6 +101,26 @@ __device__ __forceinline__ void tmem_ld8_nowait(uint32_t taddr, uint32_t *r)
                  : "memory");
 }
 
+__device__ __forceinline__ void tmem_ld4_nowait(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+}
+// tcgen05.wait::ld that also names the 24 registers of one chunk as read and
+// written, so no use of them can be scheduled above the wait
+__device__ __forceinline__ void tmem_wait_ld_regs(uint32_t (&r)[6][4])
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0][0]), "+r"(r[0][1]), "+r"(r[0][2]), "+r"(r[0][3]), "+r"(r[1][0]), "+r"(r[1][1]),
+                   "+r"(r[1][2]), "+r"(r[1][3]), "+r"(r[2][0]), "+r"(r[2][1]), "+r"(r[2][2]), "+r"(r[2][3]),
+                   "+r"(r[3][0]), "+r"(r[3][1]), "+r"(r[3][2]), "+r"(r[3][3]), "+r"(r[4][0]), "+r"(r[4][1]),
+                   "+r"(r[4][2]), "+r"(r[4][3]), "+r"(r[5][0]), "+r"(r[5][1]), "+r"(r[5][2]), "+r"(r[5][3])
+                 :
+                 : "memory");
+}
+
 // biased FP64 exponent of a component (0 for zero and subnormals, which are
 // taken as zero)
 __device__ __forceinline__ uint32_t bexp(double x) { return (uint32_t)(__double_as_longlong(x) >> 52) & 0x7FFu; }
@@ -455,24 +475,33 @@ __global__ void __launch_bounds__(kT64Threads, 1)
             mbar_arrive(&bar_se[q]);
             tc_fence_after();
             const uint32_t lb = taddr + ACC * (uint32_t)b + ((uint32_t)(quarter * 32) << 16);
-            // one chunk of 8 columns at a time (not unrolled: the consumer's
-            // code stays small next to the converters')
-#pragma unroll 1
-            for (int n0 = half * (K / 2); n0 < (half + 1) * (K / 2); n0 += 8) {
-                uint32_t d[kPlanes][8];
+            // chunks of 4 columns (two complex outputs); the loads of chunk c + 1
+            // are issued before chunk c is converted, so their latency overlaps it
+            constexpr int CW = 4, NCH = (K / 2) / CW;
+            const int nb = half * (K / 2);
+            uint32_t d[2][kPlanes][CW];
 #pragma unroll
-                for (int l = 0; l < kPlanes; ++l) tmem_ld8_nowait(lb + 32u * (uint32_t)l + (uint32_t)n0, d[l]);
-                tmem_wait_ld();
-                double o[8];
+            for (int l = 0; l < kPlanes; ++l) tmem_ld4_nowait(lb + 32u * (uint32_t)l + (uint32_t)nb, d[0][l]);
 #pragma unroll
-                for (int e = 0; e < 8; ++e) {
+            for (int c = 0; c < NCH; ++c) {
+                uint32_t (&dc)[kPlanes][CW] = d[c & 1];
+                tmem_wait_ld_regs(dc);
+                if (c + 1 < NCH) {
+#pragma unroll
+                    for (int l = 0; l < kPlanes; ++l)
+                        tmem_ld4_nowait(lb + 32u * (uint32_t)l + (uint32_t)(nb + CW * (c + 1)), d[(c + 1) & 1][l]);
+                }
+                const int n0 = nb + CW * c;
+                double o[CW];
+#pragma unroll
+                for (int e = 0; e < CW; ++e) {
                     // exact integers below 2^22: the FP32 bits of D + 1.5 2^23 are
                     // kMagic + D, so pairs combine on the raw bits (mod 2^32) and
                     // one constant removes the magic: D_0 256 + D_1 = u_0 256 + u_1 - 257 kMagic
                     constexpr uint32_t kMagic = 0x4B400000u;
                     uint32_t u[kPlanes];
 #pragma unroll
-                    for (int l = 0; l < kPlanes; ++l) u[l] = __float_as_uint(__uint_as_float(d[l][e]) + 12582912.0f);
+                    for (int l = 0; l < kPlanes; ++l) u[l] = __float_as_uint(__uint_as_float(dc[l][e]) + 12582912.0f);
                     const int32_t a01 = (int32_t)(u[0] * 256u + u[1] - 257u * kMagic);
                     const int32_t a23 = (int32_t)(u[2] * 256u + u[3] - 257u * kMagic);
                     const int32_t a45 = (int32_t)(u[4] * 256u + u[5] - 257u * kMagic);
@@ -487,10 +516,10 @@ __global__ void __launch_bounds__(kT64Threads, 1)
                     const int sc = er + colexp[n0 + e] - 2044 - 54;
                     o[e] = (ef != 0 && ef + sc > 0) ? __hiloint2double(fh + sc * (1 << 20), __double2loint(f)) : 0.0;
                 }
-                // columns n0 .. n0 + 7 = complex columns n0 / 2 .. + 3
+                // columns n0 .. n0 + 3 = complex columns n0 / 2, n0 / 2 + 1
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    *reinterpret_cast<double2 *>(st + 2 * (base | gc[n0 / 2 + c])) = make_double2(o[2 * c], o[2 * c + 1]);
+                for (int cc = 0; cc < CW / 2; ++cc)
+                    *reinterpret_cast<double2 *>(st + 2 * (base | gc[n0 / 2 + cc])) = make_double2(o[2 * cc], o[2 * cc + 1]);
             }
             tc_fence_before();
             mbar_arrive(&bar_e[b]);
