@@ -52,12 +52,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 # captures stay at a few GB on the device) and the traffic of a launch grows
 # with the state, so it is scaled by 2^n.
 TRAFFIC = {
-    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073931 GB + dram__bytes_write.sum 1.011775 GB
-    "fused_f16": {"bytes_per_amp": (1.073931e9 + 1.011775e9) / 2 ** 27,
+    # k_fused_tmem6, 27 qubits: dram__bytes_read.sum 1.073929 GB + dram__bytes_write.sum 1.011859 GB
+    "fused_f16": {"bytes_per_amp": (1.073929e9 + 1.011859e9) / 2 ** 27,
                   "sources": [("paper_1805_00988_gb300/csrc/fused.cu",
                                "// ------------------------------------------------------------------ multi-block passes"),
                               ("paper_1805_00988_gb300/csrc/tc_ptx.cuh", None)],
-                  "sha256": "620565e547fb3d6bdcf8a1c82249426ddfa7833590b978db88f4fb3e731c3671"},
+                  "sha256": "b00b0177de2c9b21884416e46f6dc82c58a162dc8016cd6882d0b7ac7fc5687d"},
 }
 
 

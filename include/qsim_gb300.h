@@ -100,11 +100,12 @@ typedef struct sim_plan_opts {
                                 spectral norms, so states of any magnitude are applied at the same
                                 precision relative to their norm; SIM_EUNSUPPORTED if that product
                                 exceeds 2^114.  complex128: 4 only (0 = 4): rows and columns are
-                                written in 49-bit fixed point relative to their largest entry, cut
-                                into seven 7-bit integer digits, and the digit products are summed
-                                exactly on the FP16 tensor cores (error-free splitting of Ozaki,
-                                Ogita, Oishi and Rump 2012); each result is within about 2^-49 of
-                                its row's and column's largest entries.  Every fused plan needs
+                                written in 47-bit fixed point relative to their largest entry, cut
+                                into six balanced 8-bit integer digits, and the digit products are
+                                summed exactly on the FP16 tensor cores (error-free splitting of
+                                Ozaki, Ogita, Oishi and Rump 2012); each result is within about
+                                2^-42 of its row's and column's largest entries at worst (2^-47 for
+                                the fixed-point rounding).  Every fused plan needs
                                 n >= k + 7 (SIM_EINVAL otherwise). */
     int32_t tile_qubits;     /* SIM_PLAN_STAGED: tile size log2 (0 = default) */
     int32_t flags;           /* SIM_FLAG_* bits, 0 = defaults */
