@@ -81,7 +81,7 @@ def test_c128_fused_haar_cz_24q(gsim, orc):
     check(orc, got, orc.apply_circuit(orc.basis_state(n, 0), g))
 
 
-@pytest.mark.parametrize("case", ["norm1e-150", "norm1e150", "span2^-300..2^0", "zero"])
+@pytest.mark.parametrize("case", ["norm1e-150", "norm1e150", "norm1e-295", "span2^-300..2^0", "zero"])
 def test_c128_fused_state_magnitudes(gsim, orc, case):
     """Each row is put in fixed point relative to its own largest component,
     so states of any magnitude, and rows whose entries span hundreds of
@@ -94,7 +94,9 @@ def test_c128_fused_state_magnitudes(gsim, orc, case):
         rng = np.random.default_rng(4)
         psi = np.exp2(rng.uniform(-300.0, 0.0, 2 ** n)) * np.exp(2j * np.pi * rng.uniform(0.0, 1.0, 2 ** n))
     else:
-        psi = C.random_state(n, seed=6) * {"norm1e-150": 1e-150, "norm1e150": 1e150}[case]
+        # 1e-295: row exponents near the bottom of the FP64 range (results that
+        # would fall below the normal range are flushed to zero)
+        psi = C.random_state(n, seed=6) * {"norm1e-150": 1e-150, "norm1e150": 1e150, "norm1e-295": 1e-295}[case]
     got = run(gsim, n, g, psi)
     ref = orc.apply_circuit(psi, g)
     if case == "zero":
