@@ -11,9 +11,9 @@
 //   - each row r of X (the 2^k amplitudes sharing all index bits outside the
 //     block, as 2^(k+1) reals) is written in fixed point relative to its
 //     largest component: |x| < 2^E_r, t = trunc(x 2^(47 - E_r)), |t| < 2^47,
-//     and t is cut into kPlanes = 6 balanced base-256 digits: t = sum_i d_i
-//     256^(5 - i) with d_1..d_5 in -128..127 and d_0 in -128..128 (the bytes
-//     of t + 128 (1 + 256 + ... + 256^4), each less 128);
+//     and t is cut into kPlanes = 6 balanced base-256 digits, t = sum_i d_i
+//     256^(5 - i) with |d_i| <= 128: the bytes of |t| + 128 (1 + 256 + ... +
+//     256^5), each less 128 (digit 0 from bits 40 and up), times x's sign;
 //   - each column n of W likewise relative to its largest entry (2^F_n);
 //   - a digit is an integer of magnitude at most 128, exact in FP16, and a
 //     product of two is at most 2^14; a K = 32 sum of them is at most 2^19,
@@ -40,10 +40,12 @@
 //   warp 16 (one thread): the 12 MMAs of tile i once A is written and
 //       accumulator i mod 2 has been drained (tile i - 2);
 //   warps 8-15: a thread per row and half of the columns reads the row's
-//       levels, forms the FP64 results and stores them to HBM.
-// The integer digit work sets this kernel's pace, so it is spread over 512
-// threads (at most 112 registers each) rather than 256: more warps to issue
-// from while others wait on shared memory or tensor memory.
+//       levels (4-column chunks, the next chunk's loads in flight while the
+//       current one is converted), forms the FP64 results and stores them.
+// The integer work (digit split, level recombination) sets this kernel's
+// pace, so it is spread over 512 threads (at most 112 registers each) rather
+// than 256: more warps to issue from while others wait on shared memory or
+// tensor memory.
 // Row exponents pass from converter to consumer through four shared-memory
 // slots with their own full / empty barriers.  Every wait is bounded; on a
 // timeout the kernel records SIM_ETIMEOUT, lets work in flight land (bounded
