@@ -181,13 +181,21 @@ int sim_apply_circuit(sim_t s, const sim_gate *gates, size_t n_gates, const sim_
  *   products).
  * sim_norm_expect_z: sim_norm and sim_expect_z_sum from one pass over the
  *   state (both read every |a_x|^2; the norm is the unweighted sum of the
- *   same accumulators, within about 1e-12 relative of sim_norm's). */
+ *   same accumulators, within about 1e-12 relative of sim_norm's).
+ * sim_sample_observe: sim_sample, plus the norm and <sum_i Z_i> of the same
+ *   state.  complex64 from 13 qubits, with shots > 0: one pass over the state
+ *   gives the sampler's sub-block sums, their total (the norm, C_total) and
+ *   the popcount-weighted sum; the shots are the ones sim_sample draws for
+ *   the same seed.  Otherwise sim_norm_expect_z's pass runs first.  norm and
+ *   expz are host pointers (required); out as for sim_sample. */
 int sim_probabilities(sim_t s, void *dev_out, int out_real);
 int sim_norm(sim_t s, double *out);
 int sim_measure(sim_t s, int qubit, uint64_t seed, uint64_t draw, int *outcome, double *prob);
 int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
 int sim_expect_z_sum(sim_t s, double *out);
 int sim_norm_expect_z(sim_t s, double *norm, double *expz);
+int sim_sample_observe(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device, double *norm,
+                       double *expz);
 
 /* ---- density matrices and noise ---------------------------------------------
  * The paper names density matrices among a simulator's outputs (§1) without

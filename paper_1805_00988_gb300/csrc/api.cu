@@ -405,6 +405,22 @@ int sim_sample(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on
     return run_sample(s, shots, seed, out, out_on_device);
 }
 
+int sim_sample_observe(sim_t s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device, double *norm,
+                       double *expz)
+{
+    if (int rc = check_state(s, "sim_sample_observe")) return rc;
+    if (!norm || !expz) return fail(SIM_EINVAL, "sim_sample_observe: NULL norm or expz");
+    if (shots > 0 && !out) return fail(SIM_EINVAL, "sim_sample_observe: out is NULL");
+    // complex64 from 13 qubits: one pass gives the sub-block sums, the norm
+    // (their total) and <sum Z>; otherwise the reduction pass runs first
+    if (shots > 0 && sample_observe_fused(s)) return run_sample(s, shots, seed, out, out_on_device, norm, expz);
+    double r[2];
+    if (int rc = reduce_sums(s, RED_EXPZ, 0, r)) return rc;
+    *expz = r[0];
+    *norm = r[1];
+    return run_sample(s, shots, seed, out, out_on_device);
+}
+
 int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, const sim_plan_opts *opts,
                       int64_t *passes, int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap,
                       size_t *order_len)

@@ -164,7 +164,10 @@ int launch_fuse_build_c128(qsim_state *s, const void *gates, const int *goff, in
 int launch_fused_c128(qsim_state *s, const void *block, const int *pos, int grid);
 int launch_probabilities(qsim_state *s, void *dev_out, int out_real);
 int launch_collapse(qsim_state *s, int qubit, int outcome, double scale);
-int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device);
+int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device,
+               double *norm_out = nullptr, double *expz_out = nullptr);
+// whether run_sample can form <sum Z> in its sub-block pass (complex64, n >= 13)
+bool sample_observe_fused(const qsim_state *s);
 
 // ---------------------------------------------------------------- plan lowering
 // A circuit gate reduced to what the tile and block planners need: a 2x2

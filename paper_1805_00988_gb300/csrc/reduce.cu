@@ -573,9 +573,16 @@ __device__ __forceinline__ double warp_incl_scan(double x, int lane)
 // per amplitude), and a 3-step xor tree inside the group gives the sub-sum.
 // Warp 0 then scans the block's sub-sums (warp_incl_scan) and the block sum is
 // the scan's last element -- k_resolve repeats that scan bit for bit.
-template <typename R>
+// kZ (complex64 full sub-blocks only): the same pass also forms the block's
+// <sum Z> partial as k_expz32 does (each 16-amplitude chunk's squares binned
+// by the popcount of the local index, weighted by n - 2 popcount, one
+// compensated sum carried into FP64), written to zpart[2 b] (zpart[2 b + 1] =
+// 0, the pair layout k_final_sum reads).  The sub-sums are computed exactly as
+// without it.
+template <typename R, bool kZ = false>
 __global__ void __launch_bounds__(256) k_sub_sums(const R *__restrict__ st, uint64_t bs, double *__restrict__ sub,
-                                                  double *__restrict__ bsum)
+                                                  double *__restrict__ bsum, int n = 0,
+                                                  double *__restrict__ zpart = nullptr)
 {
     using T = typename Amp<R>::T;
     const SubGeo g(bs);
@@ -584,7 +591,8 @@ __global__ void __launch_bounds__(256) k_sub_sums(const R *__restrict__ st, uint
     const uint32_t gl = (uint32_t)(lane & 7);                    // lane within the group
     const uint64_t base = (uint64_t)blockIdx.x * bs;
     __shared__ double ss[32];
-    double t = 0.0;
+    __shared__ double zs[8];
+    double t = 0.0, z = 0.0;
     if (j < g.nsub) {
         const uint32_t per = g.sub >= 8 ? g.sub / 8 : 1;         // amplitudes per lane
         if (gl * per < g.sub) {
@@ -613,6 +621,28 @@ __global__ void __launch_bounds__(256) k_sub_sums(const R *__restrict__ st, uint
                         }
                         t += widen_sum(A, pw.sh);
                     }
+                    if constexpr (kZ) {
+                        // amplitudes 16 ch .. 16 ch + 15: x[u] holds local indices 2u, 2u + 1
+                        const uint64_t ch = ((base + (uint64_t)j * g.sub + (uint64_t)gl * per) >> 4) + (uint64_t)h;
+                        Sq32 bin[5];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float4 y = scale4(x[u], pw.scale);
+                            bin[__builtin_popcount(2 * u)].add_sq(y.x);
+                            bin[__builtin_popcount(2 * u)].add_sq(y.y);
+                            bin[__builtin_popcount(2 * u + 1)].add_sq(y.z);
+                            bin[__builtin_popcount(2 * u + 1)].add_sq(y.w);
+                        }
+                        const int pc = __popcll(ch);
+                        Sq32 w;
+#pragma unroll
+                        for (int b = 0; b < 5; ++b) {
+                            const float wb = (float)(n - 2 * (pc + b));
+                            w.add_prod(bin[b].s, wb);
+                            w.e = __fmaf_rn(bin[b].e, wb, w.e);
+                        }
+                        z += widen_sum(w, pw.sh);
+                    }
                 }
             } else {
                 for (uint32_t e0 = 0; e0 < per; e0 += 8) {
@@ -633,10 +663,24 @@ __global__ void __launch_bounds__(256) k_sub_sums(const R *__restrict__ st, uint
         ss[j] = t;
         sub[(uint64_t)blockIdx.x * g.nsub + j] = t;
     }
+    if constexpr (kZ) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+        if (lane == 0) zs[warp] = z;
+    }
     __syncthreads();
     if (warp == 0) {
         const double c = warp_incl_scan(((uint32_t)lane < g.nsub) ? ss[lane] : 0.0, lane);
         if ((uint32_t)lane == g.nsub - 1) bsum[blockIdx.x] = c;
+    }
+    if constexpr (kZ) {
+        if (threadIdx.x == 0) {
+            double zz = 0.0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) zz += zs[w];
+            zpart[2 * blockIdx.x] = zz;
+            zpart[2 * blockIdx.x + 1] = 0.0;
+        }
     }
 }
 
@@ -1078,9 +1122,17 @@ int launch_collapse(qsim_state *s, int qubit, int outcome, double scale)
     return launch_end(s, "collapse");
 }
 
-int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device)
+bool sample_observe_fused(const qsim_state *s)
+{
+    return s->dtype == SIM_C64 && s->n >= kSampleLog && SubGeo(1ull << kSampleLog).sub == 256;
+}
+
+int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int out_on_device, double *norm_out,
+               double *expz_out)
 {
     if (shots == 0) return SIM_OK;
+    const bool obs = expz_out != nullptr;
+    if (obs && !sample_observe_fused(s)) return fail(SIM_EINVAL, "sample with <sum Z>: complex64, n >= 13 only");
     if (shots > 0xFFFFFFFFull) return fail(SIM_EINVAL, "sim_sample: at most 2^32 - 1 shots per call");
     const uint64_t N = 1ull << s->n;
     const uint64_t bs = (s->n >= kSampleLog) ? (1ull << kSampleLog) : N;
@@ -1097,6 +1149,7 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
     const size_t o_sblk = take(shots * 4), o_order = take(shots * 4);
     const uint64_t nchunk = (nb + kScanChunk - 1) / kScanChunk;
     const size_t o_cs = take(2 * nchunk * 8), o_cs32 = take(2 * nchunk * 4);
+    const size_t o_zpart = obs ? take(2 * nb * 8) : 0, o_zout = obs ? take(2 * 8) : 0;
     const size_t o_out = out_on_device ? 0 : take(shots * 8);
     char *scratch = nullptr;
     QSIM_CUDA(cudaMallocAsync((void **)&scratch, off, s->stream));
@@ -1110,27 +1163,39 @@ int run_sample(qsim_state *s, uint64_t shots, uint64_t seed, uint64_t *out, int 
     uint64_t *dout = out_on_device ? out : (uint64_t *)(scratch + o_out);
     double *cs = (double *)(scratch + o_cs);
     uint32_t *cs32 = (uint32_t *)(scratch + o_cs32);
+    double *zpart = obs ? (double *)(scratch + o_zpart) : nullptr, *zout = obs ? (double *)(scratch + o_zout) : nullptr;
     int rc = SIM_OK;
     const bool c128 = s->dtype == SIM_C128;
     do {
         launch_begin(s, KC_SAMPLE, (double)s->bytes);
         if (c128) k_sub_sums<double><<<(unsigned)nb, 256, 0, s->stream>>>((const double *)s->amps, bs, sub, bsum);
+        else if (obs)
+            k_sub_sums<float, true><<<(unsigned)nb, 256, 0, s->stream>>>((const float *)s->amps, bs, sub, bsum, s->n,
+                                                                       zpart);
         else k_sub_sums<float><<<(unsigned)nb, 256, 0, s->stream>>>((const float *)s->amps, bs, sub, bsum);
         if ((rc = launch_end(s, "sub-block sums"))) break;
+        if (obs) {
+            launch_begin(s, KC_REDUCE);
+            k_final_sum<<<1, kRedThreads, 0, s->stream>>>(zpart, (int)nb, zout);
+            if ((rc = launch_end(s, "<sum Z> total"))) break;
+        }
         if ((rc = scan_exclusive<double>(s, bsum, bexcl, nb, tot, cs, "block scan"))) break;
         launch_begin(s, KC_SAMPLE);
         k_last_nonzero<<<1, 32, 0, s->stream>>>(bsum, nb, last);
         if ((rc = launch_end(s, "last nonzero"))) break;
         // the host needs the last non-zero block as a launch argument: read it
         // together with the total (one small copy; the state stays on device)
-        double htot = 0.0;
+        double htot = 0.0, hz = 0.0;
         uint64_t hlast = 0;
         if (cudaMemcpyAsync(&htot, tot, 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
             cudaMemcpyAsync(&hlast, last, 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess ||
+            (obs && cudaMemcpyAsync(&hz, zout, 8, cudaMemcpyDeviceToHost, s->stream) != cudaSuccess) ||
             cudaStreamSynchronize(s->stream) != cudaSuccess) {
             rc = cuda_fail(cudaGetLastError(), "sample readback");
             break;
         }
+        if (norm_out) *norm_out = htot;
+        if (expz_out) *expz_out = hz;
         if (!(htot > 0.0)) { rc = fail(SIM_EINVAL, "sim_sample: the state has zero norm"); break; }
         if (cudaMemsetAsync(cnt, 0, nb * 4, s->stream) != cudaSuccess) { rc = cuda_fail(cudaGetLastError(), "memset"); break; }
         launch_begin(s, KC_SAMPLE);

@@ -82,6 +82,7 @@ _sig("sim_probabilities", [P, P, _i32])
 _sig("sim_norm", [P, P])
 _sig("sim_measure", [P, _i32, _u64, _u64, P, P])
 _sig("sim_sample", [P, _u64, _u64, P, _i32])
+_sig("sim_sample_observe", [P, _u64, _u64, P, _i32, P, P])
 _sig("sim_expect_z_sum", [P, P])
 _sig("sim_profile_enable", [P, _i32])
 _sig("sim_profile_read", [P, _i32, P, P, P, P, _i32])
@@ -230,6 +231,19 @@ def sim_sample(h: int, shots: int, seed: int, out=None, out_on_device: bool = Fa
 
 
 _sig("sim_plan_describe", [_i32, _i32, P, _sz, P, P, P, P, P, _sz, P])
+
+
+def sim_sample_observe(h: int, shots: int, seed: int, out=None, out_on_device: bool = False):
+    """Shots as sim_sample draws them, plus (norm, <sum Z>) of the same state:
+    returns (shots, norm, expz); for complex64 from 13 qubits all three come
+    from one pass over the state."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    if out_on_device:
+        check(_lib.sim_sample_observe(P(h), shots, seed, P(out), 1, ctypes.byref(a), ctypes.byref(b)))
+        return out, a.value, b.value
+    arr = np.empty(shots, dtype=np.uint64) if out is None else out
+    check(_lib.sim_sample_observe(P(h), shots, seed, arr.ctypes.data_as(P), 0, ctypes.byref(a), ctypes.byref(b)))
+    return arr, a.value, b.value
 
 
 def sim_plan_describe(n: int, dtype: int, sim_gates: np.ndarray, opts: sim_plan_opts):

@@ -250,6 +250,31 @@ def test_sample_matches_oracle(sim, orc, dt, n):
     st.close()
 
 
+@pytest.mark.parametrize("dt", ["c64", "c128"])
+@pytest.mark.parametrize("n,scale", [(3, 1.0), (12, 1.0), (13, 1.0), (16, 1.0), (16, 3e-5), (21, 1.0)])
+def test_sample_observe_matches_sample_and_oracle(sim, orc, dt, n, scale):
+    """sim_sample_observe: the shots are sim_sample's for the same seed (the
+    one-pass form computes the sub-block sums with the same operations), and
+    the norm and <sum Z> match the oracle on the GPU's own state (complex64
+    from 13 qubits: from the sampler's pass; otherwise from the reduction)."""
+    st = sim.State(n, dt)
+    psi0 = C.random_state(n, seed=n + 3) * scale
+    st.load(psi0)
+    st.apply(C.random_gates(n, 50, seed=n + 3))
+    psi = st.state().astype(np.complex128)
+    nref, zref = orc.norm2(psi), orc.expect_z_sum(psi)
+    shots = 20000
+    ref_shots = st.sample(shots, seed=55)
+    got, nrm, ez = sim.sim_sample_observe(st.h, shots, 55)
+    np.testing.assert_array_equal(got, ref_shots)
+    assert abs(nrm - nref) <= 1e-12 * nref
+    assert abs(ez - zref) <= 1e-11 * nref
+    # zero shots: the norm and <sum Z> only
+    _, nrm0, ez0 = sim.sim_sample_observe(st.h, 0, 55)
+    assert abs(nrm0 - nref) <= 1e-12 * nref and abs(ez0 - zref) <= 1e-11 * nref
+    st.close()
+
+
 @pytest.mark.parametrize("q", [0, 9, 15])
 def test_sample_after_collapse_matches_oracle(sim, orc, q):
     """After a measurement half of the amplitudes are exactly zero: whole
