@@ -362,6 +362,7 @@ extern "C" int sim_batch_create_opts(int count, const int32_t *n_qubits, const i
         // the state, every pass but the last writes it (8 B per amplitude)
         if (ps.size() > 1) alg_scratch += 2.0 * (double)(ps.size() - 1) * std::ldexp(8.0, nplan);
         PlanBuilder<float> pb{nplan, M, M - kThrBits, 2, {}, {}, 0};
+        pb.allow_ramps = false;   // the batched kernel runs the tile engine without ramps
         BCirc bc{};
         bc.n = n;
         bc.npass = (int)ps.size();

@@ -29,8 +29,10 @@ namespace qsim {
 namespace {
 
 // complex64 tiles of up to 12 qubits hold 16 amplitudes a thread and fit 80
-// registers: three CTAs per SM; 13-qubit and complex128 tiles two
-template <typename R, int M>
+// registers: three CTAs per SM; 13-qubit and complex128 tiles two.  kRamp:
+// the variant that also runs SK_RAMP ops, launched for the passes that have
+// them.
+template <typename R, int M, bool kRamp>
 __global__ void __launch_bounds__(kThr, (sizeof(R) == 4 && M <= 12 ? 3 : 2))
 k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
                                                    TileGeom geo)
@@ -91,7 +93,7 @@ k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
         }
     }
 
-    apply_ops<R, M>(v, ops, nops, base, tid, sm,
+    apply_ops<R, M, kRamp>(v, ops, nops, base, tid, sm,
                     reinterpret_cast<StOp<R> *>(smem_raw + ((size_t)1 << M) * 2 * sizeof(R)));
     {
         int t2 = tid;
@@ -121,17 +123,24 @@ k_staged(R *__restrict__ st, const StOp<R> *__restrict__ ops, int nops,
     }
 }
 
-template <typename R, int M>
-int launch_staged(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &geo, double flops)
+template <typename R, int M, bool kRamp>
+int launch_staged_v(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &geo, double flops)
 {
     const size_t smem = ((size_t)1 << M) * 2 * sizeof(R) + op_stage_bytes<R>();
     // set on every launch: the attribute belongs to the current device's
     // context, and the call costs a microsecond against a multi-ms pass
-    QSIM_CUDA(cudaFuncSetAttribute(k_staged<R, M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    QSIM_CUDA(cudaFuncSetAttribute(k_staged<R, M, kRamp>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const uint64_t tiles = 1ull << (s->n - M);
     launch_begin(s, KC_STAGED, 2.0 * (double)s->bytes, flops);
-    k_staged<R, M><<<(unsigned)tiles, kThr, smem, s->stream>>>((R *)s->amps, dops, nops, geo);
+    k_staged<R, M, kRamp><<<(unsigned)tiles, kThr, smem, s->stream>>>((R *)s->amps, dops, nops, geo);
     return launch_end(s, "staged pass");
+}
+
+template <typename R, int M>
+int launch_staged(qsim_state *s, const StOp<R> *dops, int nops, const TileGeom &geo, double flops, bool ramp)
+{
+    return ramp ? launch_staged_v<R, M, true>(s, dops, nops, geo, flops)
+                : launch_staged_v<R, M, false>(s, dops, nops, geo, flops);
 }
 
 template <typename R>
@@ -142,8 +151,13 @@ int run_staged(qsim_state *s, const std::vector<SGate> &g, int M)
     PlanBuilder<R> pb{s->n, M, M - kThrBits, VEC, {}, {}, 0};
     std::vector<int> counts;
     std::vector<double> pflops;
+    std::vector<char> ramp;
     for (const Pass &ps : passes) {
+        const size_t first = pb.ops.size();
         counts.push_back(pb.schedule(ps, g));
+        bool r = false;
+        for (size_t k = first; k < pb.ops.size() && !r; ++k) r = pb.ops[k].kind == SK_RAMP;
+        ramp.push_back(r);
         double f = 0.0;
         for (int m : ps.members) f += sgate_flops(g[m], s->n);
         pflops.push_back(f);
@@ -167,10 +181,10 @@ int run_staged(qsim_state *s, const std::vector<SGate> &g, int M)
             if (!((q >> b) & 1)) geo.outer_pos[geo.n_outer++] = b;
         int rc;
         switch (M) {
-        case 11: rc = launch_staged<R, 11>(s, dops + off, counts[p], geo, pflops[p]); break;
-        case 12: rc = launch_staged<R, 12>(s, dops + off, counts[p], geo, pflops[p]); break;
+        case 11: rc = launch_staged<R, 11>(s, dops + off, counts[p], geo, pflops[p], ramp[p]); break;
+        case 12: rc = launch_staged<R, 12>(s, dops + off, counts[p], geo, pflops[p], ramp[p]); break;
         case 13:
-            if constexpr (sizeof(R) == 4) rc = launch_staged<R, 13>(s, dops + off, counts[p], geo, pflops[p]);
+            if constexpr (sizeof(R) == 4) rc = launch_staged<R, 13>(s, dops + off, counts[p], geo, pflops[p], ramp[p]);
             else rc = fail(SIM_EINVAL, "staged: complex128 tiles are at most 12 qubits");
             break;
         default: rc = fail(SIM_EINVAL, "staged: unsupported tile size");

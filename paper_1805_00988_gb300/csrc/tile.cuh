@@ -17,7 +17,18 @@ constexpr int kLow = 5;          // qubits 0..4 are local bits 0..4 of every til
 constexpr int kThr = 256;        // threads per CTA
 constexpr int kThrBits = 8;
 
-enum StKind { SK_LAYOUT = 0, SK_DENSE, SK_ANTI, SK_XPERM, SK_DIAG, SK_PHASE, SK_NEG };
+enum StKind { SK_LAYOUT = 0, SK_DENSE, SK_ANTI, SK_XPERM, SK_DIAG, SK_PHASE, SK_NEG, SK_RAMP, SK_NOP };
+
+// SK_RAMP: a run of controlled phases that share one qubit q, each pairing q
+// with a different tile-local qubit m (phase f_m when both bits are 1),
+// applied at once: amplitudes whose q bit is 1 are multiplied by the product
+// of f_m over the local bits m that are 1.  The op is kRampRecords records:
+// the first carries q as a diagonal op's target (km_t / thr_t / out_t), and
+// the coefficient slots m[] of all four hold the factors, factor f at record
+// f / 4, slots 2 (f % 4) and 2 (f % 4) + 1: f = j for register bit j (j < 5),
+// f = 5 + i for thread bit i (1 where no qubit of the run sits).
+constexpr int kRampRecords = 4;
+constexpr int kRampThr0 = 5;
 
 template <typename R>
 struct __align__(16) StOp {
@@ -360,7 +371,7 @@ __host__ __device__ constexpr size_t op_stage_bytes() { return (size_t)kOpChunk 
 // tile outside Q; sm = the tile's shared memory (2^M amplitudes); sops =
 // shared memory for kOpChunk ops.  Every thread of the CTA runs the same op
 // sequence (the chunk copies are CTA-wide).
-template <typename R, int M>
+template <typename R, int M, bool kRamp = false>
 __device__ __forceinline__ void apply_ops(Regs<R, (1 << (M - kThrBits))> &v, const StOp<R> *__restrict__ gops,
                                           int nops, uint64_t base, int tid, R *sm, StOp<R> *sops)
 {
@@ -388,6 +399,51 @@ __device__ __forceinline__ void apply_ops(Regs<R, (1 << (M - kThrBits))> &v, con
             flush_neg(v, negm);
             relayout<M, RB, VEC>(layout, arg, v, sm, tid);
             layout = arg;
+            continue;
+        }
+        if (kind == SK_NOP) continue;
+        // passes with ramps run the kernel variant compiled with kRamp (the
+        // ramp's code costs registers the other passes need)
+        if (kRamp && kind == SK_RAMP) {
+            // the records of one ramp never straddle a chunk (the planner pads)
+            const StOp<R> *rp = ops + p;
+            auto factor = [&](int f, R &fr, R &fi) {
+                fr = rp[f >> 2].m[2 * (f & 3)];
+                fi = rp[f >> 2].m[2 * (f & 3) + 1];
+            };
+            const bool qt = ((tid & rp->thr_t) != 0) || ((base & rp->out_t) != 0);
+            const uint64_t one = qt ? ~0ull : rp->km_t;
+            if (one) {
+                // the thread's factor: its thread bits that are 1
+                R Fr = (R)1, Fi = (R)0;
+#pragma unroll
+                for (int i = 0; i < kThrBits; ++i)
+                    if ((tid >> i) & 1) {
+                        R ar, ai;
+                        factor(kRampThr0 + i, ar, ai);
+                        const R tr = Fr * ar - Fi * ai;
+                        Fi = Fr * ai + Fi * ar;
+                        Fr = tr;
+                    }
+#pragma unroll
+                for (int k = 0; k < RA; ++k)
+                    if ((one >> k) & 1) {
+                        R Gr = Fr, Gi = Fi;
+#pragma unroll
+                        for (int j = 0; j < RB; ++j)
+                            if ((k >> j) & 1) {
+                                R ar, ai;
+                                factor(j, ar, ai);
+                                const R tr = Gr * ar - Gi * ai;
+                                Gi = Gr * ai + Gi * ar;
+                                Gr = tr;
+                            }
+                        const R vr = v.getr(k), vi = v.geti(k);
+                        v.setr(k, Gr * vr - Gi * vi);
+                        v.seti(k, Gr * vi + Gi * vr);
+                    }
+            }
+            p += kRampRecords - 1;
             continue;
         }
         const bool tok = ((tid & ops[p].thr_c) == ops[p].thr_c) && ((base & ops[p].out_c) == ops[p].out_c);
@@ -492,12 +548,21 @@ std::vector<Pass> form_passes(const std::vector<SGate> &g, int n, int M)
     return passes;
 }
 
+// a controlled phase on two qubits (phase on |11>, not a sign flip, which
+// the lazy sign mask handles for free): a candidate for a ramp
+inline bool ramp_candidate(const SGate &g)
+{
+    return g.op == OP_DIAG_HI && __builtin_popcountll(g.ctrl) == 1 && !(g.m[6] == -1.0 && g.m[7] == 0.0);
+}
+
 template <typename R>
 struct PlanBuilder {
     int n, M, RB, VEC;
     std::vector<StOp<R>> ops;
     std::vector<int> order;       // circuit index of each emitted gate op
     int layout_changes = 0;
+    size_t pass_start = 0;        // first op of the pass being scheduled (chunks count from it)
+    bool allow_ramps = true;      // merge runs of controlled phases into SK_RAMP ops
 
     int local_of(const Pass &ps, int q) const
     {
@@ -552,6 +617,47 @@ struct PlanBuilder {
         ops.push_back(o);
     }
 
+    // one SK_RAMP: amplitudes with qubit q at 1 times the product of the phases
+    // of the pairs (q, m) whose local qubit m is 1 (see SK_RAMP)
+    void emit_ramp(const Pass &ps, int q, const std::vector<std::pair<int, const SGate *>> &pairs, int layout)
+    {
+        // the records stay inside one chunk of kOpChunk ops
+        while ((ops.size() - pass_start) % kOpChunk > (size_t)(kOpChunk - kRampRecords)) {
+            StOp<R> nop;
+            memset(&nop, 0, sizeof nop);
+            nop.kind = SK_NOP;
+            ops.push_back(nop);
+        }
+        constexpr int nf = 4 * kRampRecords;      // factor slots: four complex values per record
+        double fr[nf], fi[nf];
+        for (int f = 0; f < nf; ++f) { fr[f] = 1.0; fi[f] = 0.0; }
+        for (const auto &pm : pairs) {
+            const int b = local_of(ps, pm.first);
+            const int j = reg_of(layout, b);
+            const int f = (j >= 0) ? j : kRampThr0 + thr_of(layout, b);
+            const double pr = pm.second->m[6], pi = pm.second->m[7];
+            const double tr = fr[f] * pr - fi[f] * pi;
+            fi[f] = fr[f] * pi + fi[f] * pr;
+            fr[f] = tr;
+        }
+        StOp<R> rec[kRampRecords];
+        memset(rec, 0, sizeof rec);
+        rec[0].kind = SK_RAMP;
+        const int bq = local_of(ps, q);
+        uint32_t reg_t = 0;
+        if (bq < 0) rec[0].out_t = 1ull << q;
+        else if (reg_of(layout, bq) >= 0) reg_t = 1u << reg_of(layout, bq);
+        else rec[0].thr_t = 1u << thr_of(layout, bq);
+        for (int k = 0; k < (1 << RB); ++k)
+            if ((uint32_t)k & reg_t) rec[0].km_t |= 1ull << k;
+        for (int f = 0; f < nf; ++f) {
+            rec[f >> 2].m[2 * (f & 3)] = (R)fr[f];
+            rec[f >> 2].m[2 * (f & 3) + 1] = (R)fi[f];
+        }
+        for (int r = 1; r < kRampRecords; ++r) rec[r].kind = SK_NOP;
+        for (int r = 0; r < kRampRecords; ++r) ops.push_back(rec[r]);
+    }
+
     void emit_layout(int l)
     {
         ++layout_changes;
@@ -568,6 +674,7 @@ struct PlanBuilder {
     {
         const size_t P = ps.members.size();
         const size_t start = ops.size();
+        pass_start = start;
         std::vector<int> indeg(P, 0);
         std::vector<std::vector<int>> succ(P);
         for (size_t a = 0; a < P; ++a)
@@ -586,7 +693,12 @@ struct PlanBuilder {
             return reg_of(l, local_of(ps, s.target)) >= 0;
         };
         while (left) {
+            // controlled phases wait while any other gate can run: the gates
+            // that run first free more phases to join one ramp
             int pick = -1;
+            for (size_t i = 0; i < P && pick < 0 && allow_ramps; ++i)
+                if (!emitted[i] && indeg[i] == 0 && !ramp_candidate(g[ps.members[i]]) && fits((int)i, layout))
+                    pick = (int)i;
             for (size_t i = 0; i < P && pick < 0; ++i)
                 if (!emitted[i] && indeg[i] == 0 && fits((int)i, layout)) pick = (int)i;
             if (pick < 0) {
@@ -602,11 +714,52 @@ struct PlanBuilder {
                 layout = best;
                 continue;
             }
+            auto mark = [&](int i) {
+                order.push_back(g[ps.members[i]].orig);
+                emitted[i] = 1;
+                --left;
+                for (int s2 : succ[i]) indeg[s2]--;
+            };
+            if (allow_ramps && ramp_candidate(g[ps.members[pick]])) {
+                // every controlled phase that could run now and shares a qubit
+                // with this one goes into one ramp over the qubit they share
+                // most (the partner qubit must be inside the tile)
+                const SGate &a = g[ps.members[pick]];
+                const int qa = a.target, qb = __builtin_ctzll(a.ctrl);
+                auto partner = [&](const SGate &c, int q) {
+                    const int t = c.target, u = __builtin_ctzll(c.ctrl);
+                    return t == q ? u : (u == q ? t : -1);
+                };
+                std::vector<int> cand;
+                for (size_t i = 0; i < P; ++i)
+                    if (!emitted[i] && indeg[i] == 0 && ramp_candidate(g[ps.members[i]])) cand.push_back((int)i);
+                int best_q = -1;
+                size_t best = 0;
+                for (int q : {qa, qb}) {
+                    size_t c = 0;
+                    for (int i : cand) {
+                        const int m = partner(g[ps.members[i]], q);
+                        if (m >= 0 && local_of(ps, m) >= 0) ++c;
+                    }
+                    if (c > best) { best = c; best_q = q; }
+                }
+                if (best >= 3) {
+                    std::vector<std::pair<int, const SGate *>> pairs;
+                    std::vector<int> used;
+                    for (int i : cand) {
+                        const int m = partner(g[ps.members[i]], best_q);
+                        if (m >= 0 && local_of(ps, m) >= 0) {
+                            pairs.push_back({m, &g[ps.members[i]]});
+                            used.push_back(i);
+                        }
+                    }
+                    emit_ramp(ps, best_q, pairs, layout);
+                    for (int i : used) mark(i);
+                    continue;
+                }
+            }
             emit_gate(ps, g[ps.members[pick]], layout);
-            order.push_back(g[ps.members[pick]].orig);
-            emitted[pick] = 1;
-            --left;
-            for (int s2 : succ[pick]) indeg[s2]--;
+            mark(pick);
         }
         if (layout != 0) emit_layout(0);
         return (int)(ops.size() - start);
