@@ -26,7 +26,9 @@ enum StKind { SK_LAYOUT = 0, SK_DENSE, SK_ANTI, SK_XPERM, SK_DIAG, SK_PHASE, SK_
 // the first carries q as a diagonal op's target (km_t / thr_t / out_t), and
 // the coefficient slots m[] of all four hold the factors, factor f at record
 // f / 4, slots 2 (f % 4) and 2 (f % 4) + 1: f = j for register bit j (j < 5),
-// f = 5 + i for thread bit i (1 where no qubit of the run sits).
+// f = 5 + i for thread bit i (1 where no qubit of the run sits).  Its three
+// trailing records, and the padding that keeps a ramp inside one staged chunk
+// of kOpChunk ops, are SK_NOP records.
 constexpr int kRampRecords = 4;
 constexpr int kRampThr0 = 5;
 
