@@ -5,6 +5,7 @@
     python -m paper_1805_00988_gb300.kernel_cases batch     # 512 variational circuits, one persistent launch
     python -m paper_1805_00988_gb300.kernel_cases c128      # complex128 fused 4-qubit blocks, 27 qubits (2 GiB)
     python -m paper_1805_00988_gb300.kernel_cases channel   # density-matrix channel passes, 13-qubit rho (26-qubit register)
+    python -m paper_1805_00988_gb300.kernel_cases qft       # App. A QFT in register tiles (phase ramps), 26 qubits
 
 Each case holds a few GB on the device at most (a 27-qubit complex64 state
 is 1 GiB, 8x the L2), so a full ncu capture of one launch ends in a minute
@@ -35,6 +36,9 @@ def main(argv=None):
     elif mode == "c128":
         st = sim.State(27, "c128")
         st.apply(C.haar_cz(27, 3, seed=1234), plan="fused", fuse_k=4)
+    elif mode == "qft":
+        st = sim.State(26, "c64")
+        st.apply(C.qft_paper(26), plan="staged")
     elif mode == "channel":
         rho = sim.DensityMatrix(13, "c64")
         rho.apply(C.haar_cz(13, 1, seed=1234), plan="per_gate")
@@ -49,7 +53,7 @@ def main(argv=None):
         b.run()
         b.close()
     else:
-        raise SystemExit("unknown case %r (k6, pergate, batch, c128, channel)" % mode)
+        raise SystemExit("unknown case %r (k6, pergate, batch, c128, channel, qft)" % mode)
     torch.cuda.synchronize()
     print("ok", mode)
 
