@@ -4,6 +4,7 @@
 // See staged.cu for the design.
 #pragma once
 
+#include <complex>
 #include <cstring>
 #include <vector>
 
@@ -20,17 +21,19 @@ constexpr int kThrBits = 8;
 enum StKind { SK_LAYOUT = 0, SK_DENSE, SK_ANTI, SK_XPERM, SK_DIAG, SK_PHASE, SK_NEG, SK_RAMP, SK_NOP };
 
 // SK_RAMP: a run of controlled phases that share one qubit q, each pairing q
-// with a different tile-local qubit m (phase f_m when both bits are 1),
-// applied at once: amplitudes whose q bit is 1 are multiplied by the product
-// of f_m over the local bits m that are 1.  The op is kRampRecords records:
-// the first carries q as a diagonal op's target (km_t / thr_t / out_t), and
-// the coefficient slots m[] of all four hold the factors, factor f at record
-// f / 4, slots 2 (f % 4) and 2 (f % 4) + 1: f = j for register bit j (j < 5),
-// f = 5 + i for thread bit i (1 where no qubit of the run sits).  Its three
-// trailing records, and the padding that keeps a ramp inside one staged chunk
-// of kOpChunk ops, are SK_NOP records.
-constexpr int kRampRecords = 4;
-constexpr int kRampThr0 = 5;
+// with a tile-local qubit m (phase f_m when both bits are 1), applied at
+// once: amplitudes whose q bit is 1 are multiplied by the product of f_m over
+// the local bits m that are 1 -- the product over the thread's thread bits
+// times the product over the register's register bits.  The host tabulates
+// both: entry k < RA is register k's product, entries RA + x and RA + 16 + y
+// the products over thread bits 0..3 set in x and 4..7 set in y, so a thread
+// forms its factor from two entries and each register needs one more.  Entry
+// e sits in record e / 4 of the op, coefficient slots 2 (e % 4) and
+// 2 (e % 4) + 1; the first record also carries q as a diagonal op's target
+// (km_t / thr_t / out_t).  The other records, and the padding that keeps a
+// ramp inside one staged chunk of kOpChunk ops, are SK_NOP records.
+__host__ __device__ constexpr int ramp_records(int RA) { return (RA + 32 + 3) / 4; }
+static_assert(kThrBits == 8, "ramp tables cover thread bits as two groups of four");
 
 template <typename R>
 struct __align__(16) StOp {
@@ -409,43 +412,30 @@ __device__ __forceinline__ void apply_ops(Regs<R, (1 << (M - kThrBits))> &v, con
         if (kRamp && kind == SK_RAMP) {
             // the records of one ramp never straddle a chunk (the planner pads)
             const StOp<R> *rp = ops + p;
-            auto factor = [&](int f, R &fr, R &fi) {
-                fr = rp[f >> 2].m[2 * (f & 3)];
-                fi = rp[f >> 2].m[2 * (f & 3) + 1];
+            auto entry = [&](int e, R &fr, R &fi) {
+                fr = rp[e >> 2].m[2 * (e & 3)];
+                fi = rp[e >> 2].m[2 * (e & 3) + 1];
             };
             const bool qt = ((tid & rp->thr_t) != 0) || ((base & rp->out_t) != 0);
             const uint64_t one = qt ? ~0ull : rp->km_t;
             if (one) {
-                // the thread's factor: its thread bits that are 1
-                R Fr = (R)1, Fi = (R)0;
-#pragma unroll
-                for (int i = 0; i < kThrBits; ++i)
-                    if ((tid >> i) & 1) {
-                        R ar, ai;
-                        factor(kRampThr0 + i, ar, ai);
-                        const R tr = Fr * ar - Fi * ai;
-                        Fi = Fr * ai + Fi * ar;
-                        Fr = tr;
-                    }
+                // the thread's factor from its low and high four thread bits
+                R ar, ai, br, bi;
+                entry(RA + (tid & 15), ar, ai);
+                entry(RA + 16 + ((tid >> 4) & 15), br, bi);
+                const R Fr = ar * br - ai * bi, Fi = ar * bi + ai * br;
 #pragma unroll
                 for (int k = 0; k < RA; ++k)
                     if ((one >> k) & 1) {
-                        R Gr = Fr, Gi = Fi;
-#pragma unroll
-                        for (int j = 0; j < RB; ++j)
-                            if ((k >> j) & 1) {
-                                R ar, ai;
-                                factor(j, ar, ai);
-                                const R tr = Gr * ar - Gi * ai;
-                                Gi = Gr * ai + Gi * ar;
-                                Gr = tr;
-                            }
+                        R gr, gi;
+                        entry(k, gr, gi);
+                        const R Gr = Fr * gr - Fi * gi, Gi = Fr * gi + Fi * gr;
                         const R vr = v.getr(k), vi = v.geti(k);
                         v.setr(k, Gr * vr - Gi * vi);
                         v.seti(k, Gr * vi + Gi * vr);
                     }
             }
-            p += kRampRecords - 1;
+            p += ramp_records(RA) - 1;
             continue;
         }
         const bool tok = ((tid & ops[p].thr_c) == ops[p].thr_c) && ((base & ops[p].out_c) == ops[p].out_c);
@@ -624,40 +614,51 @@ struct PlanBuilder {
     void emit_ramp(const Pass &ps, int q, const std::vector<std::pair<int, const SGate *>> &pairs, int layout)
     {
         // the records stay inside one chunk of kOpChunk ops
-        while ((ops.size() - pass_start) % kOpChunk > (size_t)(kOpChunk - kRampRecords)) {
+        const int RA = 1 << RB, nrec = ramp_records(RA);
+        while ((ops.size() - pass_start) % kOpChunk > (size_t)(kOpChunk - nrec)) {
             StOp<R> nop;
             memset(&nop, 0, sizeof nop);
             nop.kind = SK_NOP;
             ops.push_back(nop);
         }
-        constexpr int nf = 4 * kRampRecords;      // factor slots: four complex values per record
-        double fr[nf], fi[nf];
-        for (int f = 0; f < nf; ++f) { fr[f] = 1.0; fi[f] = 0.0; }
+        // per-bit factors: register bit j, thread bit i (products of repeated pairs)
+        std::complex<double> freg[8], fthr[kThrBits];
+        for (auto &f : freg) f = 1.0;
+        for (auto &f : fthr) f = 1.0;
         for (const auto &pm : pairs) {
             const int b = local_of(ps, pm.first);
             const int j = reg_of(layout, b);
-            const int f = (j >= 0) ? j : kRampThr0 + thr_of(layout, b);
-            const double pr = pm.second->m[6], pi = pm.second->m[7];
-            const double tr = fr[f] * pr - fi[f] * pi;
-            fi[f] = fr[f] * pi + fi[f] * pr;
-            fr[f] = tr;
+            const std::complex<double> ph(pm.second->m[6], pm.second->m[7]);
+            if (j >= 0) freg[j] *= ph;
+            else fthr[thr_of(layout, b)] *= ph;
         }
-        StOp<R> rec[kRampRecords];
-        memset(rec, 0, sizeof rec);
+        // the tables (see SK_RAMP), each entry one FP64 product rounded once
+        std::vector<std::complex<double>> tab(4 * nrec, 1.0);
+        for (int k = 0; k < RA; ++k)
+            for (int j = 0; j < RB; ++j)
+                if ((k >> j) & 1) tab[k] *= freg[j];
+        for (int x = 0; x < 16; ++x)
+            for (int i = 0; i < 4; ++i)
+                if ((x >> i) & 1) {
+                    tab[RA + x] *= fthr[i];
+                    tab[RA + 16 + x] *= fthr[4 + i];
+                }
+        std::vector<StOp<R>> rec(nrec);
+        memset(rec.data(), 0, sizeof(StOp<R>) * nrec);
         rec[0].kind = SK_RAMP;
         const int bq = local_of(ps, q);
         uint32_t reg_t = 0;
         if (bq < 0) rec[0].out_t = 1ull << q;
         else if (reg_of(layout, bq) >= 0) reg_t = 1u << reg_of(layout, bq);
         else rec[0].thr_t = 1u << thr_of(layout, bq);
-        for (int k = 0; k < (1 << RB); ++k)
+        for (int k = 0; k < RA; ++k)
             if ((uint32_t)k & reg_t) rec[0].km_t |= 1ull << k;
-        for (int f = 0; f < nf; ++f) {
-            rec[f >> 2].m[2 * (f & 3)] = (R)fr[f];
-            rec[f >> 2].m[2 * (f & 3) + 1] = (R)fi[f];
+        for (int e = 0; e < 4 * nrec; ++e) {
+            rec[e >> 2].m[2 * (e & 3)] = (R)tab[e].real();
+            rec[e >> 2].m[2 * (e & 3) + 1] = (R)tab[e].imag();
         }
-        for (int r = 1; r < kRampRecords; ++r) rec[r].kind = SK_NOP;
-        for (int r = 0; r < kRampRecords; ++r) ops.push_back(rec[r]);
+        for (int r = 1; r < nrec; ++r) rec[r].kind = SK_NOP;
+        for (int r = 0; r < nrec; ++r) ops.push_back(rec[r]);
     }
 
     void emit_layout(int l)
