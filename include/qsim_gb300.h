@@ -367,7 +367,8 @@ int sim_last_plan(sim_t s, int32_t *variants, size_t cap, size_t *len);
 /* ---- plan introspection (host only, no GPU needed) ---------------------------
  * sim_plan_describe: build the SIM_PLAN_STAGED schedule of a circuit for an
  *   n-qubit register of the given dtype without running it.  Outputs (any may
- *   be NULL): the number of tile passes, of encoded ops, of register-layout
+ *   be NULL): the number of tile passes, of ops (gate ops, layout changes,
+ *   and phase ramps -- one per ramp, whatever its records), of register-layout
  *   changes, and the order in which the gates are applied (circuit indices;
  *   a SWAP appears three times, lowered to three CNOT-type moves; identity
  *   gates are dropped) -- up to order_cap entries, the full length in

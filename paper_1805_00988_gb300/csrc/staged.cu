@@ -211,7 +211,7 @@ int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int
     PlanBuilder<double> pb{n, M, M - kThrBits, c128 ? 1 : 2, {}, {}, 0};
     for (const Pass &p : ps) pb.schedule(p, g);
     if (passes) *passes = (int64_t)ps.size();
-    if (ops) *ops = (int64_t)pb.ops.size();
+    if (ops) *ops = (int64_t)(pb.ops.size() - pb.filler);   // a phase ramp counts once
     if (layout_changes) *layout_changes = pb.layout_changes;
     if (order_len) *order_len = pb.order.size();
     if (order)

@@ -555,6 +555,7 @@ struct PlanBuilder {
     int layout_changes = 0;
     size_t pass_start = 0;        // first op of the pass being scheduled (chunks count from it)
     bool allow_ramps = true;      // merge runs of controlled phases into SK_RAMP ops
+    size_t filler = 0;            // SK_NOP records (a ramp's table records and padding)
 
     int local_of(const Pass &ps, int q) const
     {
@@ -620,6 +621,7 @@ struct PlanBuilder {
             memset(&nop, 0, sizeof nop);
             nop.kind = SK_NOP;
             ops.push_back(nop);
+            ++filler;
         }
         // per-bit factors: register bit j, thread bit i (products of repeated pairs)
         std::complex<double> freg[8], fthr[kThrBits];
@@ -658,6 +660,7 @@ struct PlanBuilder {
             rec[e >> 2].m[2 * (e & 3) + 1] = (R)tab[e].imag();
         }
         for (int r = 1; r < nrec; ++r) rec[r].kind = SK_NOP;
+        filler += (size_t)(nrec - 1);
         for (int r = 0; r < nrec; ++r) ops.push_back(rec[r]);
     }
 
