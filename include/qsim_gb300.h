@@ -382,6 +382,43 @@ int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, c
                       int64_t *passes, int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap,
                       size_t *order_len);
 
+/* sim_plan_staged_ops: the SIM_PLAN_STAGED encoding of a circuit, host only,
+ *   for inspection and for checking the planner without a GPU (the record
+ *   layout follows the library's version).  A tile is 2^M amplitudes: local
+ *   bits 0..4 are qubits 0..4, local bit 5 + i is the pass's high qubit i;
+ *   256 threads hold 2^(M - 8) registers each.  Register layout l places
+ *   register bit j and thread bit i on local bits given by the library's
+ *   layout tables (layout 0: the I/O layout).  Each record: kind (0 layout
+ *   change to arg, 1 dense / 2 antidiagonal / 3 exchange 2 x 2 on register
+ *   bit arg, 4 diagonal diag(a, d), 5 phase d on |1>, 6 sign flip, 7 phase
+ *   ramp, 8 no-op), the conditions thr_c / out_c / km_c (thread bits, outer
+ *   qubits, registers that satisfy the controls; plain = no condition), the
+ *   target of a diagonal op or a ramp's shared qubit as thr_t / out_t / km_t,
+ *   and the coefficients m = (A, B, C, D) as (re, im) pairs (a ramp's tables
+ *   span its records' m, four complex entries per record: entry k < 2^RB is
+ *   register k's factor, 2^RB + x and 2^RB + 16 + y the factors of thread
+ *   bits 0..3 set in x and 4..7 set in y).  ops: up to ops_cap records;
+ *   info: SIM_TILE_PASS_INFO int32 per pass (first record, record count, M,
+ *   register bits, amplitudes per I/O vector, number of high qubits, the
+ *   high qubits); *n_ops, *n_passes the full counts.  SIM_EINVAL if no tile
+ *   fits or a gate is invalid. */
+typedef struct sim_tile_op {
+    int32_t kind;
+    int32_t arg;
+    uint32_t thr_c;
+    int32_t plain;
+    uint64_t out_c;
+    uint64_t km_c;
+    uint64_t km_t;
+    uint32_t thr_t;
+    uint32_t pad;
+    uint64_t out_t;
+    double m[8];
+} sim_tile_op;
+#define SIM_TILE_PASS_INFO 24
+int sim_plan_staged_ops(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, sim_tile_op *ops,
+                        size_t ops_cap, int32_t *info, size_t info_cap, size_t *n_ops, size_t *n_passes);
+
 /* ---- instrumentation --------------------------------------------------------
  * sim_profile_enable: when on, every kernel launch of the handle is bracketed
  *   by CUDA events on the handle's stream.

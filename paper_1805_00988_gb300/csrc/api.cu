@@ -449,6 +449,20 @@ int sim_plan_describe(int n, int dtype, const sim_gate *gates, size_t n_gates, c
                            order_cap, order_len);
 }
 
+int sim_plan_staged_ops(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, sim_tile_op *ops,
+                        size_t ops_cap, int32_t *info, size_t info_cap, size_t *n_ops, size_t *n_passes)
+{
+    set_error("");
+    if (n < 1 || n > 34) return fail(SIM_EINVAL, "sim_plan_staged_ops: n must be in [1, 34]");
+    if (dtype != SIM_C64 && dtype != SIM_C128) return fail(SIM_EINVAL, "sim_plan_staged_ops: bad dtype");
+    if (n_gates && !gates) return fail(SIM_EINVAL, "sim_plan_staged_ops: gates is NULL");
+    for (size_t k = 0; k < n_gates; ++k) {
+        std::string why;
+        if (validate_gate(n, gates[k], &why)) return fail(SIM_EINVAL, "sim_plan_staged_ops: " + why);
+    }
+    return encode_staged(n, dtype, gates, n_gates, tile_qubits, ops, ops_cap, info, info_cap, n_ops, n_passes);
+}
+
 int sim_profile_enable(sim_t s, int on)
 {
     if (int rc = check_handle(s)) return rc;

@@ -216,6 +216,8 @@ int describe_fused(int n, const sim_gate *gates, size_t n_gates, int k, int64_t 
 int fused_feature_depth();
 int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, int64_t *passes,
                     int64_t *ops, int64_t *layout_changes, int32_t *order, size_t order_cap, size_t *order_len);
+int encode_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, sim_tile_op *ops,
+                  size_t ops_cap, int32_t *info, size_t info_cap, size_t *n_ops, size_t *n_passes);
 
 // f(0) .. f(count - 1) on up to 16 host threads: the calling thread and a
 // persistent pool (pool.cu).  Serial for one index, inside a pool thread, or

@@ -219,6 +219,52 @@ int describe_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int
     return SIM_OK;
 }
 
+int encode_staged(int n, int dtype, const sim_gate *gates, size_t n_gates, int tile_qubits, sim_tile_op *ops,
+                  size_t ops_cap, int32_t *info, size_t info_cap, size_t *n_ops, size_t *n_passes)
+{
+    const bool c128 = dtype == SIM_C128;
+    int M = tile_qubits ? tile_qubits : (c128 ? 11 : 13);
+    if (M > n || M < 11 || M > (c128 ? 12 : 13)) return fail(SIM_EINVAL, "encode: no staged tile fits");
+    std::vector<SGate> g;
+    lower_gates(gates, n_gates, &g);
+    std::vector<Pass> ps = form_passes(g, n, M);
+    PlanBuilder<double> pb{n, M, M - kThrBits, c128 ? 1 : 2, {}, {}, 0};
+    std::vector<size_t> first;
+    for (const Pass &p : ps) {
+        first.push_back(pb.ops.size());
+        pb.schedule(p, g);
+    }
+    if (n_ops) *n_ops = pb.ops.size();
+    if (n_passes) *n_passes = ps.size();
+    for (size_t k = 0; k < pb.ops.size() && k < ops_cap && ops; ++k) {
+        const StOp<double> &o = pb.ops[k];
+        sim_tile_op &t = ops[k];
+        t.kind = o.kind;
+        t.arg = o.arg;
+        t.thr_c = o.thr_c;
+        t.plain = o.plain;
+        t.out_c = o.out_c;
+        t.km_c = o.km_c;
+        t.km_t = o.km_t;
+        t.thr_t = o.thr_t;
+        t.pad = 0;
+        t.out_t = o.out_t;
+        for (int j = 0; j < 8; ++j) t.m[j] = o.m[j];
+    }
+    for (size_t p = 0; p < ps.size() && info && (p + 1) * SIM_TILE_PASS_INFO <= info_cap; ++p) {
+        int32_t *r = info + p * SIM_TILE_PASS_INFO;
+        for (int j = 0; j < SIM_TILE_PASS_INFO; ++j) r[j] = 0;
+        r[0] = (int32_t)first[p];
+        r[1] = (int32_t)((p + 1 < ps.size() ? first[p + 1] : pb.ops.size()) - first[p]);
+        r[2] = M;
+        r[3] = M - kThrBits;
+        r[4] = c128 ? 1 : 2;
+        r[5] = (int32_t)ps[p].high.size();
+        for (size_t i = 0; i < ps[p].high.size() && i < 16; ++i) r[6 + i] = ps[p].high[i];
+    }
+    return SIM_OK;
+}
+
 int apply_circuit_staged(qsim_state *s, const sim_gate *gates, size_t n_gates, const sim_plan_opts &o)
 {
     const bool c128 = s->dtype == SIM_C128;

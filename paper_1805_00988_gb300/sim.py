@@ -246,6 +246,29 @@ def sim_sample_observe(h: int, shots: int, seed: int, out=None, out_on_device: b
     return arr, a.value, b.value
 
 
+SIM_TILE_OP_DTYPE = np.dtype([("kind", "<i4"), ("arg", "<i4"), ("thr_c", "<u4"), ("plain", "<i4"),
+                              ("out_c", "<u8"), ("km_c", "<u8"), ("km_t", "<u8"), ("thr_t", "<u4"),
+                              ("pad", "<u4"), ("out_t", "<u8"), ("m", "<f8", (8,))])
+SIM_TILE_PASS_INFO = 24
+_sig("sim_plan_staged_ops", [_i32, _i32, P, _sz, _i32, P, _sz, P, _sz, P, P])
+
+
+def sim_plan_staged_ops(n: int, dtype: int, sim_gates: np.ndarray, tile_qubits: int = 0):
+    """The staged plan's encoded op records and per-pass geometry (host only):
+    returns (ops as SIM_TILE_OP_DTYPE records, info as an int32 array of
+    shape (passes, SIM_TILE_PASS_INFO))."""
+    g = np.ascontiguousarray(sim_gates, dtype=SIM_GATE_DTYPE)
+    nops, npass = ctypes.c_size_t(), ctypes.c_size_t()
+    check(_lib.sim_plan_staged_ops(n, dtype, g.ctypes.data_as(P), len(g), tile_qubits, None, 0, None, 0,
+                                   ctypes.byref(nops), ctypes.byref(npass)))
+    ops = np.zeros(nops.value, dtype=SIM_TILE_OP_DTYPE)
+    info = np.zeros((npass.value, SIM_TILE_PASS_INFO), dtype=np.int32)
+    check(_lib.sim_plan_staged_ops(n, dtype, g.ctypes.data_as(P), len(g), tile_qubits, ops.ctypes.data_as(P),
+                                   len(ops), info.ctypes.data_as(P), info.size, ctypes.byref(nops),
+                                   ctypes.byref(npass)))
+    return ops, info
+
+
 def sim_plan_describe(n: int, dtype: int, sim_gates: np.ndarray, opts: sim_plan_opts):
     """Host-only: (passes, ops, layout_changes, order) of the staged schedule."""
     g = np.ascontiguousarray(sim_gates, dtype=SIM_GATE_DTYPE)
